@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the alpha_{2,3} generator on GB300: one JSON line.
+
+Workload (per GPU): one stream seeded with a = 3^33+12345, n = 2^28 FP64
+variates (2 GiB) per step, written to device memory by the library's tiled
+kernel.  Under torchrun each rank generates its own consecutive block of the
+same sequence (rank r: variates r*n .. (r+1)*n-1, skip-ahead, no collective
+on the data path), so the work per GPU is fixed ("weak" scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain C, unsigned __int128 %) on this
+host's cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import datetime as _dt
+import io
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("variates/sec and % of HBM-write roofline (FP64) at 1 GB300; "
+          "p50/p99 request latency")
+UNIT = "variates/s"
+SEED = 3 ** 33 + 12345
+N_DEFAULT = 1 << 28
+WORKLOAD = ("single stream, start index a = 3^33+12345, n = 2^28 FP64 uniforms (2 GiB) "
+            "per GPU per step; rank r generates variates r*n..(r+1)*n-1 of the sequence")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="target CPU time of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": FALLBACK_PEAKS["hbm_gbs"], "source": "fallback"}
+
+
+def profiled_traffic(tag: str):
+    """DRAM bytes per launch recorded in profiles/ for the current sources.
+
+    A summary line reads `traffic_bytes_per_launch[<tag>]: <bytes> digest <hex>`;
+    the value is used only if <hex> matches the library's current source digest
+    (a changed kernel invalidates its counters)."""
+    try:
+        from paper_1206_1187_gb300 import _build
+        digest = _build._inputs_digest([])[:16]
+    except Exception:
+        return None
+    pat = re.compile(r"traffic_bytes_per_launch\[" + re.escape(tag) +
+                     r"\]:\s*([0-9.eE+]+)\s+digest\s+([0-9a-f]+)")
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(pdir, name)) as fh:
+            for m in pat.finditer(fh.read()):
+                if m.group(2) == digest:
+                    return float(m.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("timestamp,index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None, interval_ms: int = 50):
+        self.bus_id = (bus_id or "").lower()
+        self.interval_ms = interval_ms
+        self.proc = None
+        self.file = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 f"-lms={self.interval_ms}"], stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def mark_begin(self):
+        self.t0 = _dt.datetime.now()
+
+    def mark_end(self):
+        self.t1 = _dt.datetime.now()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "nvidia-smi unavailable"}
+        time.sleep(2 * self.interval_ms / 1000.0)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = list(csv.reader(io.StringIO(self.file.read())))
+        self.file.close()
+        os.unlink(self.file.name)
+        samples = []
+        for r in rows:
+            if len(r) < 11:
+                continue
+            r = [x.strip() for x in r]
+            if self.bus_id and self.bus_id not in r[2].lower():
+                continue
+            try:
+                ts = _dt.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                continue
+            samples.append((ts, r))
+        inside = [s for s in samples if self.t0 and self.t1 and self.t0 <= s[0] <= self.t1]
+        if not inside and samples and self.t0:  # region shorter than a sample period
+            after = [s for s in samples if s[0] >= self.t0]
+            inside = after[:1] if after else samples[-1:]
+        reasons = set()
+        sm, smax = [], []
+        for _, r in inside:
+            try:
+                sm.append(float(r[3]))
+                smax.append(float(r[4]))
+            except ValueError:
+                pass
+            for name, col in (("hw_slowdown", 7), ("hw_thermal_slowdown", 8),
+                              ("sw_thermal_slowdown", 9), ("sw_power_cap", 10)):
+                if r[col].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+def cpu_baseline(seconds: float, dtype: str = "f64"):
+    """The oracle, as it stands, on all host cores for a bounded sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    trial = 1 << 20
+    t = time.perf_counter()
+    oracle.generate_mt(SEED, 0, trial, dtype, threads=cores)
+    rate = trial / max(time.perf_counter() - t, 1e-9)
+    sample = int(min(max(rate * seconds, 1 << 20), N_DEFAULT))
+    t = time.perf_counter()
+    oracle.generate_mt(SEED, 0, sample, dtype, threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} FP64 variates of the workload's stream "
+                      f"(a = 3^33+12345), split over {cores} threads by skip-ahead; "
+                      f"{dt:.2f} s wall"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    cores = os.cpu_count() or 1
+    trial = 1 << 18
+    t = time.perf_counter()
+    oracle.generate_mt(SEED, 0, trial, "f64", threads=cores)
+    rate = trial / max(time.perf_counter() - t, 1e-9)
+    budget = min(120.0 / max(args.steps + args.warmup, 1), 10.0)  # whole run ~2 min
+    sample = int(min(max(rate * budget, 1 << 12), args.n))
+    buf = None
+    import numpy as np
+    buf = np.empty(sample, dtype=np.float64)
+    for _ in range(args.warmup):
+        oracle.generate_mt(SEED, 0, sample, "f64", threads=cores, out=buf)
+    t = time.perf_counter()
+    for k in range(args.steps):
+        oracle.generate_mt(SEED, k * sample, sample, "f64", threads=cores, out=buf)
+    dt = time.perf_counter() - t
+    ms = dt * 1e3 / max(args.steps, 1)
+    value = sample / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": args.n, "seed": SEED,
+                   "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} consecutive FP64 variates of the workload's "
+                                   f"stream per step, {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1206_1187_gb300 import rng
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    offset = rank * n
+    dev = torch.device("cuda", local)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    ptr = out.data_ptr()
+    tune = rng.resolve_tune(n, "f64")
+
+    def step():
+        rng.generate_at_ptr(SEED, offset, n, "f64", ptr, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(dev)
+    bus = None
+    try:
+        bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}"
+    except Exception:
+        pass
+    sampler = ClockSampler(bus if rank == 0 else None)
+    if rank == 0:
+        sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler.mark_begin()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark_end()
+    barrier()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    clocks = sampler.stop() if rank == 0 else None
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms / 1e3)
+
+    # the paper's Constant kernel: same tiled store path, no generation
+    fills = max(min(args.steps, 200), 3)
+    for _ in range(3):
+        rng.fill_constant(n, "f64", 0.5, out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(fills):
+        rng.fill_constant(n, "f64", 0.5, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fill = e0.elapsed_time(e1) / fills
+
+    # end to end through the public API with a pinned host buffer
+    host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    s = rng.Stream(SEED)
+    s.skip(offset)
+    for _ in range(1):
+        s.generate(n, "f64", out=out, stream=stream)
+        host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    t = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.generate(n, "f64", out=out, stream=stream)
+        host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t) / max(args.e2e_steps, 1)
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": 8 * n,
+           "note": "inputs are the scalars (seed, offset, n) passed by value; each step "
+                   "generates into device memory and copies the 8n-byte result to pinned "
+                   "host memory, host wall clock"}
+    del host
+
+    if rank == 0:
+        peaks = load_peaks()
+        bytes_per_launch = 8.0 * n
+        achieved = bytes_per_launch / (ms / 1e3) / 1e9
+        fill_gbs = bytes_per_launch / (ms_fill / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": profiled_traffic("bulk_f64_2e28"),
+                    "peak_source": f"{peaks['source']} HBM copy bandwidth (read+write), "
+                                   "MEASURED_PEAKS.json",
+                    "algorithmic_bytes_per_launch": bytes_per_launch}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "output_dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "seed": SEED, "tune": tune,
+                       "l2": "each step writes 2 GiB (> 126 MB L2); no flush needed"},
+            "roofline": roofline,
+            "write_ceiling": {"kernel": "constant fill, same tiled store path (Sec. 3.2)",
+                              "gbs": fill_gbs, "frac_of_peak": fill_gbs / peaks["hbm_gbs"],
+                              "generation_frac_of_ceiling": achieved / fill_gbs},
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * bcn_rng.h -- C ABI of the GB300 (sm_103a) alpha_{2,3} random variate
+ * generator of Beliakov, Johnstone, Creighton and Wilkin, "Parallel random
+ * variates generator for GPUs based on normal numbers".
+ *
+ * The generator is Algorithm BB (Sec. 1): a start index a in
+ * [3^33+100, 2^53] is the seed, Eq. 2 gives
+ *     z_0 = 2^(a - 3^33) * floor(3^33/2)  mod 3^33,
+ * Eq. 3 iterates z_k = 2^53 z_(k-1) mod 3^33 and each z_k * 3^-33 is one
+ * variate in (0,1).  Variate number i (counted from 0) of a stream is
+ *     z = 2^((a - 3^33 + 53*(i+1)) mod P) * floor(3^33/2)  mod 3^33,
+ * P = 2*3^32 the period, so any block of the sequence is reachable directly
+ * (the skip-ahead property of Sec. 1) and the output does not depend on how
+ * the work is split over threads.
+ *
+ * Output types:
+ *   RNG_F64  double, RN(z * r3i) with r3i = 1.0/5559060566555523.0 (Fig. 4),
+ *            one round-to-nearest multiply, no fused multiply-add.
+ *   RNG_F32  float, the RNG_F64 variate rounded toward zero (stays in (0,1)).
+ *   RNG_U64  the integer state z itself.
+ *
+ * Conventions for every entry point:
+ *   - Return value: an rng_status; RNG_OK on success.  Nothing is thrown
+ *     across this boundary.  rng_last_error() gives a message for the
+ *     calling thread's last failure.
+ *   - Device pointers are caller-owned CUDA global-memory addresses (for
+ *     example a torch tensor's data_ptr()) on the current CUDA device; the
+ *     library never frees them.  A pointer must be aligned to its element
+ *     size, else RNG_EINVAL.
+ *   - `cuda_stream` arguments are cudaStream_t handles passed as void*
+ *     (NULL = the legacy default stream).  Generation calls are asynchronous
+ *     on that stream: they return after the launch, and the caller orders
+ *     later use of the output on the same stream.  They allocate nothing
+ *     and synchronise nothing, so they may be captured in a CUDA graph.
+ *   - A launch failure reported by the CUDA runtime is RNG_ECUDA.
+ *   - bcn_stream objects are not thread-safe; use one per host thread.
+ */
+#ifndef BCN_RNG_H
+#define BCN_RNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bcn_stream bcn_stream;
+
+typedef enum { RNG_F64 = 0, RNG_F32 = 1, RNG_U64 = 2 } rng_dtype;
+
+typedef enum {
+  RNG_OK = 0,
+  RNG_EINVAL = 1,   /* bad pointer, alignment, dtype, size or tuning field */
+  RNG_ERANGE = 2,   /* seed outside [3^33+100, 2^53], or a count overflow  */
+  RNG_ENOMEM = 3,   /* host allocation failed                              */
+  RNG_ECUDA = 4,    /* the CUDA runtime reported an error                  */
+  RNG_ETIMEOUT = 5, /* a bounded device-side wait ran out                  */
+  RNG_EBUSY = 6     /* resource in use                                     */
+} rng_status;
+
+/* The reduction that advances the state (Sec. 2.1). */
+typedef enum {
+  RNG_STEP_AUTO = 0,       /* the measured-fastest variant                  */
+  RNG_STEP_BARRETT = 1,    /* Modified Barrett, Sec. 2.1.3, forward         */
+  RNG_STEP_MONTGOMERY = 2  /* Montgomery-style, R = 2^53, blocks run back   */
+} rng_step;
+
+/* How a state becomes an FP64 variate (the RN multiply of Algorithm BB). */
+typedef enum {
+  RNG_CONV_AUTO = 0,
+  RNG_CONV_INT = 1,   /* exact rounding emulated on the integer pipes      */
+  RNG_CONV_FP64 = 2   /* int->double conversion and DMUL on the FP64 pipe  */
+} rng_conv;
+
+/* Work layout of a bulk call. */
+typedef enum {
+  RNG_LAYOUT_AUTO = 0,
+  RNG_LAYOUT_TILED = 1,  /* lanes of a warp own consecutive runs of `depth`
+                            variates of one tile; the warp's tile is staged in
+                            shared memory and written by one bulk async copy */
+  RNG_LAYOUT_DIRECT = 2  /* thread t of T owns [t*n/T, (t+1)*n/T) and stores
+                            each variate itself (the paper's per-thread split,
+                            Sec. 1; uncoalesced) */
+} rng_layout;
+
+/* Skip-ahead method for the state at the start of a block (Eq. 2). */
+typedef enum {
+  RNG_SKIP_AUTO = 0,
+  RNG_SKIP_TABLE = 1,  /* 2^e from a compile-time table of 2^(d*256^k) */
+  RNG_SKIP_SQMUL = 2   /* binary square-and-multiply                   */
+} rng_skip_method;
+
+/* Launch tuning.  Zero in any field means "choose".  Results never depend on
+ * these fields; only speed does. */
+typedef struct {
+  uint32_t step;    /* rng_step                                              */
+  uint32_t conv;    /* rng_conv                                              */
+  uint32_t layout;  /* rng_layout                                            */
+  uint32_t skip;    /* rng_skip_method                                       */
+  uint32_t depth;   /* TILED: variates per lane per tile, odd, 1..255        */
+  uint32_t block;   /* threads per block (TILED: multiple of 32, <= 1024)    */
+  uint32_t grid;    /* blocks                                                */
+  uint32_t reserved;
+} rng_tune;
+
+/* Largest n accepted by one generation call. */
+#define RNG_MAX_N (1ULL << 46)
+
+/* ---------------------------------------------------------------- streams */
+
+/* Create a stream seeded with start index `start_index` (Algorithm BB,
+ * step 1: 3^33+100 <= start_index <= 2^53, else RNG_ERANGE).  The stream's
+ * count starts at 0 and it launches on the default CUDA stream until
+ * rng_set_cuda_stream.  *out is library-owned; free it with rng_destroy. */
+rng_status rng_create(uint64_t start_index, bcn_stream **out);
+
+/* Free a stream created by rng_create.  NULL is a no-op. */
+rng_status rng_destroy(bcn_stream *s);
+
+/* Launch this stream's work on `cuda_stream` (a cudaStream_t). */
+rng_status rng_set_cuda_stream(bcn_stream *s, void *cuda_stream);
+
+/* Write the stream's next n variates (numbers count .. count+n-1, Eq. 3)
+ * to the device array `out` (n elements of `dt`) and advance count by n.
+ * n = 0 is a no-op.  n > RNG_MAX_N or a count past 2^64-1 is RNG_ERANGE. */
+rng_status rng_generate(bcn_stream *s, uint64_t n, rng_dtype dt, void *out);
+
+/* rng_generate with explicit launch tuning (NULL = automatic). */
+rng_status rng_generate_tuned(bcn_stream *s, uint64_t n, rng_dtype dt, void *out,
+                              const rng_tune *tune);
+
+/* Advance the count by k without generating (skip-ahead, Sec. 1; O(1)). */
+rng_status rng_skip(bcn_stream *s, uint64_t k);
+
+/* Checkpoint: the stream's seed and count.  The pair fully determines every
+ * later variate; rng_set_state restores it (seed range as rng_create). */
+rng_status rng_get_state(const bcn_stream *s, uint64_t *start_index, uint64_t *count);
+rng_status rng_set_state(bcn_stream *s, uint64_t start_index, uint64_t count);
+
+/* Wait for the stream's CUDA stream and report any asynchronous error. */
+rng_status rng_sync(bcn_stream *s);
+
+/* ------------------------------------------------------------- stateless */
+
+/* Variates offset .. offset+n-1 of the sequence seeded with start_index,
+ * written to `out` on `cuda_stream`.  Same rules as rng_generate. */
+rng_status rng_generate_at(uint64_t start_index, uint64_t offset, uint64_t n,
+                           rng_dtype dt, void *out, void *cuda_stream,
+                           const rng_tune *tune);
+
+/* Roofline probe (the paper's "Constant" kernel, Sec. 3.2): write the FP64
+ * (dt = RNG_F64) or FP32 constant `value` n times to `out` with the same
+ * tiled shared-memory + bulk-copy store path as generation.  Its rate is the
+ * write ceiling the generator is measured against. */
+rng_status rng_fill_constant(uint64_t n, rng_dtype dt, double value, void *out,
+                             void *cuda_stream, const rng_tune *tune);
+
+/* ------------------------------------------------------------- utilities */
+
+/* The calling thread's last error message ("" if none). */
+const char *rng_last_error(void);
+
+/* The choices an automatic call makes for (n, dt) on the current device. */
+rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune *in, rng_tune *out);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int rng_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCN_RNG_H */

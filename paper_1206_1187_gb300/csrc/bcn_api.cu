@@ -1,0 +1,224 @@
+// bcn_api.cu -- the C ABI of include/bcn_rng.h: streams, argument checks,
+// error reporting and device properties.  All numerical work happens in the
+// kernels; this file only validates, resolves launch shapes and launches.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "bcn_internal.h"
+#include "bcn_math.cuh"
+
+struct bcn_stream {
+  uint64_t seed;
+  uint64_t count;
+  cudaStream_t cs;
+};
+
+namespace bcn {
+
+static thread_local char g_err[512];
+
+rng_status set_error(rng_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+rng_status cuda_error(cudaError_t e, const char* what) {
+  return set_error(RNG_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e),
+                   cudaGetErrorString(e));
+}
+
+rng_status device_info(DeviceInfo* out) {
+  static std::mutex mu;
+  static std::vector<DeviceInfo> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(mu);
+  for (const DeviceInfo& d : cache)
+    if (d.device == dev) {
+      *out = d;
+      return RNG_OK;
+    }
+  DeviceInfo d = {};
+  d.device = dev;
+  e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute(SM count)");
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute(shared memory)");
+  d.smem_optin = (size_t)optin;
+  cache.push_back(d);
+  *out = d;
+  return RNG_OK;
+}
+
+static bool seed_ok(uint64_t seed) { return seed >= kSeedMin && seed <= kSeedMax; }
+
+// Shared checks of a bulk call; returns RNG_OK when there is work to launch
+// and sets *empty when n == 0.
+static rng_status check_bulk(uint64_t seed, uint64_t n, int dt, const void* out,
+                             bool* empty) {
+  *empty = false;
+  if (!seed_ok(seed))
+    return set_error(RNG_ERANGE, "start index %llu outside [3^33+100, 2^53]",
+                     (unsigned long long)seed);
+  if (dt != RNG_F64 && dt != RNG_F32 && dt != RNG_U64)
+    return set_error(RNG_EINVAL, "dtype %d is not an rng_dtype", dt);
+  if (n == 0) {
+    *empty = true;
+    return RNG_OK;
+  }
+  if (n > RNG_MAX_N)
+    return set_error(RNG_ERANGE, "n = %llu exceeds RNG_MAX_N", (unsigned long long)n);
+  if (out == nullptr) return set_error(RNG_EINVAL, "output pointer is NULL");
+  if ((uintptr_t)out % dtype_size(dt) != 0)
+    return set_error(RNG_EINVAL, "output pointer is not aligned to its %zu-byte elements",
+                     dtype_size(dt));
+  return RNG_OK;
+}
+
+static rng_status generate_impl(uint64_t seed, uint64_t i0, uint64_t n, int dt, void* out,
+                                cudaStream_t cs, const rng_tune* tune) {
+  bool empty = false;
+  rng_status st = check_bulk(seed, n, dt, out, &empty);
+  if (st != RNG_OK || empty) return st;
+  BulkLaunch L;
+  st = resolve_bulk(n, dt, tune, &L, false);
+  if (st != RNG_OK) return st;
+  return launch_bulk(L, seed, i0, n, out, 0, cs);
+}
+
+}  // namespace bcn
+
+using namespace bcn;
+
+extern "C" {
+
+rng_status rng_create(uint64_t start_index, bcn_stream** out) {
+  if (!out) return set_error(RNG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!seed_ok(start_index))
+    return set_error(RNG_ERANGE, "start index %llu outside [3^33+100, 2^53]",
+                     (unsigned long long)start_index);
+  bcn_stream* s = new (std::nothrow) bcn_stream;
+  if (!s) return set_error(RNG_ENOMEM, "out of host memory");
+  s->seed = start_index;
+  s->count = 0;
+  s->cs = nullptr;
+  *out = s;
+  return RNG_OK;
+}
+
+rng_status rng_destroy(bcn_stream* s) {
+  delete s;
+  return RNG_OK;
+}
+
+rng_status rng_set_cuda_stream(bcn_stream* s, void* cuda_stream) {
+  if (!s) return set_error(RNG_EINVAL, "stream is NULL");
+  s->cs = static_cast<cudaStream_t>(cuda_stream);
+  return RNG_OK;
+}
+
+rng_status rng_generate_tuned(bcn_stream* s, uint64_t n, rng_dtype dt, void* out,
+                              const rng_tune* tune) {
+  if (!s) return set_error(RNG_EINVAL, "stream is NULL");
+  if (n > UINT64_MAX - s->count)
+    return set_error(RNG_ERANGE, "count would pass 2^64-1");
+  rng_status st = generate_impl(s->seed, s->count, n, dt, out, s->cs, tune);
+  if (st == RNG_OK) s->count += n;
+  return st;
+}
+
+rng_status rng_generate(bcn_stream* s, uint64_t n, rng_dtype dt, void* out) {
+  return rng_generate_tuned(s, n, dt, out, nullptr);
+}
+
+rng_status rng_skip(bcn_stream* s, uint64_t k) {
+  if (!s) return set_error(RNG_EINVAL, "stream is NULL");
+  if (k > UINT64_MAX - s->count) return set_error(RNG_ERANGE, "count would pass 2^64-1");
+  s->count += k;
+  return RNG_OK;
+}
+
+rng_status rng_get_state(const bcn_stream* s, uint64_t* start_index, uint64_t* count) {
+  if (!s || !start_index || !count) return set_error(RNG_EINVAL, "NULL argument");
+  *start_index = s->seed;
+  *count = s->count;
+  return RNG_OK;
+}
+
+rng_status rng_set_state(bcn_stream* s, uint64_t start_index, uint64_t count) {
+  if (!s) return set_error(RNG_EINVAL, "stream is NULL");
+  if (!seed_ok(start_index))
+    return set_error(RNG_ERANGE, "start index %llu outside [3^33+100, 2^53]",
+                     (unsigned long long)start_index);
+  s->seed = start_index;
+  s->count = count;
+  return RNG_OK;
+}
+
+rng_status rng_sync(bcn_stream* s) {
+  if (!s) return set_error(RNG_EINVAL, "stream is NULL");
+  cudaError_t e = cudaStreamSynchronize(s->cs);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "asynchronous error");
+  return RNG_OK;
+}
+
+rng_status rng_generate_at(uint64_t start_index, uint64_t offset, uint64_t n, rng_dtype dt,
+                           void* out, void* cuda_stream, const rng_tune* tune) {
+  return generate_impl(start_index, offset, n, dt, out, static_cast<cudaStream_t>(cuda_stream),
+                       tune);
+}
+
+rng_status rng_fill_constant(uint64_t n, rng_dtype dt, double value, void* out,
+                             void* cuda_stream, const rng_tune* tune) {
+  bool empty = false;
+  rng_status st = check_bulk(kSeedMin, n, dt, out, &empty);
+  if (st != RNG_OK || empty) return st;
+  if (dt == RNG_U64) return set_error(RNG_EINVAL, "the constant fill writes RNG_F64 or RNG_F32");
+  uint64_t bits = 0;
+  if (dt == RNG_F64) {
+    std::memcpy(&bits, &value, 8);
+  } else {
+    float f = (float)value;
+    uint32_t b32;
+    std::memcpy(&b32, &f, 4);
+    bits = b32;
+  }
+  BulkLaunch L;
+  st = resolve_bulk(n, dt, tune, &L, true);
+  if (st != RNG_OK) return st;
+  return launch_bulk(L, kSeedMin, 0, n, out, bits, static_cast<cudaStream_t>(cuda_stream));
+}
+
+const char* rng_last_error(void) { return g_err; }
+
+rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune* in, rng_tune* out) {
+  if (!out) return set_error(RNG_EINVAL, "out is NULL");
+  BulkLaunch L;
+  rng_status st = resolve_bulk(n, dt, in, &L, false);
+  if (st != RNG_OK) return st;
+  out->step = (uint32_t)L.step;
+  out->conv = (uint32_t)L.conv;
+  out->layout = (uint32_t)L.layout;
+  out->skip = (uint32_t)L.skip;
+  out->depth = L.depth;
+  out->block = L.block;
+  out->grid = L.grid;
+  out->reserved = 0;
+  return RNG_OK;
+}
+
+int rng_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,405 @@
+// bcn_bulk.cu -- bulk generation kernels for one stream (sm_103a).
+//
+// TILED layout (the fast path).  Output elements [head, head + ntiles*32*c)
+// are cut into tiles of 32*c elements (c = depth, odd).  Each warp owns a
+// contiguous range of tiles; in a tile, lane l owns elements [l*c, (l+1)*c)
+// and produces them with c consecutive steps of Eq. 3 from one state, so the
+// per-variate work is one reduction and one conversion.  Lanes write their
+// runs to a per-warp shared-memory tile (odd c makes the 8-byte and 4-byte
+// stores bank-conflict free), and one lane hands the whole tile to the bulk
+// async-copy engine (cp.async.bulk shared::cta -> global), so global memory
+// sees one contiguous, 16-byte aligned write per tile with no per-thread
+// store instructions.  Two tile buffers per warp let the copy of one tile
+// overlap the generation of the next.  Moving from a tile to the warp's next
+// tile is one modular product by a precomputed power of 2^53.
+//
+// DIRECT layout (the paper's per-thread split, Sec. 1): thread t of T owns
+// [t*n/T, (t+1)*n/T) and stores each variate itself.  It serves odd thread
+// counts (down to one thread) and is the uncoalesced baseline.
+//
+// The head (elements before the first 16-byte boundary) and the tail (fewer
+// than one tile) are produced by the last warp of the grid with direct
+// stores.  Every element's value depends only on its index, so the result is
+// identical for every layout, depth, block and grid.
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "bcn_internal.h"
+#include "bcn_math.cuh"
+
+namespace bcn {
+
+template <int DT> struct Word { typedef uint64_t type; };
+template <> struct Word<DT_F32> { typedef uint32_t type; };
+
+// The output word of state z.  (phi, plo) is the product z*mu when the
+// caller has it (Barrett) -- the integer conversion reuses it.
+template <int DT, int CONV>
+__device__ __forceinline__ typename Word<DT>::type to_word(uint64_t z, uint64_t phi,
+                                                           uint64_t plo) {
+  if constexpr (DT == DT_U64) {
+    return z;
+  } else {
+    uint64_t bits;
+    if constexpr (CONV == CV_INT) {
+      uint64_t qh, ql;
+      p_from_barrett_product(z, phi, plo, qh, ql);
+      bits = f64_bits_from_p(qh, ql);
+    } else {
+      bits = f64_bits_fp64(z);
+    }
+    if constexpr (DT == DT_F64) return bits;
+    else return f32_bits_from_f64_bits(bits);
+  }
+}
+
+// One chain of the generator.  Barrett runs forward (z is the state of the
+// next variate to emit); Montgomery runs backward (z is the state of the
+// variate emitted next, going down).
+template <int DT, int STEP, int CONV>
+struct Gen {
+  uint64_t z;
+  __device__ __forceinline__ typename Word<DT>::type next() {
+    if constexpr (STEP == ST_BARRETT) {
+      uint64_t plo = z * kMu, phi = umulhi(z, kMu);
+      auto w = to_word<DT, CONV>(z, phi, plo);
+      z = barrett_from_product(phi, plo);
+      return w;
+    } else {
+      uint64_t plo = 0, phi = 0;
+      if constexpr (DT != DT_U64 && CONV == CV_INT) {
+        plo = z * kMu;
+        phi = umulhi(z, kMu);
+      }
+      auto w = to_word<DT, CONV>(z, phi, plo);
+      z = montgomery_back(z);
+      return w;
+    }
+  }
+};
+
+__device__ __forceinline__ uint64_t seed_state(uint64_t e, uint32_t skip) {
+  return skip == SK_SQMUL ? seed_state_sqmul(e) : seed_state_table(e);
+}
+
+// State of element idx of the call: exponent ebase + 53*(idx+1)  (mod P).
+__device__ __forceinline__ uint64_t state_of(uint64_t ebase, uint64_t idx, uint32_t skip) {
+  return seed_state(exponent_add(ebase, idx + 1), skip);
+}
+
+// Elements [a, b) with plain global stores.
+template <int DT, int STEP, int CONV>
+__device__ void run_direct(typename Word<DT>::type* __restrict__ out, uint64_t ebase,
+                           uint32_t skip, uint64_t a, uint64_t b, uint64_t cbits) {
+  typedef typename Word<DT>::type W;
+  if (a >= b) return;
+  if constexpr (STEP == ST_CONST) {
+    for (uint64_t i = a; i < b; ++i) out[i] = (W)cbits;
+  } else if constexpr (STEP == ST_BARRETT) {
+    Gen<DT, STEP, CONV> g{state_of(ebase, a, skip)};
+    for (uint64_t i = a; i < b; ++i) out[i] = g.next();
+  } else {
+    Gen<DT, STEP, CONV> g{state_of(ebase, b - 1, skip)};
+    for (uint64_t i = b; i-- > a;) out[i] = g.next();
+  }
+}
+
+// ------------------------------------------------------- bulk async copies
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+  const uint64_t g = (uint64_t)__cvta_generic_to_global(gdst);
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+               :: "l"(g), "r"(s), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+struct TiledParams {
+  unsigned char* out;  // element 0 of the call
+  uint64_t n;          // elements in the call
+  uint64_t head;       // elements before the first 16-byte boundary
+  uint64_t ntiles;     // full tiles of 32*depth elements after the head
+  uint64_t ebase;      // (seed - 3^33 + 53*i0) mod P
+  uint64_t jump;       // 2^(53*31*depth) (Barrett) / 2^(53*33*depth) (Montgomery)
+  uint64_t cbits;      // ST_CONST: the word written
+  uint32_t depth;
+  uint32_t skip;
+};
+
+struct DirectParams {
+  unsigned char* out;
+  uint64_t n;
+  uint64_t ebase;
+  uint64_t cbits;
+  uint32_t skip;
+};
+
+template <int DT, int STEP, int CONV>
+__global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
+  typedef typename Word<DT>::type W;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t wpb = blockDim.x >> 5;
+  const uint64_t gw = (uint64_t)blockIdx.x * wpb + warp;
+  const uint64_t nw = (uint64_t)gridDim.x * wpb;
+  const uint32_t c = p.depth;
+  const uint32_t tile_elems = 32u * c;
+  const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
+  W* const buf0 = reinterpret_cast<W*>(smem + (size_t)warp * 2u * tile_bytes);
+  W* const out = reinterpret_cast<W*>(p.out);
+
+  const uint64_t t0 = gw * p.ntiles / nw;
+  const uint64_t t1 = (gw + 1) * p.ntiles / nw;
+  if (t0 < t1) {
+    // this lane's first element in the warp's first tile
+    const uint64_t first = p.head + t0 * tile_elems + (uint64_t)lane * c;
+    Gen<DT, STEP, CONV> g{0};
+    if constexpr (STEP == ST_BARRETT) g.z = state_of(p.ebase, first, p.skip);
+    if constexpr (STEP == ST_MONT) g.z = state_of(p.ebase, first + c - 1, p.skip);
+    for (uint64_t t = t0; t < t1; ++t) {
+      const uint32_t k = (uint32_t)(t - t0);
+      W* const buf = buf0 + (k & 1u) * tile_elems;
+      if (k >= 2) {  // the copy that last read this buffer must be done
+        if (lane == 0) bulk_wait_read_1();
+        __syncwarp();
+      }
+      W* const mine = buf + lane * c;
+      if constexpr (STEP == ST_CONST) {
+        for (uint32_t i = 0; i < c; ++i) mine[i] = (W)p.cbits;
+      } else if constexpr (STEP == ST_BARRETT) {
+#pragma unroll 4
+        for (uint32_t i = 0; i < c; ++i) mine[i] = g.next();
+      } else {
+#pragma unroll 4
+        for (uint32_t i = c; i-- > 0;) mine[i] = g.next();
+      }
+      fence_proxy_async_shared();
+      __syncwarp();
+      if (lane == 0) {
+        bulk_store(out + p.head + t * tile_elems, buf, tile_bytes);
+        bulk_commit();
+      }
+      if constexpr (STEP != ST_CONST) {
+        if (t + 1 < t1) g.z = mulmod(g.z, p.jump);
+      }
+    }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+  }
+
+  if (gw == nw - 1) {  // head and tail, split contiguously over the lanes
+    const uint64_t tail0 = p.head + p.ntiles * tile_elems;
+    const uint64_t tl = p.n - tail0;
+    run_direct<DT, STEP, CONV>(out, p.ebase, p.skip, lane * p.head / 32,
+                               (lane + 1) * p.head / 32, p.cbits);
+    run_direct<DT, STEP, CONV>(out, p.ebase, p.skip, tail0 + lane * tl / 32,
+                               tail0 + (lane + 1) * tl / 32, p.cbits);
+  }
+}
+
+template <int DT, int STEP, int CONV>
+__global__ void __launch_bounds__(1024) direct_kernel(const DirectParams p) {
+  typedef typename Word<DT>::type W;
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t a = (uint64_t)((u128)p.n * t / T);
+  const uint64_t b = (uint64_t)((u128)p.n * (t + 1) / T);
+  run_direct<DT, STEP, CONV>(reinterpret_cast<W*>(p.out), p.ebase, p.skip, a, b, p.cbits);
+}
+
+// ------------------------------------------------------------ dispatch
+template <int DT, int ST>
+static const void* pick_cv(int layout, int cv) {
+  if (layout == RNG_LAYOUT_TILED)
+    return cv == CV_FP64 ? (const void*)tiled_kernel<DT, ST, CV_FP64>
+                         : (const void*)tiled_kernel<DT, ST, CV_INT>;
+  return cv == CV_FP64 ? (const void*)direct_kernel<DT, ST, CV_FP64>
+                       : (const void*)direct_kernel<DT, ST, CV_INT>;
+}
+
+template <int DT>
+static const void* pick_st(int layout, int st, int cv) {
+  if (DT == DT_U64) cv = CV_INT;  // no conversion for raw states
+  switch (st) {
+    case ST_BARRETT: return pick_cv<DT, ST_BARRETT>(layout, cv);
+    case ST_MONT: return pick_cv<DT, ST_MONT>(layout, cv);
+    default: return nullptr;
+  }
+}
+
+static const void* pick_kernel(int layout, int dt, int st, int cv) {
+  if (st == ST_CONST) {
+    if (dt == DT_F64) return layout == RNG_LAYOUT_TILED
+                                 ? (const void*)tiled_kernel<DT_F64, ST_CONST, CV_INT>
+                                 : (const void*)direct_kernel<DT_F64, ST_CONST, CV_INT>;
+    if (dt == DT_F32) return layout == RNG_LAYOUT_TILED
+                                 ? (const void*)tiled_kernel<DT_F32, ST_CONST, CV_INT>
+                                 : (const void*)direct_kernel<DT_F32, ST_CONST, CV_INT>;
+    return nullptr;
+  }
+  switch (dt) {
+    case DT_F64: return pick_st<DT_F64>(layout, st, cv);
+    case DT_F32: return pick_st<DT_F32>(layout, st, cv);
+    case DT_U64: return pick_st<DT_U64>(layout, st, cv);
+    default: return nullptr;
+  }
+}
+
+// Large dynamic shared memory must be enabled once per kernel and device.
+static rng_status enable_smem(const void* fn, int device, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({fn, device})) return RNG_OK;
+  DeviceInfo di;
+  rng_status st = device_info(&di);
+  if (st != RNG_OK) return st;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)di.smem_optin);
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+  (void)bytes;
+  done.insert({fn, device});
+  return RNG_OK;
+}
+
+static uint64_t tile_count(uint64_t n, uint64_t head, uint32_t depth) {
+  return n > head ? (n - head) / (32ull * depth) : 0;
+}
+
+static uint64_t head_elems(const void* out, size_t esz, uint64_t n) {
+  const uintptr_t addr = (uintptr_t)out;
+  uint64_t h = ((16 - (addr & 15)) & 15) / esz;
+  return h < n ? h : n;
+}
+
+rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* out,
+                        bool constant) {
+  rng_tune t = {};
+  if (tune) t = *tune;
+  BulkLaunch L = {};
+  L.dt = dt;
+  L.layout = t.layout ? (int)t.layout : RNG_LAYOUT_TILED;
+  L.step = constant ? ST_CONST : (t.step ? (int)t.step : ST_BARRETT);
+  L.conv = t.conv ? (int)t.conv : CV_INT;
+  L.skip = t.skip ? (int)t.skip : SK_TABLE;
+  if (L.layout != RNG_LAYOUT_TILED && L.layout != RNG_LAYOUT_DIRECT)
+    return set_error(RNG_EINVAL, "tune.layout %u is not a layout", t.layout);
+  if (!constant && L.step != ST_BARRETT && L.step != ST_MONT)
+    return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
+  if (L.conv != CV_INT && L.conv != CV_FP64)
+    return set_error(RNG_EINVAL, "tune.conv %u is not a conversion", t.conv);
+  if (L.skip != SK_TABLE && L.skip != SK_SQMUL)
+    return set_error(RNG_EINVAL, "tune.skip %u is not a skip-ahead method", t.skip);
+  if (dt != DT_F64 && dt != DT_F32 && dt != DT_U64)
+    return set_error(RNG_EINVAL, "dtype %d is not an rng_dtype", dt);
+  if (constant && dt == DT_U64)
+    return set_error(RNG_EINVAL, "the constant fill writes RNG_F64 or RNG_F32");
+  DeviceInfo di;
+  rng_status st = device_info(&di);
+  if (st != RNG_OK) return st;
+  const void* fn = pick_kernel(L.layout, dt, L.step, L.conv);
+  if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
+  if (L.layout == RNG_LAYOUT_TILED) {
+    L.depth = t.depth ? t.depth : 15;
+    L.block = t.block ? t.block : 256;
+    if (L.depth % 2 == 0 || L.depth > kMaxDepth)
+      return set_error(RNG_EINVAL, "tune.depth %u must be odd and at most %u", L.depth,
+                       kMaxDepth);
+    if (L.block % 32 != 0 || L.block == 0 || L.block > 1024)
+      return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024",
+                       L.block);
+    L.smem_bytes = (size_t)(L.block / 32) * 2 * 32 * L.depth * dtype_size(dt);
+    if (L.smem_bytes > di.smem_optin)
+      return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
+                       L.smem_bytes, di.smem_optin);
+    if (t.grid) {
+      L.grid = t.grid;
+    } else {
+      st = enable_smem(fn, di.device, L.smem_bytes);
+      if (st != RNG_OK) return st;
+      int per_sm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)L.block,
+                                                                    L.smem_bytes);
+      if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      if (per_sm < 1) per_sm = 1;
+      uint64_t full = (uint64_t)per_sm * (uint64_t)di.sms;
+      // no more warps than tiles (at least one block for the edges)
+      uint64_t tiles = tile_count(n, 0, L.depth);
+      uint64_t need = (tiles + L.block / 32 - 1) / (L.block / 32);
+      if (need < 1) need = 1;
+      L.grid = (uint32_t)(need < full ? need : full);
+    }
+  } else {
+    L.depth = 0;
+    L.block = t.block ? t.block : 256;
+    if (L.block == 0 || L.block > 1024)
+      return set_error(RNG_EINVAL, "tune.block %u must be in 1..1024", L.block);
+    if (t.grid) {
+      L.grid = t.grid;
+    } else {
+      // the paper's best split: about 4096 variates per thread (Sec. 2.2)
+      uint64_t threads = (n + 4095) / 4096;
+      uint64_t g = (threads + L.block - 1) / L.block;
+      if (g < 1) g = 1;
+      if (g > (1u << 30)) g = 1u << 30;
+      L.grid = (uint32_t)g;
+    }
+  }
+  if (L.grid == 0 || L.grid > (1u << 30))
+    return set_error(RNG_EINVAL, "tune.grid %u out of range", L.grid);
+  *out = L;
+  return RNG_OK;
+}
+
+rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t n,
+                       void* out, uint64_t const_bits, cudaStream_t cs) {
+  const void* fn = pick_kernel(L.layout, L.dt, L.step, L.conv);
+  if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
+  const uint64_t ebase = (L.step == ST_CONST) ? 0 : host_exponent_base(seed, i0);
+  cudaError_t e;
+  if (L.layout == RNG_LAYOUT_TILED) {
+    DeviceInfo di;
+    rng_status st = device_info(&di);
+    if (st != RNG_OK) return st;
+    st = enable_smem(fn, di.device, L.smem_bytes);
+    if (st != RNG_OK) return st;
+    TiledParams p;
+    p.out = static_cast<unsigned char*>(out);
+    p.n = n;
+    p.head = head_elems(out, dtype_size(L.dt), n);
+    p.ntiles = tile_count(n, p.head, L.depth);
+    p.ebase = ebase;
+    const uint64_t stride = (L.step == ST_MONT) ? 33ull : 31ull;
+    p.jump = host_pow2((53ull * stride * L.depth) % kP);
+    p.cbits = const_bits;
+    p.depth = L.depth;
+    p.skip = (uint32_t)L.skip;
+    void* args[] = {&p};
+    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.block), args, L.smem_bytes, cs);
+  } else {
+    DirectParams p;
+    p.out = static_cast<unsigned char*>(out);
+    p.n = n;
+    p.ebase = ebase;
+    p.cbits = const_bits;
+    p.skip = (uint32_t)L.skip;
+    void* args[] = {&p};
+    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.block), args, 0, cs);
+  }
+  if (e != cudaSuccess) return cuda_error(e, "bulk kernel launch");
+  return RNG_OK;
+}
+
+}  // namespace bcn

@@ -1,0 +1,53 @@
+// bcn_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bcn_rng.h"
+
+namespace bcn {
+
+// Output element kinds used as template arguments.
+enum { DT_F64 = 0, DT_F32 = 1, DT_U64 = 2 };
+// State advance: Modified Barrett (forward), Montgomery (backward), or the
+// roofline probe that writes a constant and computes nothing.
+enum { ST_BARRETT = 1, ST_MONT = 2, ST_CONST = 3 };
+enum { CV_INT = 1, CV_FP64 = 2 };
+enum { SK_TABLE = 1, SK_SQMUL = 2 };
+
+constexpr uint32_t kMaxDepth = 255;
+
+// A fully resolved bulk launch.
+struct BulkLaunch {
+  int dt, step, conv, layout, skip;
+  uint32_t depth, block, grid;
+  size_t smem_bytes;  // TILED only
+};
+
+// Element size in bytes of an rng_dtype.
+inline size_t dtype_size(int dt) { return dt == DT_F32 ? 4 : 8; }
+
+// Set the calling thread's error message and return `st`.
+rng_status set_error(rng_status st, const char* fmt, ...);
+rng_status cuda_error(cudaError_t e, const char* what);
+
+// Device properties cached per device.
+struct DeviceInfo {
+  int device;
+  int sms;
+  size_t smem_optin;  // max dynamic shared memory per block
+};
+rng_status device_info(DeviceInfo* out);
+
+// Fill in every zero field of `tune` for a bulk call of n elements of dt.
+rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* out,
+                        bool constant);
+
+// Launch a bulk generation (or constant fill) of elements [0, n) of the
+// call, whose element 0 is variate number i0 of the stream seeded with
+// `seed`.  `out` is aligned to the element size.
+rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t n,
+                       void* out, uint64_t const_bits, cudaStream_t cs);
+
+}  // namespace bcn

@@ -1,0 +1,205 @@
+// bcn_math.cuh -- constants and modular arithmetic of the alpha_{2,3} generator
+// for sm_103a.  Everything here is integer arithmetic on 64-bit words; the
+// only floating-point value is r3i, used by the FP64-pipe conversion variant.
+//
+// The generator (Beliakov et al., Algorithm BB with Eq. 2 and Eq. 3):
+//   seed a in [3^33+100, 2^53];  z_0 = 2^(a-3^33) * floor(3^33/2) mod 3^33;
+//   z_k = 2^53 z_(k-1) mod 3^33;  variate = z_k * 3^-33.
+// Variate i (0-based) of a stream therefore has the state
+//   z = 2^e * floor(3^33/2) mod 3^33,  e = (a - 3^33 + 53*(i+1)) mod P,
+// with P = 2*3^32 the period (Sec. 1).  Output is "step, then emit".
+#pragma once
+#include <cstdint>
+
+namespace bcn {
+
+typedef unsigned __int128 u128;
+
+// ---------------------------------------------------------------- constants
+constexpr uint64_t kM = 5559060566555523ULL;       // 3^33 (Eq. 3 modulus)
+constexpr uint64_t kH = kM / 2;                    // floor(3^33/2)   (Eq. 2)
+constexpr uint64_t kP = 2ULL * (kM / 3);           // 2*3^32, period  (Sec. 1)
+constexpr uint64_t kTwo53 = 1ULL << 53;
+constexpr uint64_t kMask53 = kTwo53 - 1;
+constexpr uint64_t kSeedMin = kM + 100;            // Algorithm BB, step 1
+constexpr uint64_t kSeedMax = kTwo53;              // Algorithm BB, step 1
+
+constexpr uint64_t pow3(int k) { return k == 0 ? 1 : 3 * pow3(k - 1); }
+static_assert(pow3(33) == kM, "m = 3^33");
+
+// Barrett's mu = floor(2^(2k)/m) with k = 53 (Sec. 2.1, Barrett and
+// Modified Barrett); Fig. 4 prints it as 0x33D9481681D79D.
+constexpr uint64_t kMu = (uint64_t)(((u128)1 << 106) / kM);
+static_assert(kMu == 0x33D9481681D79DULL, "mu as printed in Fig. 4");
+
+// r3i = RN(1/3^33) (Fig. 4).  Its significand as an integer: r3i = kMr*2^-105.
+// kMu + 1 = 2*kMr, so the Barrett product z*mu also yields the exact product
+// z*r3i*2^106 = z*mu + z that the integer conversion rounds.
+constexpr uint64_t kMr = 0x19ECA40B40EBCFULL;
+constexpr double kR3i = 0x1.9eca40b40ebcfp-53;
+static_assert(kMu + 1 == 2 * kMr, "mu + 1 = 2 * significand(r3i)");
+static_assert(kR3i == 1.0 / 5559060566555523.0, "r3i as printed in Fig. 4");
+static_assert(kR3i == (double)kMr * 0x1p-105, "r3i = kMr * 2^-105");
+
+// -m^-1 mod 2^53 for the Montgomery-style reduction with R = 2^53.
+constexpr uint64_t inv_mod_2_64(uint64_t x) {  // Newton: y <- y(2 - xy)
+  uint64_t y = x;  // correct to 3 bits for odd x
+  for (int i = 0; i < 6; ++i) y *= 2 - x * y;
+  return y;
+}
+constexpr uint64_t kNegMinv53 = (0 - inv_mod_2_64(kM)) & kMask53;
+static_assert(((kM * kNegMinv53 + 1) & kMask53) == 0, "m * (-m^-1) = -1 mod 2^53");
+
+// ------------------------------------------------------- host-side helpers
+constexpr uint64_t host_mulmod(uint64_t a, uint64_t b) {
+  return (uint64_t)(((u128)a * b) % kM);
+}
+constexpr uint64_t host_pow2(uint64_t e) {  // 2^e mod m, square-and-multiply
+  uint64_t r = 1, g = 2;
+  while (e) {
+    if (e & 1) r = host_mulmod(r, g);
+    g = host_mulmod(g, g);
+    e >>= 1;
+  }
+  return r;
+}
+static_assert(host_pow2(kP) == 1 && host_pow2(kP / 2) == kM - 1, "period");
+
+// Fixed-base exponent table: 2^e mod m for e < P < 2^56 is the product of
+// one entry per byte of e.  Row 0 also carries the floor(3^33/2) factor of
+// Eq. 2, so  z = T[0][e_0] * T[1][e_1] * ... * T[6][e_6]  mod m.
+// This is square-and-multiply with the squarings of the fixed base 2 done
+// once, at compile time.
+constexpr int kTabRows = 7;
+struct PowTable {
+  uint64_t t[kTabRows][256];
+};
+constexpr PowTable make_pow_table() {
+  PowTable T{};
+  uint64_t g = 2;  // 2^(256^k)
+  for (int k = 0; k < kTabRows; ++k) {
+    T.t[k][0] = (k == 0) ? kH : 1;
+    for (int d = 1; d < 256; ++d) T.t[k][d] = host_mulmod(T.t[k][d - 1], g);
+    for (int s = 0; s < 8; ++s) g = host_mulmod(g, g);
+  }
+  return T;
+}
+static_assert(make_pow_table().t[1][1] == host_pow2(256), "table row 1");
+static_assert(make_pow_table().t[0][5] == host_mulmod(32, kH), "table row 0");
+
+// Exponent of the state that precedes variate `index` of a stream whose
+// first call starts at absolute count i0:  (a - 3^33 + 53*i0) mod P.
+inline uint64_t host_exponent_base(uint64_t seed, uint64_t i0) {
+  return (uint64_t)(((u128)(seed - kM) + (u128)53 * (i0 % kP)) % kP);
+}
+
+#ifdef __CUDACC__
+// --------------------------------------------------------- device helpers
+// One copy per translation unit, constant-initialised when the module loads.
+static __device__ const PowTable kPowTable = make_pow_table();
+
+__device__ __forceinline__ uint64_t umulhi(uint64_t a, uint64_t b) {
+  return __umul64hi(a, b);
+}
+
+// x*y mod m for x, y < m (Barrett, Sec. 2.1.2, with k = 53: q1 = t >> 52,
+// q3 = (q1*mu) >> 54 lies in [Q-2, Q], so t - q3*m < 3m < 2^55 fits a word).
+__device__ __forceinline__ uint64_t mulmod(uint64_t x, uint64_t y) {
+  uint64_t lo = x * y, hi = umulhi(x, y);
+  uint64_t q1 = (hi << 12) | (lo >> 52);
+  uint64_t q3 = (umulhi(q1, kMu) << 10) | ((q1 * kMu) >> 54);
+  uint64_t r = lo - q3 * kM;
+  r = (r >= kM) ? r - kM : r;
+  r = (r >= kM) ? r - kM : r;
+  return r;
+}
+
+// (e0 + 53*x) mod P for e0 < P, any 64-bit x.
+__device__ __forceinline__ uint64_t exponent_add(uint64_t e0, uint64_t x) {
+  uint64_t e = e0 + 53ULL * (x % kP);  // < 2^59
+  return e % kP;
+}
+
+// 2^e * floor(3^33/2) mod m (Eq. 2) from the fixed-base table: 6 products.
+__device__ __forceinline__ uint64_t seed_state_table(uint64_t e) {
+  uint64_t z = __ldg(&kPowTable.t[0][e & 255]);
+#pragma unroll
+  for (int k = 1; k < kTabRows; ++k)
+    z = mulmod(z, __ldg(&kPowTable.t[k][(e >> (8 * k)) & 255]));
+  return z;
+}
+
+// The same value by plain right-to-left square-and-multiply (about 52
+// squarings and 26 products); kept as a selectable variant.
+__device__ __forceinline__ uint64_t seed_state_sqmul(uint64_t e) {
+  uint64_t r = kH, g = 2;
+  while (e) {
+    if (e & 1) r = mulmod(r, g);
+    g = mulmod(g, g);
+    e >>= 1;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------- steps
+// Modified Barrett (Sec. 2.1.3): q3 = floor(mu*z / 2^53) lies in {Q-1, Q}
+// for Q = floor(2^53 z / m); r = 2^53 - (q3*m mod 2^53); if r >= m, r -= m.
+// For m = 3^33 the 53-bit wrap of x - q3*m cannot happen: q3 = Q-1 needs
+// frac(2^53 z/m) < z*(2^106/m - mu)/2^53 < m/2^53 ~ 0.6172, while a wrap
+// needs frac(2^53 z/m) >= 2^53/m - 1 ~ 0.6203.  The step consumes the
+// product z*mu, which the caller forms once and shares with the conversion.
+__device__ __forceinline__ uint64_t barrett_from_product(uint64_t phi, uint64_t plo) {
+  uint64_t q3 = (phi << 11) | (plo >> 53);
+  uint64_t r = kTwo53 - ((q3 * kM) & kMask53);
+  return (r >= kM) ? r - kM : r;
+}
+
+// Montgomery-style inverse step with R = 2^53: 2^-53 z mod m, i.e. Eq. 3
+// run backwards.  u = -z/m mod 2^53 makes z + u*m divisible by 2^53, and
+// (z + u*m)/2^53 = floor(u*m/2^53) + 1 lies in [1, m-1] for 0 < z < m, so
+// no final subtraction is needed.
+__device__ __forceinline__ uint64_t montgomery_back(uint64_t z) {
+  uint64_t u = (z * kNegMinv53) & kMask53;
+  uint64_t hi = umulhi(u, kM), lo = u * kM;
+  return ((hi << 11) | (lo >> 53)) + 1;
+}
+
+// ---------------------------------------------------------- conversions
+// FP64 bits of RN(z * r3i) by integer arithmetic only.  p = z*mu + z =
+// z*r3i*2^106 exactly (< 2^106); the variate is p*2^-106 rounded to 53
+// significant bits, ties to even.  q = p >> 53 is in [1, 2^53); lz leading
+// zeros of q below bit 52 give the binary exponent -1-lz.
+__device__ __forceinline__ uint64_t f64_bits_from_p(uint64_t phi, uint64_t plo) {
+  uint64_t q = (phi << 11) | (plo >> 53);
+  uint64_t low = plo & kMask53;
+  int lz = __clzll((long long)q) - 11;                // 0 .. 52
+  uint64_t mant = (q << lz) | (low >> (53 - lz));      // 53 significant bits
+  uint64_t rest = low << (11 + lz);                    // dropped bits, top-aligned
+  const uint64_t half = 1ULL << 63;
+  uint64_t up = (rest > half) | ((rest == half) & (mant & 1));
+  return ((uint64_t)(1021 - lz) << 52) + mant + up;   // carry may bump exponent
+}
+
+// p = z*(mu+1) as a 128-bit (hi, lo) pair, from the Barrett product z*mu.
+__device__ __forceinline__ void p_from_barrett_product(uint64_t z, uint64_t phi,
+                                                       uint64_t plo, uint64_t& qhi,
+                                                       uint64_t& qlo) {
+  qlo = plo + z;
+  qhi = phi + (qlo < z ? 1ULL : 0ULL);
+}
+
+// FP64-pipe conversion: exact int->double, then one RN multiply (no FMA).
+__device__ __forceinline__ uint64_t f64_bits_fp64(uint64_t z) {
+  double v = __dmul_rn(__ull2double_rn(z), kR3i);
+  return (uint64_t)__double_as_longlong(v);
+}
+
+// FP32 variate: the FP64 variate truncated toward zero.  Every variate is
+// at least 2^-53, a normal float, so this is a shift and a re-bias of the
+// exponent (1023 - 127 = 896).
+__device__ __forceinline__ uint32_t f32_bits_from_f64_bits(uint64_t b) {
+  return (uint32_t)((b >> 29) - (896ULL << 23));
+}
+#endif  // __CUDACC__
+
+}  // namespace bcn

@@ -1,0 +1,227 @@
+"""Python binding of ``libbcn_rng.so`` (include/bcn_rng.h).
+
+Argument marshalling only: every variate is produced by the library's CUDA
+kernels.  torch provides device memory and the current CUDA stream.  There is
+no fallback: if the library is missing this module raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+M = 3 ** 33
+SEED_MIN = M + 100
+SEED_MAX = 2 ** 53
+PERIOD = 2 * 3 ** 32
+MAX_N = 1 << 46
+
+F64, F32, U64 = 0, 1, 2
+_DTYPES = {
+    "f64": (F64, torch.float64),
+    "f32": (F32, torch.float32),
+    "u64": (U64, torch.uint64),
+}
+STATUS = {0: "RNG_OK", 1: "RNG_EINVAL", 2: "RNG_ERANGE", 3: "RNG_ENOMEM",
+          4: "RNG_ECUDA", 5: "RNG_ETIMEOUT", 6: "RNG_EBUSY"}
+STEP = {"auto": 0, "barrett": 1, "montgomery": 2}
+CONV = {"auto": 0, "int": 1, "fp64": 2}
+LAYOUT = {"auto": 0, "tiled": 1, "direct": 2}
+SKIP = {"auto": 0, "table": 1, "sqmul": 2}
+
+
+class RNGError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in
+                ("step", "conv", "layout", "skip", "depth", "block", "grid", "reserved")]
+
+
+def make_tune(step="auto", conv="auto", layout="auto", skip="auto", depth=0, block=0,
+              grid=0) -> Tune:
+    """Launch tuning; zero / "auto" lets the library choose.  Results never
+    depend on it, only speed does."""
+    return Tune(STEP[step] if isinstance(step, str) else step,
+                CONV[conv] if isinstance(conv, str) else conv,
+                LAYOUT[layout] if isinstance(layout, str) else layout,
+                SKIP[skip] if isinstance(skip, str) else skip,
+                depth, block, grid, 0)
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(
+            f"the CUDA library {path} is not built; run "
+            "`python -m paper_1206_1187_gb300._build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    u64, u32, i32, vp, dbl = (ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                              ctypes.c_void_p, ctypes.c_double)
+    tp = ctypes.POINTER(Tune)
+    sig = {
+        "rng_create": ([u64, ctypes.POINTER(vp)], i32),
+        "rng_destroy": ([vp], i32),
+        "rng_set_cuda_stream": ([vp, vp], i32),
+        "rng_generate": ([vp, u64, i32, vp], i32),
+        "rng_generate_tuned": ([vp, u64, i32, vp, tp], i32),
+        "rng_skip": ([vp, u64], i32),
+        "rng_get_state": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i32),
+        "rng_set_state": ([vp, u64, u64], i32),
+        "rng_sync": ([vp], i32),
+        "rng_generate_at": ([u64, u64, u64, i32, vp, vp, tp], i32),
+        "rng_fill_constant": ([u64, i32, dbl, vp, vp, tp], i32),
+        "rng_last_error": ([], ctypes.c_char_p),
+        "rng_resolve_tune": ([u64, i32, tp, tp], i32),
+        "rng_version": ([], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise RNGError(rc, lib.rng_last_error().decode(errors="replace"))
+
+
+def _dtype(dtype: str):
+    try:
+        return _DTYPES[dtype]
+    except KeyError:
+        raise ValueError(f"dtype must be one of {sorted(_DTYPES)}") from None
+
+
+def _out_tensor(n: int, dtype: str, out):
+    code, tdt = _dtype(dtype)
+    if out is None:
+        out = torch.empty(n, dtype=tdt, device="cuda")
+    else:
+        if out.dtype != tdt or not out.is_cuda or not out.is_contiguous() or out.numel() < n:
+            raise ValueError(f"out must be a contiguous CUDA {tdt} tensor with >= {n} elements")
+    return code, out
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _tune_ptr(tune):
+    if tune is None:
+        return None
+    if isinstance(tune, dict):
+        tune = make_tune(**tune)
+    return ctypes.byref(tune)
+
+
+class Stream:
+    """One generator stream: a seed (start index, Algorithm BB step 1) and a
+    count of variates already produced.  Launches go to torch's current CUDA
+    stream at each call unless `cuda_stream` is given."""
+
+    def __init__(self, start_index: int):
+        h = ctypes.c_void_p()
+        _check(lib.rng_create(start_index, ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if self._h:
+            lib.rng_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind(self, stream) -> None:
+        _check(lib.rng_set_cuda_stream(self._h, ctypes.c_void_p(_stream_handle(stream))))
+
+    def generate(self, n: int, dtype: str = "f64", out=None, tune=None, stream=None):
+        code, out = _out_tensor(n, dtype, out)
+        self._bind(stream)
+        _check(lib.rng_generate_tuned(self._h, n, code, ctypes.c_void_p(out.data_ptr()),
+                                      _tune_ptr(tune)))
+        return out
+
+    def generate_into_ptr(self, n: int, dtype: str, ptr: int, tune=None, stream=None) -> None:
+        code, _ = _dtype(dtype)
+        self._bind(stream)
+        _check(lib.rng_generate_tuned(self._h, n, code, ctypes.c_void_p(ptr), _tune_ptr(tune)))
+
+    def skip(self, k: int) -> None:
+        _check(lib.rng_skip(self._h, k))
+
+    @property
+    def state(self) -> tuple[int, int]:
+        a, c = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib.rng_get_state(self._h, ctypes.byref(a), ctypes.byref(c)))
+        return a.value, c.value
+
+    def set_state(self, start_index: int, count: int) -> None:
+        _check(lib.rng_set_state(self._h, start_index, count))
+
+    def sync(self) -> None:
+        _check(lib.rng_sync(self._h))
+
+
+def generate_at(start_index: int, offset: int, n: int, dtype: str = "f64", out=None,
+                tune=None, stream=None):
+    """Variates offset .. offset+n-1 of the sequence seeded with start_index."""
+    code, out = _out_tensor(n, dtype, out)
+    _check(lib.rng_generate_at(start_index, offset, n, code, ctypes.c_void_p(out.data_ptr()),
+                               ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
+    return out
+
+
+def generate_at_ptr(start_index: int, offset: int, n: int, dtype: str, ptr: int, tune=None,
+                    stream=None) -> None:
+    code, _ = _dtype(dtype)
+    _check(lib.rng_generate_at(start_index, offset, n, code, ctypes.c_void_p(ptr),
+                               ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
+
+
+def fill_constant(n: int, dtype: str = "f64", value: float = 0.5, out=None, tune=None,
+                  stream=None):
+    """The write-ceiling probe: n copies of `value` through the tiled store path."""
+    code, out = _out_tensor(n, dtype, out)
+    _check(lib.rng_fill_constant(n, code, value, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
+    return out
+
+
+def resolve_tune(n: int, dtype: str = "f64", tune=None) -> dict:
+    code, _ = _dtype(dtype)
+    res = Tune()
+    _check(lib.rng_resolve_tune(n, code, _tune_ptr(tune), ctypes.byref(res)))
+    inv = lambda d, v: next((k for k, x in d.items() if x == v), v)
+    return {"step": inv(STEP, res.step), "conv": inv(CONV, res.conv),
+            "layout": inv(LAYOUT, res.layout), "skip": inv(SKIP, res.skip),
+            "depth": res.depth, "block": res.block, "grid": res.grid}
+
+
+def version() -> int:
+    return lib.rng_version()
+
+
+@dataclass
+class _Info:
+    path: str = _build.LIB
+
+
+library_info = _Info()

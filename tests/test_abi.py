@@ -1,0 +1,92 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares;
+host-side argument checks that need no GPU.  (No compute calls here.)"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        for m in re.finditer(r"\b([a-z_][a-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            # a declaration: the name follows a type, not a keyword or macro
+            before = text[:m.start()].rstrip()
+            if name.startswith("rng_") and (before.endswith("*") or re.search(r"[\w]$", before)):
+                names.add(name)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1206_1187_gb300 import _build
+    _build.build()
+    from paper_1206_1187_gb300 import rng
+    return rng
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("rng_create", "rng_generate", "rng_skip", "rng_destroy",
+                     "rng_get_state", "rng_set_state", "rng_generate_at", "rng_sync",
+                     "rng_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(lib.library_info.path)
+    missing = [n for n in sorted(_declared_functions()) if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_seed_range_is_checked_on_the_host(lib):
+    with pytest.raises(lib.RNGError) as e:
+        lib.Stream(3 ** 33 + 99)
+    assert e.value.status == 2
+    with pytest.raises(lib.RNGError):
+        lib.Stream(2 ** 53 + 1)
+    s = lib.Stream(3 ** 33 + 100)
+    assert s.state == (3 ** 33 + 100, 0)
+    s2 = lib.Stream(2 ** 53)
+    assert s2.state == (2 ** 53, 0)
+
+
+def test_state_skip_and_checkpoint(lib):
+    s = lib.Stream(3 ** 33 + 12345)
+    s.skip(1000)
+    s.skip(5)
+    assert s.state == (3 ** 33 + 12345, 1005)
+    s.set_state(8 * 10 ** 15, 77)
+    assert s.state == (8 * 10 ** 15, 77)
+    with pytest.raises(lib.RNGError) as e:
+        s.set_state(5, 0)
+    assert e.value.status == 2
+    s.set_state(8 * 10 ** 15, 2 ** 64 - 10)
+    with pytest.raises(lib.RNGError) as e:
+        s.skip(11)
+    assert e.value.status == 2
+    assert s.state == (8 * 10 ** 15, 2 ** 64 - 10)
+
+
+def test_empty_and_bad_pointer_calls_fail_before_any_launch(lib):
+    raw = lib.lib
+    s = lib.Stream(3 ** 33 + 100)
+    # n = 0 is a no-op and touches no device
+    assert raw.rng_generate(s._h, 0, 0, None) == 0
+    assert s.state[1] == 0
+    # NULL output, misaligned output, bad dtype, oversize n: all rejected
+    assert raw.rng_generate(s._h, 10, 0, None) == 1
+    assert raw.rng_generate(s._h, 10, 0, ctypes.c_void_p(4)) == 1
+    assert raw.rng_generate(s._h, 10, 1, ctypes.c_void_p(2)) == 1
+    assert raw.rng_generate(s._h, 10, 7, ctypes.c_void_p(4096)) == 1
+    assert raw.rng_generate(s._h, (1 << 46) + 1, 0, ctypes.c_void_p(4096)) == 2
+    assert s.state[1] == 0
+    assert b"aligned" in raw.rng_last_error() or raw.rng_last_error()

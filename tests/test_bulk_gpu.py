@@ -1,0 +1,185 @@
+"""GPU parity of the bulk generator against the CPU oracle (bit-exact).
+
+Integer states must match exactly; FP64 variates are compared bit for bit
+(one round-to-nearest multiply by r3i, no FMA); FP32 variates likewise (the
+FP64 variate truncated).  Every launch layout, reduction, conversion,
+skip-ahead method and tile shape must give the same bytes.
+"""
+import itertools
+import os
+import random
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+M = 3 ** 33
+P = 2 * 3 ** 32
+NPDT = {"f64": np.int64, "f32": np.int32, "u64": np.int64}
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1206_1187_gb300 import rng  # raises if the library is not built
+    return rng
+
+
+def dev_bits(t):
+    import torch
+    iv = torch.int64 if t.element_size() == 8 else torch.int32
+    return t.view(iv).cpu().numpy()
+
+
+def host_bits(a: np.ndarray):
+    return a.view(NPDT["f64"] if a.itemsize == 8 else NPDT["f32"])
+
+
+def assert_same(dev, want, what=""):
+    got = dev_bits(dev)
+    exp = host_bits(want)
+    if not np.array_equal(got, exp):
+        bad = np.nonzero(got != exp)[0]
+        raise AssertionError(f"{what}: {bad.size} mismatches, first at {bad[:5]}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "u64"])
+def test_single_stream_1e6(R, oracle_mod, dtype):
+    """a = 3^33+100, n = 10^6 with the automatic launch choice."""
+    a, n = M + 100, 10 ** 6
+    s = R.Stream(a)
+    out = s.generate(n, dtype)
+    s.sync()
+    assert_same(out, oracle_mod.generate(a, 0, n, dtype), dtype)
+    assert s.state == (a, n)
+
+
+VARIANTS = list(itertools.product(["barrett", "montgomery"], ["int", "fp64"],
+                                  ["tiled", "direct"], ["table", "sqmul"]))
+
+
+@pytest.mark.parametrize("step,conv,layout,skip", VARIANTS)
+def test_every_variant_matches_the_oracle(R, oracle_mod, step, conv, layout, skip):
+    rnd = random.Random(VARIANTS.index((step, conv, layout, skip)))
+    a = rnd.randint(M + 100, 2 ** 53)
+    off = rnd.randint(0, 2 ** 40)
+    n = 100003  # several tiles and a ragged tail
+    t = R.make_tune(step=step, conv=conv, layout=layout, skip=skip)
+    for dtype in ("f64", "f32", "u64"):
+        out = R.generate_at(a, off, n, dtype, tune=t)
+        assert_same(out, oracle_mod.generate(a, off, n, dtype), f"{step}/{conv}/{layout}/{dtype}")
+
+
+def test_tile_shape_and_grid_never_change_the_output(R):
+    import torch
+    a, off, n = M + 4242, 12345, 3 * 10 ** 5 + 17
+    ref = R.generate_at(a, off, n, "f64", tune=R.make_tune(layout="direct"))
+    for depth, block, grid, step in [(1, 32, 1, "barrett"), (3, 64, 7, "montgomery"),
+                                     (15, 256, 0, "barrett"), (31, 1024, 3, "barrett"),
+                                     (63, 128, 152, "montgomery"), (127, 64, 0, "barrett"),
+                                     (255, 32, 5, "montgomery"), (9, 96, 1000, "barrett")]:
+        t = R.make_tune(step=step, layout="tiled", depth=depth, block=block, grid=grid)
+        out = R.generate_at(a, off, n, "f64", tune=t)
+        assert torch.equal(out.view(torch.int64), ref.view(torch.int64)), (depth, block, grid)
+    for block, grid in [(1, 1), (7, 3), (1024, 1), (33, 17)]:
+        t = R.make_tune(layout="direct", block=block, grid=grid)
+        out = R.generate_at(a, off, n, "f64", tune=t)
+        assert torch.equal(out.view(torch.int64), ref.view(torch.int64)), (block, grid)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_small_misaligned_outputs_and_canaries(R, oracle_mod, dtype):
+    """n = 1..97 at every element offset inside a 16-byte line; the bytes
+    around the output must stay untouched (bounds check by canary)."""
+    import torch
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    esz = 8 if dtype == "f64" else 4
+    a = M + 99991
+    sentinel = -7.25
+    for n in list(range(1, 98)) + [1000, 4097, 65537]:
+        for shift in range(16 // esz):
+            buf = torch.full((n + 64,), sentinel, dtype=tdt, device="cuda")
+            view = buf[8 + shift: 8 + shift + n]
+            R.generate_at(a, n, n, dtype, out=view)
+            host = buf.cpu().numpy()
+            assert np.all(host[: 8 + shift] == sentinel)
+            assert np.all(host[8 + shift + n:] == sentinel)
+            want = oracle_mod.generate(a, n, n, dtype)
+            assert np.array_equal(host_bits(host[8 + shift: 8 + shift + n].copy()), host_bits(want)), (n, shift)
+
+
+def test_stream_calls_concatenate(R, oracle_mod):
+    import torch
+    a = M + 31337
+    s = R.Stream(a)
+    parts = [s.generate(k, "f64") for k in (1, 2, 1000, 33333, 7)]
+    s.skip(500)
+    parts.append(s.generate(4096, "f64"))
+    got = torch.cat(parts)
+    want = np.concatenate([oracle_mod.generate(a, 0, 1 + 2 + 1000 + 33333 + 7, "f64"),
+                           oracle_mod.generate(a, 1 + 2 + 1000 + 33333 + 7 + 500, 4096, "f64")])
+    assert_same(got, want, "chunks")
+    # checkpoint and resume
+    seed, count = s.state
+    cont = s.generate(1000, "f64")
+    s2 = R.Stream(M + 100)
+    s2.set_state(seed, count)
+    assert torch.equal(s2.generate(1000, "f64").view(torch.int64), cont.view(torch.int64))
+
+
+def test_offsets_across_the_period_and_far_out(R, oracle_mod):
+    a = 2 ** 53
+    for off in (P - 50, P, 2 * P - 7, 2 ** 60 + 11, 2 ** 64 - 5000):
+        n = 4000
+        for dtype in ("u64", "f64"):
+            out = R.generate_at(a, off, n, dtype)
+            assert_same(out, oracle_mod.generate(a, off, n, dtype), f"off={off}")
+
+
+def test_seed_bounds_on_device(R, oracle_mod):
+    for a in (M + 100, 2 ** 53):
+        out = R.generate_at(a, 0, 5000, "u64")
+        assert_same(out, oracle_mod.generate(a, 0, 5000, "u64"), f"a={a}")
+    with pytest.raises(R.RNGError):
+        R.generate_at(M + 99, 0, 10, "f64")
+
+
+def test_bad_tuning_is_rejected(R):
+    for kw in ({"depth": 16, "layout": "tiled"}, {"block": 48, "layout": "tiled"},
+               {"block": 2048}, {"step": 9}, {"conv": 5}, {"skip": 4}):
+        with pytest.raises(R.RNGError) as e:
+            R.generate_at(M + 100, 0, 1000, "f64", tune=R.make_tune(**kw))
+        assert e.value.status == 1
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_fill_constant_writes_every_element(R, dtype):
+    import torch
+    for n in (1, 31, 4097, 10 ** 6 + 3):
+        out = R.fill_constant(n, dtype, 0.375)
+        assert bool(torch.all(out == 0.375))
+
+
+@pytest.mark.slow
+def test_two_gib_single_stream_is_thread_count_invariant(R, oracle_mod):
+    """a = 3^33+12345, n = 2^28 FP64 (2 GiB): byte-identical for 1, 2^10 and
+    2^16 threads of the per-thread split, for the tiled kernel the library
+    picks, and to the oracle."""
+    import torch
+    a, n = M + 12345, 1 << 28
+    tiled = R.generate_at(a, 0, n, "f64")
+    want = oracle_mod.generate_mt(a, 0, n, "f64", threads=os.cpu_count() or 1)
+    assert_same(tiled, want, "tiled 2^28")
+    del want
+    tb = tiled.view(torch.int64)
+    for block, grid in [(256, 4), (256, 256), (1, 1)]:  # 2^10, 2^16, 1 thread
+        out = R.generate_at(a, 0, n, "f64", tune=R.make_tune(layout="direct", block=block,
+                                                             grid=grid))
+        assert torch.equal(out.view(torch.int64), tb), (block, grid)
+        del out
+    for step, conv in [("montgomery", "int"), ("barrett", "fp64")]:
+        out = R.generate_at(a, 0, n, "f64", tune=R.make_tune(step=step, conv=conv))
+        assert torch.equal(out.view(torch.int64), tb), (step, conv)
+        del out
