@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="use the library's built-in launch choice")
     return p.parse_args()
 
 
@@ -248,6 +250,10 @@ def run_ours(args):
     n = args.n
     offset = rank * n
     dev = torch.device("cuda", local)
+    tuned = None
+    if not args.no_autotune:  # measured choice of step, conversion and tile shape
+        from paper_1206_1187_gb300 import autotune
+        tuned = autotune.tune_bulk("f64", n=min(n, 1 << 26))
     out = torch.empty(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     ptr = out.data_ptr()
@@ -356,6 +362,11 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
+        if tuned is not None:
+            ranked = sorted((t for t in tuned["table"] if t[1] > 0), key=lambda t: t[1])
+            line["autotune"] = {"candidates": len(tuned["table"]), "n": tuned["n"],
+                                "best": tuned["best"],
+                                "top3_ms": [[c, round(t, 5)] for c, t in ranked[:3]]}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)

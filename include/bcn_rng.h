@@ -61,9 +61,11 @@ typedef enum {
 
 /* The reduction that advances the state (Sec. 2.1). */
 typedef enum {
-  RNG_STEP_AUTO = 0,       /* the measured-fastest variant                  */
-  RNG_STEP_BARRETT = 1,    /* Modified Barrett, Sec. 2.1.3, forward         */
-  RNG_STEP_MONTGOMERY = 2  /* Montgomery-style, R = 2^53, blocks run back   */
+  RNG_STEP_AUTO = 0,           /* the measured-fastest variant                */
+  RNG_STEP_BARRETT = 1,        /* Modified Barrett, Sec. 2.1.3, forward       */
+  RNG_STEP_MONTGOMERY = 2,     /* Montgomery-style, R = 2^53, blocks run back */
+  RNG_STEP_BARRETT_SHARED = 3  /* Barrett quotient estimate taken from the
+                                  output-conversion product z*(mu+1), forward */
 } rng_step;
 
 /* How a state becomes an FP64 variate (the RN multiply of Algorithm BB). */
@@ -155,6 +157,25 @@ rng_status rng_generate_at(uint64_t start_index, uint64_t offset, uint64_t n,
  * write ceiling the generator is measured against. */
 rng_status rng_fill_constant(uint64_t n, rng_dtype dt, double value, void *out,
                              void *cuda_stream, const rng_tune *tune);
+
+/* -------------------------------------------------------------- autotune */
+
+/* Time each of the `ncand` candidate tunings of a bulk call (n elements of
+ * dt written to the caller-owned device buffer `out`, which is overwritten)
+ * on `cuda_stream`: one warm-up and `reps` timed launches each, CUDA events.
+ * The fastest valid candidate, fully resolved, goes to *best; ms[i]
+ * (nullable) receives candidate i's mean milliseconds per launch, or -1 if
+ * the candidate is invalid (for example too much shared memory).  Blocks
+ * until the timings are done.  The selection-by-measurement the paper makes
+ * over threads per block (Sec. 3.2), applied to this library's parameters. */
+rng_status rng_autotune_bulk(uint64_t n, rng_dtype dt, void *out, void *cuda_stream,
+                             const rng_tune *candidates, uint32_t ncand, uint32_t reps,
+                             rng_tune *best, float *ms);
+
+/* Install `t` as the choice for the zero fields of later calls of dtype dt
+ * (its grid is ignored: the grid follows n).  NULL restores the built-in
+ * choice.  Process-wide; results never change, only speed. */
+rng_status rng_set_auto_tune(rng_dtype dt, const rng_tune *t);
 
 /* ------------------------------------------------------------- utilities */
 

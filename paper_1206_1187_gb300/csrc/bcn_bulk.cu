@@ -61,7 +61,22 @@ template <int DT, int STEP, int CONV>
 struct Gen {
   uint64_t z;
   __device__ __forceinline__ typename Word<DT>::type next() {
-    if constexpr (STEP == ST_BARRETT) {
+    if constexpr (STEP == ST_SHARED) {
+      if constexpr (DT == DT_U64) {
+        const uint64_t w = z;
+        z = shared_advance(z);
+        return w;
+      } else if constexpr (CONV == CV_FP64) {
+        const uint64_t bits = f64_bits_fp64(z);
+        z = shared_advance(z);
+        if constexpr (DT == DT_F64) return bits;
+        else return f32_bits_from_f64_bits(bits);
+      } else {
+        const uint64_t bits = shared_step_f64(z);
+        if constexpr (DT == DT_F64) return bits;
+        else return f32_bits_from_f64_bits(bits);
+      }
+    } else if constexpr (STEP == ST_BARRETT) {
       uint64_t plo = z * kMu, phi = umulhi(z, kMu);
       auto w = to_word<DT, CONV>(z, phi, plo);
       z = barrett_from_product(phi, plo);
@@ -96,7 +111,7 @@ __device__ void run_direct(typename Word<DT>::type* __restrict__ out, uint64_t e
   if (a >= b) return;
   if constexpr (STEP == ST_CONST) {
     for (uint64_t i = a; i < b; ++i) out[i] = (W)cbits;
-  } else if constexpr (STEP == ST_BARRETT) {
+  } else if constexpr (STEP != ST_MONT) {
     Gen<DT, STEP, CONV> g{state_of(ebase, a, skip)};
     for (uint64_t i = a; i < b; ++i) out[i] = g.next();
   } else {
@@ -166,7 +181,7 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
     // this lane's first element in the warp's first tile
     const uint64_t first = p.head + t0 * tile_elems + (uint64_t)lane * c;
     Gen<DT, STEP, CONV> g{0};
-    if constexpr (STEP == ST_BARRETT) g.z = state_of(p.ebase, first, p.skip);
+    if constexpr (STEP == ST_BARRETT || STEP == ST_SHARED) g.z = state_of(p.ebase, first, p.skip);
     if constexpr (STEP == ST_MONT) g.z = state_of(p.ebase, first + c - 1, p.skip);
     for (uint64_t t = t0; t < t1; ++t) {
       const uint32_t k = (uint32_t)(t - t0);
@@ -178,7 +193,7 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
       W* const mine = buf + lane * c;
       if constexpr (STEP == ST_CONST) {
         for (uint32_t i = 0; i < c; ++i) mine[i] = (W)p.cbits;
-      } else if constexpr (STEP == ST_BARRETT) {
+      } else if constexpr (STEP != ST_MONT) {
 #pragma unroll 4
         for (uint32_t i = 0; i < c; ++i) mine[i] = g.next();
       } else {
@@ -235,6 +250,7 @@ static const void* pick_st(int layout, int st, int cv) {
   switch (st) {
     case ST_BARRETT: return pick_cv<DT, ST_BARRETT>(layout, cv);
     case ST_MONT: return pick_cv<DT, ST_MONT>(layout, cv);
+    case ST_SHARED: return pick_cv<DT, ST_SHARED>(layout, cv);
     default: return nullptr;
   }
 }
@@ -288,15 +304,27 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
                         bool constant) {
   rng_tune t = {};
   if (tune) t = *tune;
+  if (!constant) {  // zero fields take the installed (measured) defaults
+    const rng_tune d = auto_defaults(dt);
+    const bool same_layout = !t.layout || !d.layout || t.layout == d.layout;
+    if (!t.step) t.step = d.step;
+    if (!t.conv) t.conv = d.conv;
+    if (!t.skip) t.skip = d.skip;
+    if (same_layout) {
+      if (!t.layout) t.layout = d.layout;
+      if (!t.depth) t.depth = d.depth;
+      if (!t.block) t.block = d.block;
+    }
+  }
   BulkLaunch L = {};
   L.dt = dt;
   L.layout = t.layout ? (int)t.layout : RNG_LAYOUT_TILED;
-  L.step = constant ? ST_CONST : (t.step ? (int)t.step : ST_BARRETT);
+  L.step = constant ? ST_CONST : (t.step ? (int)t.step : ST_SHARED);
   L.conv = t.conv ? (int)t.conv : CV_INT;
   L.skip = t.skip ? (int)t.skip : SK_TABLE;
   if (L.layout != RNG_LAYOUT_TILED && L.layout != RNG_LAYOUT_DIRECT)
     return set_error(RNG_EINVAL, "tune.layout %u is not a layout", t.layout);
-  if (!constant && L.step != ST_BARRETT && L.step != ST_MONT)
+  if (!constant && L.step != ST_BARRETT && L.step != ST_MONT && L.step != ST_SHARED)
     return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
   if (L.conv != CV_INT && L.conv != CV_FP64)
     return set_error(RNG_EINVAL, "tune.conv %u is not a conversion", t.conv);

@@ -10,9 +10,10 @@ namespace bcn {
 
 // Output element kinds used as template arguments.
 enum { DT_F64 = 0, DT_F32 = 1, DT_U64 = 2 };
-// State advance: Modified Barrett (forward), Montgomery (backward), or the
-// roofline probe that writes a constant and computes nothing.
-enum { ST_BARRETT = 1, ST_MONT = 2, ST_CONST = 3 };
+// State advance: Modified Barrett (forward), Montgomery (backward), Barrett
+// with the quotient shared with the conversion (forward), or the roofline
+// probe that writes a constant and computes nothing.
+enum { ST_BARRETT = 1, ST_MONT = 2, ST_SHARED = 3, ST_CONST = 9 };
 enum { CV_INT = 1, CV_FP64 = 2 };
 enum { SK_TABLE = 1, SK_SQMUL = 2 };
 
@@ -39,6 +40,9 @@ struct DeviceInfo {
   size_t smem_optin;  // max dynamic shared memory per block
 };
 rng_status device_info(DeviceInfo* out);
+
+// The tuning installed by rng_set_auto_tune for dtype dt (zeros if none).
+rng_tune auto_defaults(int dt);
 
 // Fill in every zero field of `tune` for a bulk call of n elements of dt.
 rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* out,

@@ -41,6 +41,12 @@ static_assert(kMu + 1 == 2 * kMr, "mu + 1 = 2 * significand(r3i)");
 static_assert(kR3i == 1.0 / 5559060566555523.0, "r3i as printed in Fig. 4");
 static_assert(kR3i == (double)kMr * 0x1p-105, "r3i = kMr * 2^-105");
 
+// K = mu + 1 = 2*kMr: z*K = z*r3i*2^106 exactly, and floor(z*K / 2^53) is a
+// Barrett quotient estimate for 2^53 z / m (see shared_step_f64).
+constexpr uint64_t kK = kMu + 1;
+constexpr uint32_t kK0 = (uint32_t)kK, kK1 = (uint32_t)(kK >> 32);
+constexpr uint32_t kM0 = (uint32_t)kM, kM1 = (uint32_t)(kM >> 32);
+
 // -m^-1 mod 2^53 for the Montgomery-style reduction with R = 2^53.
 constexpr uint64_t inv_mod_2_64(uint64_t x) {  // Newton: y <- y(2 - xy)
   uint64_t y = x;  // correct to 3 bits for odd x
@@ -186,6 +192,75 @@ __device__ __forceinline__ void p_from_barrett_product(uint64_t z, uint64_t phi,
                                                        uint64_t& qlo) {
   qlo = plo + z;
   qhi = phi + (qlo < z ? 1ULL : 0ULL);
+}
+
+// ------------------------------------------------- shared-quotient step
+// One Barrett-style step of Eq. 3 and the FP64 variate of the current state
+// from a single 106-bit product p = z*K (K = mu + 1 = 2*significand(r3i)):
+//
+//  * Reduction.  q = floor(p / 2^53) = floor(z*(mu+1)/2^53) lies in {Q, Q+1}
+//    for Q = floor(2^53 z / m): z*(mu+1)/2^53 exceeds 2^53 z/m (mu+1 > 2^106/m)
+//    by less than z/2^53 < 1.  So r = 2^53 z - q*m lies in (-m, m), is exact in
+//    64-bit two's complement, and one conditional "+ m" finishes the step --
+//    Barrett's quotient estimate (Sec. 2.1.2) with the output scale as the
+//    precomputed reciprocal.
+//  * Conversion.  The variate RN(z*r3i) = RN(p * 2^-106).  With lz the number
+//    of leading zeros of q below bit 52, the significand is p >> (53-lz) and
+//    the first dropped bit (the guard bit) decides the rounding: p = 2*z*M_r
+//    with M_r odd, so an exact tie would need v2(z) >= bitlen(z) - 2, i.e.
+//    z = 2^k or 3*2^k, and none of those is a tie.  Round-to-nearest-even is
+//    therefore "add the guard bit": bits = (G + (E << 53) + 1) >> 1 with
+//    G = p >> (52-lz) (significand and guard) and E = 1021 - lz, where a
+//    rounding carry moves into the exponent field by itself.
+//  The fast path needs the top word of q to be non-zero (variate >= 2^-21);
+//  the rest (probability about 2^-21) takes the general conversion.
+// Everything is 32-bit words: 4 wide multiply-adds form p, 3 multiplies give
+// q*m mod 2^64, funnel shifts do the normalisation.
+__device__ __forceinline__ uint64_t shared_step_f64(uint64_t& z) {
+  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
+  const uint64_t t0 = (uint64_t)z0 * kK0;
+  uint64_t t1 = (uint64_t)z0 * kK1 + (t0 >> 32);
+  t1 = (uint64_t)z1 * kK0 + t1;
+  const uint64_t t2 = (uint64_t)z1 * kK1 + (t1 >> 32);
+  const uint32_t w1 = (uint32_t)t1, w2 = (uint32_t)t2, w3 = (uint32_t)(t2 >> 32);
+  const uint32_t q0 = __funnelshift_r(w1, w2, 21);
+  const uint32_t q1 = __funnelshift_r(w2, w3, 21);
+  // next state: 2^53 z - q*m, then + m if negative
+  const uint64_t qm = (uint64_t)q0 * kM0;
+  const uint32_t qm_hi = (uint32_t)(qm >> 32) + q0 * kM1 + q1 * kM0;
+  uint64_t r = ((uint64_t)(z0 << 21) << 32) - (((uint64_t)qm_hi << 32) | (uint32_t)qm);
+  if ((int64_t)r < 0) r += kM;
+  // conversion of the current state
+  uint64_t bits;
+  if (__builtin_expect(q1 != 0, 1)) {
+    const uint32_t c = __clz((int)q1);        // 11 .. 31, lz = c - 11
+    const uint32_t s = c - 10;                // lz + 1
+    const uint32_t lh = w1 << 11;             // low bits of p below q, top-aligned
+    const uint32_t g_hi = __funnelshift_l(q0, q1, s);
+    const uint32_t g_lo = __funnelshift_l(lh, q0, s);
+    const uint64_t x = (((uint64_t)g_hi << 32) | g_lo) + (((uint64_t)(1032 - c) << 53) | 1ULL);
+    bits = x >> 1;
+  } else {
+    bits = f64_bits_from_p(t2, (t1 << 32) | (uint32_t)t0);
+  }
+  z = r;
+  return bits;
+}
+
+// The state advance of shared_step_f64 alone (raw-state output).
+__device__ __forceinline__ uint64_t shared_advance(uint64_t z) {
+  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
+  const uint64_t t0 = (uint64_t)z0 * kK0;
+  uint64_t t1 = (uint64_t)z0 * kK1 + (t0 >> 32);
+  t1 = (uint64_t)z1 * kK0 + t1;
+  const uint64_t t2 = (uint64_t)z1 * kK1 + (t1 >> 32);
+  const uint32_t q0 = __funnelshift_r((uint32_t)t1, (uint32_t)t2, 21);
+  const uint32_t q1 = __funnelshift_r((uint32_t)t2, (uint32_t)(t2 >> 32), 21);
+  const uint64_t qm = (uint64_t)q0 * kM0;
+  const uint32_t qm_hi = (uint32_t)(qm >> 32) + q0 * kM1 + q1 * kM0;
+  uint64_t r = ((uint64_t)(z0 << 21) << 32) - (((uint64_t)qm_hi << 32) | (uint32_t)qm);
+  if ((int64_t)r < 0) r += kM;
+  return r;
 }
 
 // FP64-pipe conversion: exact int->double, then one RN multiply (no FMA).

@@ -28,7 +28,7 @@ _DTYPES = {
 }
 STATUS = {0: "RNG_OK", 1: "RNG_EINVAL", 2: "RNG_ERANGE", 3: "RNG_ENOMEM",
           4: "RNG_ECUDA", 5: "RNG_ETIMEOUT", 6: "RNG_EBUSY"}
-STEP = {"auto": 0, "barrett": 1, "montgomery": 2}
+STEP = {"auto": 0, "barrett": 1, "montgomery": 2, "shared": 3}
 CONV = {"auto": 0, "int": 1, "fp64": 2}
 LAYOUT = {"auto": 0, "tiled": 1, "direct": 2}
 SKIP = {"auto": 0, "table": 1, "sqmul": 2}
@@ -81,6 +81,9 @@ def _load() -> ctypes.CDLL:
         "rng_last_error": ([], ctypes.c_char_p),
         "rng_resolve_tune": ([u64, i32, tp, tp], i32),
         "rng_version": ([], i32),
+        "rng_autotune_bulk": ([u64, i32, vp, vp, tp, u32, u32, tp,
+                               ctypes.POINTER(ctypes.c_float)], i32),
+        "rng_set_auto_tune": ([i32, tp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -213,6 +216,32 @@ def resolve_tune(n: int, dtype: str = "f64", tune=None) -> dict:
     return {"step": inv(STEP, res.step), "conv": inv(CONV, res.conv),
             "layout": inv(LAYOUT, res.layout), "skip": inv(SKIP, res.skip),
             "depth": res.depth, "block": res.block, "grid": res.grid}
+
+
+def autotune_bulk(n: int, dtype: str, candidates, reps: int = 5, out=None, stream=None):
+    """Time candidate tunings (list of Tune or dicts); returns (best, ms list)."""
+    code, out = _out_tensor(n, dtype, out)
+    cands = [c if isinstance(c, Tune) else make_tune(**c) for c in candidates]
+    arr = (Tune * len(cands))(*cands)
+    ms = (ctypes.c_float * len(cands))()
+    best = Tune()
+    _check(lib.rng_autotune_bulk(n, code, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(_stream_handle(stream)), arr, len(cands),
+                                 reps, ctypes.byref(best), ms))
+    return best, [float(x) for x in ms]
+
+
+def set_auto_tune(dtype: str, tune) -> None:
+    """Install `tune` as the default for the zero fields of later calls."""
+    code, _ = _dtype(dtype)
+    _check(lib.rng_set_auto_tune(code, _tune_ptr(tune)))
+
+
+def tune_dict(t: Tune) -> dict:
+    inv = lambda d, v: next((k for k, x in d.items() if x == v), v)
+    return {"step": inv(STEP, t.step), "conv": inv(CONV, t.conv),
+            "layout": inv(LAYOUT, t.layout), "skip": inv(SKIP, t.skip),
+            "depth": t.depth, "block": t.block, "grid": t.grid}
 
 
 def version() -> int:

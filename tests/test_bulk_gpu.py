@@ -56,7 +56,7 @@ def test_single_stream_1e6(R, oracle_mod, dtype):
     assert s.state == (a, n)
 
 
-VARIANTS = list(itertools.product(["barrett", "montgomery"], ["int", "fp64"],
+VARIANTS = list(itertools.product(["barrett", "montgomery", "shared"], ["int", "fp64"],
                                   ["tiled", "direct"], ["table", "sqmul"]))
 
 
@@ -77,9 +77,10 @@ def test_tile_shape_and_grid_never_change_the_output(R):
     a, off, n = M + 4242, 12345, 3 * 10 ** 5 + 17
     ref = R.generate_at(a, off, n, "f64", tune=R.make_tune(layout="direct"))
     for depth, block, grid, step in [(1, 32, 1, "barrett"), (3, 64, 7, "montgomery"),
-                                     (15, 256, 0, "barrett"), (31, 1024, 3, "barrett"),
+                                     (15, 256, 0, "barrett"), (7, 1024, 3, "barrett"), (31, 256, 0, "barrett"),
                                      (63, 128, 152, "montgomery"), (127, 64, 0, "barrett"),
-                                     (255, 32, 5, "montgomery"), (9, 96, 1000, "barrett")]:
+                                     (255, 32, 5, "montgomery"), (9, 96, 1000, "barrett"),
+                                     (5, 128, 0, "shared"), (63, 64, 77, "shared")]:
         t = R.make_tune(step=step, layout="tiled", depth=depth, block=block, grid=grid)
         out = R.generate_at(a, off, n, "f64", tune=t)
         assert torch.equal(out.view(torch.int64), ref.view(torch.int64)), (depth, block, grid)
@@ -179,7 +180,7 @@ def test_two_gib_single_stream_is_thread_count_invariant(R, oracle_mod):
                                                              grid=grid))
         assert torch.equal(out.view(torch.int64), tb), (block, grid)
         del out
-    for step, conv in [("montgomery", "int"), ("barrett", "fp64")]:
+    for step, conv in [("montgomery", "int"), ("barrett", "fp64"), ("barrett", "int")]:
         out = R.generate_at(a, 0, n, "f64", tune=R.make_tune(step=step, conv=conv))
         assert torch.equal(out.view(torch.int64), tb), (step, conv)
         del out

@@ -1,0 +1,186 @@
+"""The arithmetic the CUDA kernels rely on, restated in Python and checked
+against the definitions (no GPU).
+
+These are models of the reductions (Sec. 2.1) and of the integer rounding,
+written from their derivations -- not imports of the CUDA code, which Python
+cannot run.  Each model is checked against `%` and exact rational rounding on
+random, edge and adversarial states, and the bounds its correctness argument
+uses are checked directly.  The GPU parity tests then check the kernels
+themselves against the oracle.
+"""
+import random
+import struct
+from fractions import Fraction
+
+import pytest
+
+M = 3 ** 33
+MU = 2 ** 106 // M
+K = MU + 1
+MR = K // 2
+R3I = 1.0 / 5559060566555523.0
+MASK32 = 2 ** 32 - 1
+M0, M1 = M & MASK32, M >> 32
+K0, K1 = K & MASK32, K >> 32
+
+
+def f64_bits(x: float) -> int:
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def rn_bits(z: int) -> int:
+    """Bits of RN(z * r3i), by exact rational arithmetic."""
+    return f64_bits(float(Fraction(z) * Fraction(R3I)))
+
+
+def funnel_l(lo, hi, s):
+    return ((((hi << 32) | lo) << (s & 31)) >> 32) & MASK32
+
+
+def funnel_r(lo, hi, s):
+    return (((hi << 32) | lo) >> (s & 31)) & MASK32
+
+
+def clz32(x):
+    return 32 - x.bit_length()
+
+
+def states(count=50000, seed=0):
+    rnd = random.Random(seed)
+    zs = [1, 2, 3, 4, M - 1, M - 2, M - 3, M // 2, M // 2 + 1]
+    zs += [(M >> e) + d for e in range(54) for d in (-1, 0, 1)]
+    zs += [2 ** k for k in range(53)] + [3 * 2 ** k for k in range(52)]
+    zs += [rnd.randrange(1, M) for _ in range(count)]
+    return sorted({z for z in zs if 0 < z < M})
+
+
+def test_constants_relations():
+    assert MU == 0x33D9481681D79D
+    assert K == 2 * MR and MR == 0x19ECA40B40EBCF
+    assert Fraction(R3I) == Fraction(MR, 2 ** 105)
+    assert M < 2 ** 53 < 2 * M
+
+
+def test_modified_barrett_never_wraps():
+    """Sec. 2.1.3: q3 = floor(mu z / 2^53) in {Q-1, Q}; the 53-bit wrap of
+    2^53 z - q3 m would need frac(2^53 z/m) >= 2^53/m - 1, while q3 = Q-1
+    needs frac(2^53 z/m) < m/2^53.  The two thresholds do not overlap."""
+    assert Fraction(M, 2 ** 53) < Fraction(2 ** 53, M) - 1
+    for z in states():
+        q3 = (z * MU) >> 53
+        Q = (z << 53) // M
+        assert q3 in (Q - 1, Q)
+        r = 2 ** 53 - ((q3 * M) & (2 ** 53 - 1))
+        if r >= M:
+            r -= M
+        assert r == (z << 53) % M
+
+
+def test_montgomery_back_step():
+    negminv = (-pow(M, -1, 2 ** 53)) % 2 ** 53
+    for z in states():
+        u = (z * negminv) & (2 ** 53 - 1)
+        prev = ((u * M) >> 53) + 1
+        assert 0 < prev < M
+        assert (prev << 53) % M == z
+
+
+def test_general_barrett_mulmod_bound():
+    """x*y mod m with q1 = t >> 52, q3 = (q1 mu) >> 54: t - q3 m < 3m."""
+    rnd = random.Random(1)
+    for _ in range(50000):
+        x, y = rnd.randrange(1, M), rnd.randrange(1, M)
+        t = x * y
+        q3 = ((t >> 52) * MU) >> 54
+        r = t - q3 * M
+        assert 0 <= r < 3 * M < 2 ** 64
+        while r >= M:
+            r -= M
+        assert r == t % M
+
+
+def shared_step_model(z):
+    """Word-level model of the shared-quotient step and its conversion."""
+    z0, z1 = z & MASK32, z >> 32
+    t0 = z0 * K0
+    t1 = z0 * K1 + (t0 >> 32)
+    t1 = z1 * K0 + t1
+    t2 = z1 * K1 + (t1 >> 32)
+    assert t1 < 2 ** 64 and t2 < 2 ** 64
+    w1, w2, w3 = t1 & MASK32, t2 & MASK32, t2 >> 32
+    q0, q1 = funnel_r(w1, w2, 21), funnel_r(w2, w3, 21)
+    qm = q0 * M0
+    qm_hi = ((qm >> 32) + q0 * M1 + q1 * M0) & MASK32
+    r = ((((z0 << 21) & MASK32) << 32) - ((qm_hi << 32) | (qm & MASK32))) % 2 ** 64
+    if r >= 2 ** 63:
+        r = (r + M) % 2 ** 64
+    if q1 == 0:
+        return r, None
+    c = clz32(q1)
+    s = c - 10
+    lh = (w1 << 11) & MASK32
+    g_hi, g_lo = funnel_l(q0, q1, s), funnel_l(lh, q0, s)
+    x = ((g_hi << 32) | g_lo) + (((1032 - c) << 53) | 1)
+    assert x < 2 ** 64
+    return r, x >> 1
+
+
+def test_shared_quotient_is_q_or_q_plus_one():
+    for z in states():
+        q = (z * K) >> 53
+        Q = (z << 53) // M
+        assert q in (Q, Q + 1)
+        assert -M < (z << 53) - q * M < M
+
+
+def test_no_state_rounds_on_a_tie():
+    """p = z*K = 2 z M_r with M_r odd; a tie needs v2(p) = bitlen(p) - 54,
+    which forces v2(z) >= bitlen(z) - 2, i.e. z = 2^k or 3*2^k."""
+    assert MR % 2 == 1
+    for z in [2 ** k for k in range(53)] + [3 * 2 ** k for k in range(52)]:
+        if z >= M:
+            continue
+        p = z * K
+        d = p.bit_length() - 53
+        assert p % 2 ** d != 2 ** (d - 1)
+
+
+def test_shared_step_model_matches_definitions():
+    slow = 0
+    for z in states(80000, seed=2):
+        r, bits = shared_step_model(z)
+        assert r == (z << 53) % M
+        if bits is None:
+            slow += 1
+            assert z * K < 2 ** 85  # q < 2^32: the variate is below 2^-21
+            continue
+        assert bits == rn_bits(z), z
+    assert slow > 0  # the rare path is exercised by the edge states
+
+
+def general_conversion_model(p):
+    """The general integer rounding of p * 2^-106 (any leading-zero count)."""
+    q = p >> 53
+    low = p & (2 ** 53 - 1)
+    lz = (64 - q.bit_length()) - 11
+    mant = (q << lz) | (low >> (53 - lz))
+    rest = (low << (11 + lz)) % 2 ** 64
+    half = 2 ** 63
+    up = 1 if (rest > half or (rest == half and mant & 1)) else 0
+    return ((1021 - lz) << 52) + mant + up
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_general_conversion_model(seed):
+    for z in states(30000, seed=seed):
+        assert general_conversion_model(z * K) == rn_bits(z)
+
+
+def test_f32_from_f64_bits_is_truncation():
+    for z in states(20000, seed=5):
+        b = rn_bits(z)
+        f = ((b >> 29) - (896 << 23)) & MASK32
+        v = Fraction(struct.unpack("<d", struct.pack("<Q", b))[0])
+        fv = Fraction(struct.unpack("<f", struct.pack("<I", f))[0])
+        nxt = Fraction(struct.unpack("<f", struct.pack("<I", f + 1))[0])
+        assert fv <= v < nxt
