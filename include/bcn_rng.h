@@ -103,7 +103,7 @@ typedef struct {
   uint32_t depth;   /* TILED: variates per lane per tile, odd, 1..255        */
   uint32_t block;   /* threads per block (TILED: multiple of 32, <= 1024)    */
   uint32_t grid;    /* blocks                                                */
-  uint32_t reserved;
+  uint32_t unit;    /* BATCH: tiles per work unit (0 = choose); else ignored */
 } rng_tune;
 
 /* Largest n accepted by one generation call. */
@@ -157,6 +157,41 @@ rng_status rng_generate_at(uint64_t start_index, uint64_t offset, uint64_t n,
  * write ceiling the generator is measured against. */
 rng_status rng_fill_constant(uint64_t n, rng_dtype dt, double value, void *out,
                              void *cuda_stream, const rng_tune *tune);
+
+/* --------------------------------------------------------------- batches */
+
+/* A batch: many independent streams of uneven length generated by one
+ * persistent launch (the paper's parallel split of Sec. 1 applied to many
+ * sequences at once).  Stream s writes variates offsets[s] ..
+ * offsets[s]+counts[s]-1 of the sequence seeded with starts[s] to the device
+ * array outs[s] as dtypes[s] (rng_dtype values); offsets may be NULL (all 0).
+ * Each seed must satisfy Algorithm BB, step 1 (else RNG_ERANGE); each non-empty
+ * output must be aligned to its element size (else RNG_EINVAL).  The host
+ * arrays are copied; the output arrays stay caller-owned and must outlive the
+ * plan's launches.  tune (NULL = choose) sets step, conversion, tile depth,
+ * block, grid and `unit` (tiles per work unit).  Creation allocates a small
+ * device table (about 48 bytes per stream) and synchronises the device, so it
+ * is not capturable; launches are. */
+typedef struct bcn_batch bcn_batch;
+rng_status rng_batch_create(uint32_t nstreams, const uint64_t *starts, const uint64_t *offsets,
+                            const uint64_t *counts, const uint8_t *dtypes, void *const *outs,
+                            const rng_tune *tune, bcn_batch **out);
+
+/* Generate every stream of the plan on `cuda_stream` (asynchronous: one
+ * memset of the plan's work counter and one kernel launch).  Launches of one
+ * plan must not overlap on the device: they share the work counter. */
+rng_status rng_batch_launch(bcn_batch *b, void *cuda_stream);
+
+/* The same work replayed as a CUDA graph (captured on first use, then one
+ * cudaGraphLaunch per call on `cuda_stream`). */
+rng_status rng_batch_graph_launch(bcn_batch *b, void *cuda_stream);
+
+/* Totals of the plan and its resolved tuning (each pointer nullable). */
+rng_status rng_batch_info(const bcn_batch *b, uint64_t *total_elems, uint64_t *total_bytes,
+                          uint64_t *units, rng_tune *resolved);
+
+/* Free the plan (its device table and graph).  NULL is a no-op. */
+rng_status rng_batch_destroy(bcn_batch *b);
 
 /* -------------------------------------------------------------- autotune */
 

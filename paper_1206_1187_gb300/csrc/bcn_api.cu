@@ -215,7 +215,7 @@ rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune* in, rng_tu
   out->depth = L.depth;
   out->block = L.block;
   out->grid = L.grid;
-  out->reserved = 0;
+  out->unit = 0;
   return RNG_OK;
 }
 

@@ -1,0 +1,341 @@
+// bcn_batch.cu -- many streams of uneven length in one persistent launch.
+//
+// A batch plan holds one descriptor per stream (exponent base, length, output
+// pointer, element type) and cuts every stream into work units of
+// unit_tiles tiles (32*depth elements each); the last unit of a stream may be
+// short.  One persistent grid, sized to fill the GPU, pulls unit numbers from
+// a device counter; a warp maps its unit to a stream by binary search over the
+// prefix of unit counts, jumps every lane to its run (Eq. 2), and produces the
+// unit's full tiles through the same shared-memory + bulk-copy path as the
+// single-stream kernel, its short remainder with plain stores.  Unit 0 of a
+// stream also writes the stream's head (elements before its first 16-byte
+// boundary).  The counter is cleared by a memset node before each launch, so a
+// plan can be replayed as a two-node CUDA graph.
+//
+// This follows the paper's parallel split (Sec. 1): every unit is a block of
+// a stream reached by skip-ahead, so no result depends on which warp runs it.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "bcn_gen.cuh"
+
+struct bcn_batch {
+  uint32_t nstreams;
+  uint64_t total_units;
+  uint64_t total_elems;
+  uint64_t total_bytes;
+  rng_tune tune;       // resolved
+  uint32_t unit_elems;
+  void* dev;           // descriptors | prefix | counter (one allocation)
+  size_t dev_bytes;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int device;
+};
+
+namespace bcn {
+
+struct BatchDesc {
+  uint64_t ebase;       // (seed - 3^33 + 53*offset) mod P
+  uint64_t n;           // elements
+  unsigned char* out;   // element 0
+  uint64_t unit0;       // first unit number
+  uint32_t dt;          // DT_F64 / DT_F32 / DT_U64
+  uint32_t head;        // elements before the first 16-byte boundary
+};
+
+struct BatchParams {
+  const BatchDesc* desc;
+  const uint64_t* prefix;  // nstreams + 1 unit counts, prefix[s] = desc[s].unit0
+  unsigned long long* counter;
+  uint64_t total_units;
+  uint64_t jump;
+  uint32_t nstreams;
+  uint32_t depth;
+  uint32_t unit_tiles;
+  uint32_t skip;
+};
+
+// The unit's elements [s0, s1) of stream d: full tiles by bulk copy, the
+// remainder by plain stores; unit 0 also writes the head [0, head).
+template <int DT, int STEP, int CONV>
+__device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const BatchParams& p,
+                                           unsigned char* buf0_bytes, uint32_t& issued,
+                                           uint32_t lane) {
+  typedef typename Word<DT>::type W;
+  W* const out = reinterpret_cast<W*>(d.out);
+  const uint32_t c = p.depth;
+  const uint64_t tile_elems = 32ull * c;
+  const uint64_t unit_elems = tile_elems * p.unit_tiles;
+  const uint64_t s0 = d.head + k * unit_elems;
+  const uint64_t s1 = min(s0 + unit_elems, d.n);
+  if (k == 0)
+    run_direct<DT, STEP, CONV>(out, d.ebase, p.skip, lane * d.head / 32,
+                               (lane + 1) * d.head / 32, 0);
+  if (s0 >= s1) return;
+  const uint64_t ntiles = (s1 - s0) / tile_elems;
+  if (ntiles > 0) {
+    Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(d.ebase, s0 + (uint64_t)lane * c, c, p.skip);
+    warp_tiles<DT, STEP, CONV>(out, s0, ntiles, c, p.jump, g, reinterpret_cast<W*>(buf0_bytes),
+                               issued, lane, 0);
+  }
+  const uint64_t r0 = s0 + ntiles * tile_elems, rl = s1 - r0;
+  run_direct<DT, STEP, CONV>(out, d.ebase, p.skip, r0 + lane * rl / 32, r0 + (lane + 1) * rl / 32,
+                             0);
+}
+
+template <int STEP, int CONV>
+__global__ void __launch_bounds__(1024) batch_kernel(const BatchParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = threadIdx.x >> 5;
+  // two tile buffers per warp, sized for 8-byte elements
+  unsigned char* const buf0 = smem + (size_t)warp * 2u * 32u * p.depth * 8u;
+  uint32_t issued = 0;
+  for (;;) {
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd(p.counter, 1ull);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= p.total_units) break;
+    // stream s: prefix[s] <= u < prefix[s+1]
+    uint32_t lo = 0, hi = p.nstreams;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&p.prefix[mid]) <= u) lo = mid;
+      else hi = mid;
+    }
+    const BatchDesc d = p.desc[lo];
+    const uint64_t k = u - d.unit0;
+    if (d.dt == DT_F64) batch_unit<DT_F64, STEP, CONV>(d, k, p, buf0, issued, lane);
+    else if (d.dt == DT_F32) batch_unit<DT_F32, STEP, CONV>(d, k, p, buf0, issued, lane);
+    else batch_unit<DT_U64, STEP, CONV>(d, k, p, buf0, issued, lane);
+  }
+  if (lane == 0) bulk_wait_all();
+  __syncwarp();
+}
+
+static const void* pick_batch(int st, int cv) {
+  switch (st) {
+    case ST_SHARED: return cv == CV_FP64 ? (const void*)batch_kernel<ST_SHARED, CV_FP64>
+                                         : (const void*)batch_kernel<ST_SHARED, CV_INT>;
+    case ST_BARRETT: return cv == CV_FP64 ? (const void*)batch_kernel<ST_BARRETT, CV_FP64>
+                                          : (const void*)batch_kernel<ST_BARRETT, CV_INT>;
+    case ST_MONT: return cv == CV_FP64 ? (const void*)batch_kernel<ST_MONT, CV_FP64>
+                                       : (const void*)batch_kernel<ST_MONT, CV_INT>;
+    default: return nullptr;
+  }
+}
+
+static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
+  const void* fn = pick_batch((int)b->tune.step, (int)b->tune.conv);
+  if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
+  unsigned char* base = static_cast<unsigned char*>(b->dev);
+  BatchParams p;
+  p.desc = reinterpret_cast<const BatchDesc*>(base);
+  p.prefix = reinterpret_cast<const uint64_t*>(base + sizeof(BatchDesc) * b->nstreams);
+  p.counter = reinterpret_cast<unsigned long long*>(base + sizeof(BatchDesc) * b->nstreams +
+                                                    sizeof(uint64_t) * (b->nstreams + 1));
+  p.total_units = b->total_units;
+  const uint64_t stride = (b->tune.step == ST_MONT) ? 33ull : 31ull;
+  p.jump = host_pow2((53ull * stride * b->tune.depth) % kP);
+  p.nstreams = b->nstreams;
+  p.depth = b->tune.depth;
+  p.unit_tiles = b->tune.unit;
+  p.skip = b->tune.skip;
+  cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), cs);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(batch counter)");
+  const size_t smem = (size_t)(b->tune.block / 32) * 2 * 32 * b->tune.depth * 8;
+  void* args[] = {&p};
+  e = cudaLaunchKernel(fn, dim3(b->tune.grid), dim3(b->tune.block), args, smem, cs);
+  if (e != cudaSuccess) return cuda_error(e, "batch kernel launch");
+  return RNG_OK;
+}
+
+}  // namespace bcn
+
+using namespace bcn;
+
+extern "C" {
+
+rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uint64_t* offsets,
+                            const uint64_t* counts, const uint8_t* dtypes, void* const* outs,
+                            const rng_tune* tune, bcn_batch** out) {
+  if (!out) return set_error(RNG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nstreams == 0 || !starts || !counts || !dtypes || !outs)
+    return set_error(RNG_EINVAL, "nstreams > 0 and the starts/counts/dtypes/outs arrays are required");
+  rng_tune t = {};
+  if (tune) t = *tune;
+  const rng_tune d = auto_defaults(RNG_F64);
+  if (!t.step) t.step = d.step ? d.step : ST_SHARED;
+  if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
+  if (!t.skip) t.skip = SK_TABLE;
+  if (!t.depth) t.depth = d.depth ? d.depth : 15;
+  if (!t.block) t.block = 256;
+  if (!t.unit) t.unit = 16;  // tiles per work unit
+  t.layout = RNG_LAYOUT_TILED;
+  if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
+    return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
+  if (t.conv != CV_INT && t.conv != CV_FP64)
+    return set_error(RNG_EINVAL, "tune.conv %u is not a conversion", t.conv);
+  if (t.skip != SK_TABLE && t.skip != SK_SQMUL)
+    return set_error(RNG_EINVAL, "tune.skip %u is not a skip-ahead method", t.skip);
+  if (t.depth % 2 == 0 || t.depth > kMaxDepth)
+    return set_error(RNG_EINVAL, "tune.depth %u must be odd and at most %u", t.depth, kMaxDepth);
+  if (t.block % 32 != 0 || t.block == 0 || t.block > 1024)
+    return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024", t.block);
+  if (t.unit > 4096) return set_error(RNG_EINVAL, "tune.unit (tiles per work unit) > 4096");
+  DeviceInfo di;
+  rng_status st = device_info(&di);
+  if (st != RNG_OK) return st;
+  const size_t smem = (size_t)(t.block / 32) * 2 * 32 * t.depth * 8;
+  if (smem > di.smem_optin)
+    return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
+                     smem, di.smem_optin);
+  const uint64_t unit_elems = 32ull * t.depth * t.unit;
+
+  std::vector<BatchDesc> desc(nstreams);
+  std::vector<uint64_t> prefix(nstreams + 1);
+  uint64_t units = 0, elems = 0, bytes = 0;
+  for (uint32_t s = 0; s < nstreams; ++s) {
+    const uint64_t seed = starts[s], off = offsets ? offsets[s] : 0, n = counts[s];
+    if (seed < kSeedMin || seed > kSeedMax)
+      return set_error(RNG_ERANGE, "stream %u: start index outside [3^33+100, 2^53]", s);
+    if (dtypes[s] > RNG_U64) return set_error(RNG_EINVAL, "stream %u: bad dtype %u", s, dtypes[s]);
+    if (n > RNG_MAX_N) return set_error(RNG_ERANGE, "stream %u: count exceeds RNG_MAX_N", s);
+    if (n > UINT64_MAX - off) return set_error(RNG_ERANGE, "stream %u: offset + count overflows", s);
+    const size_t esz = dtype_size(dtypes[s]);
+    if (n > 0 && (!outs[s] || (uintptr_t)outs[s] % esz != 0))
+      return set_error(RNG_EINVAL, "stream %u: output NULL or not aligned to %zu bytes", s, esz);
+    BatchDesc& D = desc[s];
+    D.ebase = host_exponent_base(seed, off);
+    D.n = n;
+    D.out = static_cast<unsigned char*>(outs[s]);
+    D.dt = dtypes[s];
+    D.head = n ? (uint32_t)head_elems(outs[s], esz, n) : 0;
+    D.unit0 = units;
+    prefix[s] = units;
+    uint64_t nu = 0;
+    if (n > 0) nu = n > D.head ? (n - D.head + unit_elems - 1) / unit_elems : 1;
+    units += nu;
+    elems += n;
+    bytes += n * esz;
+  }
+  prefix[nstreams] = units;
+
+  bcn_batch* b = new (std::nothrow) bcn_batch;
+  if (!b) return set_error(RNG_ENOMEM, "out of host memory");
+  b->nstreams = nstreams;
+  b->total_units = units;
+  b->total_elems = elems;
+  b->total_bytes = bytes;
+  b->unit_elems = (uint32_t)unit_elems;
+  b->graph = nullptr;
+  b->exec = nullptr;
+  b->device = di.device;
+  b->dev = nullptr;
+  const size_t desc_bytes = sizeof(BatchDesc) * nstreams;
+  const size_t prefix_bytes = sizeof(uint64_t) * (nstreams + 1);
+  b->dev_bytes = desc_bytes + prefix_bytes + 16;
+  cudaError_t e = cudaMalloc(&b->dev, b->dev_bytes);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_error(e, "cudaMalloc(batch plan)");
+  }
+  unsigned char* base = static_cast<unsigned char*>(b->dev);
+  e = cudaMemcpy(base, desc.data(), desc_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(base + desc_bytes, prefix.data(), prefix_bytes,
+                                       cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(base + desc_bytes + prefix_bytes, 0, 16);
+  if (e != cudaSuccess) {
+    cudaFree(b->dev);
+    delete b;
+    return cuda_error(e, "uploading the batch plan");
+  }
+  const void* fn = pick_batch((int)t.step, (int)t.conv);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin);
+  if (e != cudaSuccess) {
+    cudaFree(b->dev);
+    delete b;
+    return cuda_error(e, "cudaFuncSetAttribute(batch)");
+  }
+  if (!t.grid) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)t.block, smem);
+    if (e != cudaSuccess) {
+      cudaFree(b->dev);
+      delete b;
+      return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)");
+    }
+    uint64_t full = (uint64_t)std::max(per_sm, 1) * (uint64_t)di.sms;
+    uint64_t need = (units + t.block / 32 - 1) / (t.block / 32);
+    t.grid = (uint32_t)std::max<uint64_t>(1, std::min(full, need));
+  }
+  b->tune = t;
+  *out = b;
+  return RNG_OK;
+}
+
+rng_status rng_batch_launch(bcn_batch* b, void* cuda_stream) {
+  if (!b) return set_error(RNG_EINVAL, "batch is NULL");
+  if (b->total_units == 0) return RNG_OK;
+  return batch_launch_raw(b, static_cast<cudaStream_t>(cuda_stream));
+}
+
+rng_status rng_batch_graph_launch(bcn_batch* b, void* cuda_stream) {
+  if (!b) return set_error(RNG_EINVAL, "batch is NULL");
+  if (b->total_units == 0) return RNG_OK;
+  cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+  if (!b->exec) {  // capture memset + kernel once, on a private stream
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate(capture)");
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_error(e, "cudaStreamBeginCapture");
+    }
+    rng_status st = batch_launch_raw(b, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (st != RNG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_error(e, "cudaGraphInstantiate");
+    }
+    b->graph = g;
+    b->exec = x;
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, cs);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+  return RNG_OK;
+}
+
+rng_status rng_batch_info(const bcn_batch* b, uint64_t* total_elems, uint64_t* total_bytes,
+                          uint64_t* units, rng_tune* resolved) {
+  if (!b) return set_error(RNG_EINVAL, "batch is NULL");
+  if (total_elems) *total_elems = b->total_elems;
+  if (total_bytes) *total_bytes = b->total_bytes;
+  if (units) *units = b->total_units;
+  if (resolved) *resolved = b->tune;
+  return RNG_OK;
+}
+
+rng_status rng_batch_destroy(bcn_batch* b) {
+  if (!b) return RNG_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->dev) cudaFree(b->dev);
+  delete b;
+  return RNG_OK;
+}
+
+}  // extern "C"

@@ -25,120 +25,9 @@
 #include <set>
 #include <utility>
 
-#include "bcn_internal.h"
-#include "bcn_math.cuh"
+#include "bcn_gen.cuh"
 
 namespace bcn {
-
-template <int DT> struct Word { typedef uint64_t type; };
-template <> struct Word<DT_F32> { typedef uint32_t type; };
-
-// The output word of state z.  (phi, plo) is the product z*mu when the
-// caller has it (Barrett) -- the integer conversion reuses it.
-template <int DT, int CONV>
-__device__ __forceinline__ typename Word<DT>::type to_word(uint64_t z, uint64_t phi,
-                                                           uint64_t plo) {
-  if constexpr (DT == DT_U64) {
-    return z;
-  } else {
-    uint64_t bits;
-    if constexpr (CONV == CV_INT) {
-      uint64_t qh, ql;
-      p_from_barrett_product(z, phi, plo, qh, ql);
-      bits = f64_bits_from_p(qh, ql);
-    } else {
-      bits = f64_bits_fp64(z);
-    }
-    if constexpr (DT == DT_F64) return bits;
-    else return f32_bits_from_f64_bits(bits);
-  }
-}
-
-// One chain of the generator.  Barrett runs forward (z is the state of the
-// next variate to emit); Montgomery runs backward (z is the state of the
-// variate emitted next, going down).
-template <int DT, int STEP, int CONV>
-struct Gen {
-  uint64_t z;
-  __device__ __forceinline__ typename Word<DT>::type next() {
-    if constexpr (STEP == ST_SHARED) {
-      if constexpr (DT == DT_U64) {
-        const uint64_t w = z;
-        z = shared_advance(z);
-        return w;
-      } else if constexpr (CONV == CV_FP64) {
-        const uint64_t bits = f64_bits_fp64(z);
-        z = shared_advance(z);
-        if constexpr (DT == DT_F64) return bits;
-        else return f32_bits_from_f64_bits(bits);
-      } else {
-        const uint64_t bits = shared_step_f64(z);
-        if constexpr (DT == DT_F64) return bits;
-        else return f32_bits_from_f64_bits(bits);
-      }
-    } else if constexpr (STEP == ST_BARRETT) {
-      uint64_t plo = z * kMu, phi = umulhi(z, kMu);
-      auto w = to_word<DT, CONV>(z, phi, plo);
-      z = barrett_from_product(phi, plo);
-      return w;
-    } else {
-      uint64_t plo = 0, phi = 0;
-      if constexpr (DT != DT_U64 && CONV == CV_INT) {
-        plo = z * kMu;
-        phi = umulhi(z, kMu);
-      }
-      auto w = to_word<DT, CONV>(z, phi, plo);
-      z = montgomery_back(z);
-      return w;
-    }
-  }
-};
-
-__device__ __forceinline__ uint64_t seed_state(uint64_t e, uint32_t skip) {
-  return skip == SK_SQMUL ? seed_state_sqmul(e) : seed_state_table(e);
-}
-
-// State of element idx of the call: exponent ebase + 53*(idx+1)  (mod P).
-__device__ __forceinline__ uint64_t state_of(uint64_t ebase, uint64_t idx, uint32_t skip) {
-  return seed_state(exponent_add(ebase, idx + 1), skip);
-}
-
-// Elements [a, b) with plain global stores.
-template <int DT, int STEP, int CONV>
-__device__ void run_direct(typename Word<DT>::type* __restrict__ out, uint64_t ebase,
-                           uint32_t skip, uint64_t a, uint64_t b, uint64_t cbits) {
-  typedef typename Word<DT>::type W;
-  if (a >= b) return;
-  if constexpr (STEP == ST_CONST) {
-    for (uint64_t i = a; i < b; ++i) out[i] = (W)cbits;
-  } else if constexpr (STEP != ST_MONT) {
-    Gen<DT, STEP, CONV> g{state_of(ebase, a, skip)};
-    for (uint64_t i = a; i < b; ++i) out[i] = g.next();
-  } else {
-    Gen<DT, STEP, CONV> g{state_of(ebase, b - 1, skip)};
-    for (uint64_t i = b; i-- > a;) out[i] = g.next();
-  }
-}
-
-// ------------------------------------------------------- bulk async copies
-__device__ __forceinline__ void fence_proxy_async_shared() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
-  const uint64_t g = (uint64_t)__cvta_generic_to_global(gdst);
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-               :: "l"(g), "r"(s), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_commit() {
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read_1() {
-  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
 
 struct TiledParams {
   unsigned char* out;  // element 0 of the call
@@ -171,8 +60,7 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
   const uint64_t nw = (uint64_t)gridDim.x * wpb;
   const uint32_t c = p.depth;
   const uint32_t tile_elems = 32u * c;
-  const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
-  W* const buf0 = reinterpret_cast<W*>(smem + (size_t)warp * 2u * tile_bytes);
+  W* const buf0 = reinterpret_cast<W*>(smem + (size_t)warp * 2u * tile_elems * sizeof(W));
   W* const out = reinterpret_cast<W*>(p.out);
 
   const uint64_t t0 = gw * p.ntiles / nw;
@@ -180,36 +68,10 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
   if (t0 < t1) {
     // this lane's first element in the warp's first tile
     const uint64_t first = p.head + t0 * tile_elems + (uint64_t)lane * c;
-    Gen<DT, STEP, CONV> g{0};
-    if constexpr (STEP == ST_BARRETT || STEP == ST_SHARED) g.z = state_of(p.ebase, first, p.skip);
-    if constexpr (STEP == ST_MONT) g.z = state_of(p.ebase, first + c - 1, p.skip);
-    for (uint64_t t = t0; t < t1; ++t) {
-      const uint32_t k = (uint32_t)(t - t0);
-      W* const buf = buf0 + (k & 1u) * tile_elems;
-      if (k >= 2) {  // the copy that last read this buffer must be done
-        if (lane == 0) bulk_wait_read_1();
-        __syncwarp();
-      }
-      W* const mine = buf + lane * c;
-      if constexpr (STEP == ST_CONST) {
-        for (uint32_t i = 0; i < c; ++i) mine[i] = (W)p.cbits;
-      } else if constexpr (STEP != ST_MONT) {
-#pragma unroll 4
-        for (uint32_t i = 0; i < c; ++i) mine[i] = g.next();
-      } else {
-#pragma unroll 4
-        for (uint32_t i = c; i-- > 0;) mine[i] = g.next();
-      }
-      fence_proxy_async_shared();
-      __syncwarp();
-      if (lane == 0) {
-        bulk_store(out + p.head + t * tile_elems, buf, tile_bytes);
-        bulk_commit();
-      }
-      if constexpr (STEP != ST_CONST) {
-        if (t + 1 < t1) g.z = mulmod(g.z, p.jump);
-      }
-    }
+    Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
+    uint32_t issued = 0;
+    warp_tiles<DT, STEP, CONV>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump, g, buf0,
+                               issued, lane, p.cbits);
     if (lane == 0) bulk_wait_all();
     __syncwarp();
   }
@@ -292,12 +154,6 @@ static rng_status enable_smem(const void* fn, int device, size_t bytes) {
 
 static uint64_t tile_count(uint64_t n, uint64_t head, uint32_t depth) {
   return n > head ? (n - head) / (32ull * depth) : 0;
-}
-
-static uint64_t head_elems(const void* out, size_t esz, uint64_t n) {
-  const uintptr_t addr = (uintptr_t)out;
-  uint64_t h = ((16 - (addr & 15)) & 15) / esz;
-  return h < n ? h : n;
 }
 
 rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* out,

@@ -29,6 +29,13 @@ struct BulkLaunch {
 // Element size in bytes of an rng_dtype.
 inline size_t dtype_size(int dt) { return dt == DT_F32 ? 4 : 8; }
 
+// Elements before the first 16-byte boundary of `out` (at most n).
+inline uint64_t head_elems(const void* out, size_t esz, uint64_t n) {
+  const uintptr_t addr = (uintptr_t)out;
+  const uint64_t h = ((16 - (addr & 15)) & 15) / esz;
+  return h < n ? h : n;
+}
+
 // Set the calling thread's error message and return `st`.
 rng_status set_error(rng_status st, const char* fmt, ...);
 rng_status cuda_error(cudaError_t e, const char* what);

@@ -94,7 +94,7 @@ rng_status rng_autotune_bulk(uint64_t n, rng_dtype dt, void* out, void* cuda_str
       best->depth = L.depth;
       best->block = L.block;
       best->grid = L.grid;
-      best->reserved = 0;
+      best->unit = 0;
     }
   }
   cudaEventDestroy(e0);

@@ -42,18 +42,18 @@ class RNGError(RuntimeError):
 
 class Tune(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint32) for f in
-                ("step", "conv", "layout", "skip", "depth", "block", "grid", "reserved")]
+                ("step", "conv", "layout", "skip", "depth", "block", "grid", "unit")]
 
 
 def make_tune(step="auto", conv="auto", layout="auto", skip="auto", depth=0, block=0,
-              grid=0) -> Tune:
+              grid=0, unit=0) -> Tune:
     """Launch tuning; zero / "auto" lets the library choose.  Results never
     depend on it, only speed does."""
     return Tune(STEP[step] if isinstance(step, str) else step,
                 CONV[conv] if isinstance(conv, str) else conv,
                 LAYOUT[layout] if isinstance(layout, str) else layout,
                 SKIP[skip] if isinstance(skip, str) else skip,
-                depth, block, grid, 0)
+                depth, block, grid, unit)
 
 
 def _load() -> ctypes.CDLL:
@@ -84,6 +84,12 @@ def _load() -> ctypes.CDLL:
         "rng_autotune_bulk": ([u64, i32, vp, vp, tp, u32, u32, tp,
                                ctypes.POINTER(ctypes.c_float)], i32),
         "rng_set_auto_tune": ([i32, tp], i32),
+        "rng_batch_create": ([u32, vp, vp, vp, vp, vp, tp, ctypes.POINTER(vp)], i32),
+        "rng_batch_launch": ([vp, vp], i32),
+        "rng_batch_graph_launch": ([vp, vp], i32),
+        "rng_batch_info": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                            ctypes.POINTER(u64), tp], i32),
+        "rng_batch_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +248,63 @@ def tune_dict(t: Tune) -> dict:
     return {"step": inv(STEP, t.step), "conv": inv(CONV, t.conv),
             "layout": inv(LAYOUT, t.layout), "skip": inv(SKIP, t.skip),
             "depth": t.depth, "block": t.block, "grid": t.grid}
+
+
+class Batch:
+    """Many streams of uneven length in one persistent launch.
+
+    starts, counts (and optional offsets) are integer sequences; dtypes a
+    sequence of "f64"/"f32"/"u64"; outs a list of CUDA tensors (or None to
+    allocate).  launch() / graph_launch() enqueue on torch's current stream."""
+
+    def __init__(self, starts, counts, dtypes, outs=None, offsets=None, tune=None):
+        import numpy as np
+        n = len(starts)
+        self.starts = np.ascontiguousarray(starts, dtype=np.uint64)
+        self.counts = np.ascontiguousarray(counts, dtype=np.uint64)
+        self.offsets = (np.ascontiguousarray(offsets, dtype=np.uint64)
+                        if offsets is not None else None)
+        self.dtypes = list(dtypes)
+        codes = np.ascontiguousarray([_dtype(d)[0] for d in self.dtypes], dtype=np.uint8)
+        if outs is None:
+            outs = [torch.empty(int(c), dtype=_dtype(d)[1], device="cuda")
+                    for c, d in zip(self.counts, self.dtypes)]
+        self.outs = outs
+        ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() if o is not None else 0 for o in outs])
+        self._ptrs = ptrs
+        h = ctypes.c_void_p()
+        _check(lib.rng_batch_create(
+            n, ctypes.c_void_p(self.starts.ctypes.data),
+            ctypes.c_void_p(self.offsets.ctypes.data) if self.offsets is not None else None,
+            ctypes.c_void_p(self.counts.ctypes.data), ctypes.c_void_p(codes.ctypes.data),
+            ptrs, _tune_ptr(tune), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None) -> None:
+        _check(lib.rng_batch_launch(self._h, ctypes.c_void_p(_stream_handle(stream))))
+
+    def graph_launch(self, stream=None) -> None:
+        _check(lib.rng_batch_graph_launch(self._h, ctypes.c_void_p(_stream_handle(stream))))
+
+    def info(self) -> dict:
+        e, b, u = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        t = Tune()
+        _check(lib.rng_batch_info(self._h, ctypes.byref(e), ctypes.byref(b), ctypes.byref(u),
+                                  ctypes.byref(t)))
+        d = tune_dict(t)
+        d["unit"] = t.unit
+        return {"elems": e.value, "bytes": b.value, "units": u.value, "tune": d}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.rng_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> int:
