@@ -53,6 +53,7 @@ def parse_args():
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched measurement")
+    p.add_argument("--no-fused", action="store_true", help="skip the fused measurement")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the library's built-in launch choice")
     return p.parse_args()
@@ -76,17 +77,21 @@ def load_peaks():
 
 
 def profiled_traffic(tag: str):
-    """DRAM bytes per launch recorded in profiles/ for the current sources.
+    return profiled_value("traffic_bytes_per_launch", tag)
 
-    A summary line reads `traffic_bytes_per_launch[<tag>]: <bytes> digest <hex>`;
-    the value is used only if <hex> matches the library's current source digest
-    (a changed kernel invalidates its counters)."""
+
+def profiled_value(key: str, tag: str):
+    """A counter-derived number recorded in profiles/ for the current sources.
+
+    A summary line reads `<key>[<tag>]: <value> digest <hex>`; the value is
+    used only if <hex> matches the library's current source digest (a changed
+    kernel invalidates its counters)."""
     try:
         from paper_1206_1187_gb300 import _build
         digest = _build._inputs_digest([])[:16]
     except Exception:
         return None
-    pat = re.compile(r"traffic_bytes_per_launch\[" + re.escape(tag) +
+    pat = re.compile(re.escape(key) + r"\[" + re.escape(tag) +
                      r"\]:\s*([0-9.eE+]+)\s+digest\s+([0-9a-f]+)")
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
@@ -234,6 +239,49 @@ def measure_batched(rng, stream, achieved_gbs: float, steps: int):
             "vs_single_stream_gbs": gbs / achieved_gbs}
 
 
+def measure_fused(rng, stream, steps: int):
+    """The fused form: 2^36 FP64 variates in 2^20 blocks of 2^16 consumed on
+    the device (quarter-circle hits, exact per-block sum and sum of squares),
+    nothing stored."""
+    import torch
+    a, nblocks, length = 3 ** 33 + 100, 1 << 20, 1 << 16
+    total = torch.empty(1, dtype=torch.uint64, device="cuda")
+    hits = torch.empty(nblocks, dtype=torch.uint64, device="cuda")
+    s1 = torch.empty(nblocks, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(nblocks, dtype=torch.float64, device="cuda")
+
+    def once():
+        rng.consume_mc_into(a, nblocks, length, total, hits, s1, s2, stream=stream)
+
+    once()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    variates = nblocks * length
+    pi_est = 4.0 * int(total.view(torch.int64).item()) / (variates / 2)
+    out = {"workload": "2^36 FP64 variates, 2^20 blocks x 2^16 from a = 3^33+100, consumed "
+                       "on the device: quarter-circle hit count + exact per-block sum and sum "
+                       "of squares, nothing stored",
+           "launches": steps, "ms_per_launch": ms, "variates_per_s": variates / (ms / 1e3),
+           "pi_estimate": pi_est}
+    ipv = profiled_value("inst_per_variate", "mc_2e36")
+    if ipv is not None:  # integer-issue roofline: 4 schedulers x 32 lanes per SM per clock
+        clk = 2.07e9
+        peak = 152 * 4 * 32 * clk
+        achieved = ipv * variates / (ms / 1e3)
+        out["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                           "unit": "T thread-instructions/s", "frac": achieved / peak,
+                           "inst_per_variate": ipv,
+                           "peak_note": "152 SMs x 4 issue slots x 32 lanes x 2.07 GHz"}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -347,6 +395,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms_fill = e0.elapsed_time(e1) / fills
 
+    fused = None
+    if not args.no_fused and rank == 0:
+        fused = measure_fused(rng, stream, steps=3)
     batched = None
     if not args.no_batch and rank == 0:
         batched = measure_batched(rng, stream, achieved_gbs=8.0 * n / (ms / 1e3) / 1e9,
@@ -406,6 +457,8 @@ def run_ours(args):
         }
         if batched is not None:
             line["batched"] = batched
+        if fused is not None:
+            line["fused"] = fused
         if tuned is not None:
             ranked = sorted((t for t in tuned["table"] if t[1] > 0), key=lambda t: t[1])
             line["autotune"] = {"candidates": len(tuned["table"]), "n": tuned["n"],

@@ -193,6 +193,26 @@ rng_status rng_batch_info(const bcn_batch *b, uint64_t *total_elems, uint64_t *t
 /* Free the plan (its device table and graph).  NULL is a no-op. */
 rng_status rng_batch_destroy(bcn_batch *b);
 
+/* ---------------------------------------------------------- fused consumer */
+
+/* A Monte-Carlo consumer fused with generation: variates are used on the
+ * device and never stored (the use Sec. 2.2 of the paper anticipates).  The
+ * sequence seeded with start_index is cut into blocks of `len` variates (len
+ * even); block g = block0 + b (b < nblocks) covers variates g*len ..
+ * (g+1)*len-1.  Its variates are paired (v_2j, v_2j+1) = (x, y) and the call
+ * writes, for each b:
+ *   hits[b]  (nullable) = number of pairs with RN(RN(x*x) + RN(y*y)) <= 1,
+ *   sum[b]   = the exact sum of the block's variates, rounded to nearest even,
+ *   sumsq[b] = the exact sum of RN(v*v) over the block, rounded likewise,
+ * and *hits_total = the hit count over all nblocks blocks (the call zeroes it
+ * first).  All outputs are caller-owned device arrays, 8-byte aligned.
+ * Results are exact (integer arithmetic on the 2^-105 and 2^-157 grids), so
+ * they do not depend on the launch shape.  Asynchronous on `cuda_stream`.
+ * tune: only `block` (multiple of 32, <= 256) and `skip` are read. */
+rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblocks, uint64_t len,
+                          uint64_t *hits_total, uint64_t *hits, double *sum, double *sumsq,
+                          void *cuda_stream, const rng_tune *tune);
+
 /* -------------------------------------------------------------- autotune */
 
 /* Time each of the `ncand` candidate tunings of a bulk call (n elements of

@@ -90,6 +90,7 @@ def _load() -> ctypes.CDLL:
         "rng_batch_info": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                             ctypes.POINTER(u64), tp], i32),
         "rng_batch_destroy": ([vp], i32),
+        "rng_consume_mc": ([u64, u64, u64, u64, vp, vp, vp, vp, vp, tp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -248,6 +249,33 @@ def tune_dict(t: Tune) -> dict:
     return {"step": inv(STEP, t.step), "conv": inv(CONV, t.conv),
             "layout": inv(LAYOUT, t.layout), "skip": inv(SKIP, t.skip),
             "depth": t.depth, "block": t.block, "grid": t.grid}
+
+
+def consume_mc(start_index: int, nblocks: int, length: int, block0: int = 0,
+               per_block_hits: bool = True, tune=None, stream=None):
+    """Fused Monte-Carlo consumer (no variates stored).  Returns
+    (hits_total[1], hits[nblocks] or None, sum[nblocks], sumsq[nblocks]) as
+    CUDA tensors, filled asynchronously on the stream."""
+    total = torch.empty(1, dtype=torch.uint64, device="cuda")
+    hits = torch.empty(nblocks, dtype=torch.uint64, device="cuda") if per_block_hits else None
+    s1 = torch.empty(nblocks, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(nblocks, dtype=torch.float64, device="cuda")
+    _check(lib.rng_consume_mc(start_index, block0, nblocks, length,
+                              ctypes.c_void_p(total.data_ptr()),
+                              ctypes.c_void_p(hits.data_ptr()) if hits is not None else None,
+                              ctypes.c_void_p(s1.data_ptr()), ctypes.c_void_p(s2.data_ptr()),
+                              ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
+    return total, hits, s1, s2
+
+
+def consume_mc_into(start_index: int, nblocks: int, length: int, total, hits, s1, s2,
+                    block0: int = 0, tune=None, stream=None) -> None:
+    """consume_mc into caller-provided CUDA tensors (hits may be None)."""
+    _check(lib.rng_consume_mc(start_index, block0, nblocks, length,
+                              ctypes.c_void_p(total.data_ptr()),
+                              ctypes.c_void_p(hits.data_ptr()) if hits is not None else None,
+                              ctypes.c_void_p(s1.data_ptr()), ctypes.c_void_p(s2.data_ptr()),
+                              ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
 
 
 class Batch:

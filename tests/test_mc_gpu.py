@@ -1,0 +1,79 @@
+"""GPU parity of the fused Monte-Carlo consumer against the oracle.
+
+Per block: the hit count is an integer, and sum / sum of squares are exactly
+rounded sums, so all three must match the oracle bit for bit for any launch
+shape.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+M = 3 ** 33
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1206_1187_gb300 import rng
+    return rng
+
+
+def _run(R, a, nblocks, length, block0=0, tune=None):
+    import torch
+    total, hits, s1, s2 = R.consume_mc(a, nblocks, length, block0=block0, tune=tune)
+    torch.cuda.synchronize()
+    return (int(total.cpu().view(torch.int64)[0]), hits.view(torch.int64).cpu().numpy(),
+            s1.cpu().numpy(), s2.cpu().numpy())
+
+
+@pytest.mark.parametrize("length", [2, 4, 62, 64, 66, 1000, 4096])
+def test_small_blocks_match_the_oracle(R, oracle_mod, length):
+    a = M + 100
+    nblocks = 37
+    total, hits, s1, s2 = _run(R, a, nblocks, length)
+    oh, o1, o2 = oracle_mod.mc(a, length, np.arange(nblocks))
+    assert np.array_equal(hits, oh.astype(np.int64))
+    assert np.array_equal(s1.view(np.int64), o1.view(np.int64))
+    assert np.array_equal(s2.view(np.int64), o2.view(np.int64))
+    assert total == int(oh.sum())
+
+
+def test_block_offset_and_launch_shape(R, oracle_mod):
+    a, length = 2 ** 53, 2048
+    block0 = 10 ** 9 + 7
+    ref = _run(R, a, 64, length, block0=block0)
+    for block in (32, 64, 256):
+        got = _run(R, a, 64, length, block0=block0, tune=R.make_tune(block=block))
+        assert got[0] == ref[0]
+        for x, y in zip(got[1:], ref[1:]):
+            assert np.array_equal(np.asarray(x).view(np.int64), np.asarray(y).view(np.int64))
+    oh, o1, o2 = oracle_mod.mc(a, length, block0 + np.arange(64))
+    assert np.array_equal(ref[1], oh.astype(np.int64))
+    assert np.array_equal(ref[2].view(np.int64), o1.view(np.int64))
+    assert np.array_equal(ref[3].view(np.int64), o2.view(np.int64))
+
+
+def test_bad_arguments(R):
+    with pytest.raises(R.RNGError):
+        R.consume_mc(M + 100, 4, 7)      # odd length
+    with pytest.raises(R.RNGError):
+        R.consume_mc(M + 99, 4, 8)       # seed below 3^33+100
+
+
+@pytest.mark.slow
+def test_2_36_variates_subsample(R, oracle_mod):
+    """2^36 variates in 2^20 blocks of 2^16, consumed without being stored;
+    the 256 blocks b = 0 mod 4096 (2^24 variates) are checked against the
+    oracle, and the total against the per-block counts."""
+    a, nblocks, length = M + 100, 1 << 20, 1 << 16
+    total, hits, s1, s2 = _run(R, a, nblocks, length)
+    assert total == int(hits.sum())
+    sub = np.arange(0, nblocks, 4096)
+    oh, o1, o2 = oracle_mod.mc(a, length, sub)
+    assert np.array_equal(hits[sub], oh.astype(np.int64))
+    assert np.array_equal(s1[sub].view(np.int64), o1.view(np.int64))
+    assert np.array_equal(s2[sub].view(np.int64), o2.view(np.int64))
+    # pi/4 sanity on 2^35 pairs
+    assert abs(total / (nblocks * length / 2) - np.pi / 4) < 1e-4
