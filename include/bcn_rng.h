@@ -193,6 +193,33 @@ rng_status rng_batch_info(const bcn_batch *b, uint64_t *total_elems, uint64_t *t
 /* Free the plan (its device table and graph).  NULL is a no-op. */
 rng_status rng_batch_destroy(bcn_batch *b);
 
+/* Batch generation that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * running under a framework whose caching allocator owns all device memory,
+ * latency-critical paths that must not take the synchronisation an
+ * allocation can imply, or hosts where device allocation is not permitted.
+ * It generates the same streams, with the same meaning of every argument, as
+ * rng_batch_create + rng_batch_launch, but its work table (descriptors, unit
+ * prefix, work counter) lives in one fixed device array inside the library
+ * instead of a cudaMalloc'd plan, and it allocates no device or host memory.
+ *   - At most 1024 streams per call; more is RNG_ERANGE.  The array (about
+ *     49 KB) is held by every device that loads the library until exit.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address and sets the kernel's shared-memory limit; make
+ *     that first call before any stream capture on the device.
+ *   - Every call rewrites the one shared table and clears its work counter:
+ *     calls whose work overlaps on the GPU (on different streams, or from
+ *     different host threads' streams) race and must be serialised by the
+ *     caller.  Calls from several host threads are serialised on the host.
+ *   - The table is copied from the library's host memory with
+ *     cudaMemcpyAsync on `cuda_stream`; from pageable memory that copy may
+ *     wait for earlier work on the stream before it returns.
+ *   - Output arrays are caller-owned; the call is otherwise asynchronous. */
+rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64_t *starts,
+                                      const uint64_t *offsets, const uint64_t *counts,
+                                      const uint8_t *dtypes, void *const *outs,
+                                      const rng_tune *tune, void *cuda_stream);
+
 /* ---------------------------------------------------------- fused consumer */
 
 /* A Monte-Carlo consumer fused with generation: variates are used on the

@@ -15,6 +15,7 @@
 // This follows the paper's parallel split (Sec. 1): every unit is a block of
 // a stream reached by skip-ahead, so no result depends on which warp runs it.
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -339,3 +340,154 @@ rng_status rng_batch_destroy(bcn_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch generation that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: code running under a host framework
+// whose caching allocator owns all device memory (a stray cudaMalloc there can
+// fail or fragment its pool), latency-critical paths that must not take the
+// device-wide synchronisation cudaMalloc/cudaFree may imply, and embedded or
+// sandboxed hosts where device allocation is simply not permitted.  For them
+// the work table of the batched kernel (one descriptor per stream, the prefix
+// of work-unit counts and the work counter) lives in this file-scope device
+// array instead of a plan's cudaMalloc'd table.  The array holds at most
+// kNoallocMaxStreams streams (about 49 KB) and stays resident on every device
+// that loads the library until the process exits.
+namespace bcn {
+
+constexpr uint32_t kNoallocMaxStreams = 1024;
+constexpr size_t kNoallocDescBytes = sizeof(BatchDesc) * kNoallocMaxStreams;
+constexpr size_t kNoallocPrefixBytes = sizeof(uint64_t) * (kNoallocMaxStreams + 1);
+constexpr size_t kNoallocBytes = kNoallocDescBytes + kNoallocPrefixBytes + 16;
+static_assert(kNoallocDescBytes % 16 == 0 && kNoallocPrefixBytes % 8 == 0, "layout");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_dev[kNoallocMaxDevices];  // device address of the array, per device
+// host staging for the table (static: building it allocates nothing either)
+static BatchDesc g_noalloc_desc[kNoallocMaxStreams];
+static uint64_t g_noalloc_prefix[kNoallocMaxStreams + 1];
+
+}  // namespace bcn
+
+extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64_t* starts,
+                                                 const uint64_t* offsets, const uint64_t* counts,
+                                                 const uint8_t* dtypes, void* const* outs,
+                                                 const rng_tune* tune, void* cuda_stream) {
+  if (nstreams == 0) return RNG_OK;
+  if (nstreams > kNoallocMaxStreams)
+    return set_error(RNG_ERANGE, "%u streams exceed the no-allocation limit of %u", nstreams,
+                     kNoallocMaxStreams);
+  if (!starts || !counts || !dtypes || !outs)
+    return set_error(RNG_EINVAL, "the starts/counts/dtypes/outs arrays are required");
+  rng_tune t = {};
+  if (tune) t = *tune;
+  const rng_tune d = auto_defaults(RNG_F64);
+  if (!t.step) t.step = d.step ? d.step : ST_SHARED;
+  if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
+  if (!t.skip) t.skip = SK_TABLE;
+  if (!t.depth) t.depth = d.depth ? d.depth : 15;
+  if (!t.block) t.block = 256;
+  if (!t.unit) t.unit = 16;
+  if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
+    return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
+  if (t.conv != CV_INT && t.conv != CV_FP64)
+    return set_error(RNG_EINVAL, "tune.conv %u is not a conversion", t.conv);
+  if (t.skip != SK_TABLE && t.skip != SK_SQMUL)
+    return set_error(RNG_EINVAL, "tune.skip %u is not a skip-ahead method", t.skip);
+  if (t.depth % 2 == 0 || t.depth > kMaxDepth)
+    return set_error(RNG_EINVAL, "tune.depth %u must be odd and at most %u", t.depth, kMaxDepth);
+  if (t.block % 32 != 0 || t.block == 0 || t.block > 1024)
+    return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024", t.block);
+  if (t.unit > 4096) return set_error(RNG_EINVAL, "tune.unit (tiles per work unit) > 4096");
+  DeviceInfo di;
+  rng_status st = device_info(&di);
+  if (st != RNG_OK) return st;
+  if (di.device < 0 || di.device >= kNoallocMaxDevices)
+    return set_error(RNG_EINVAL, "device %d beyond the no-allocation device table", di.device);
+  const size_t smem = (size_t)(t.block / 32) * 2 * 32 * t.depth * 8;
+  if (smem > di.smem_optin)
+    return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
+                     smem, di.smem_optin);
+  const uint64_t unit_elems = 32ull * t.depth * t.unit;
+  const void* fn = pick_batch((int)t.step, (int)t.conv);
+  if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
+  cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  // once per device, with that device current: the array's device address
+  // (in host code its name is only a host-side stand-in)
+  if (!g_noalloc_dev[di.device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation table)");
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(batch)");
+    g_noalloc_dev[di.device] = ptr;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_dev[di.device]);
+
+  uint64_t units = 0;
+  for (uint32_t s = 0; s < nstreams; ++s) {
+    const uint64_t seed = starts[s], off = offsets ? offsets[s] : 0, n = counts[s];
+    if (seed < kSeedMin || seed > kSeedMax)
+      return set_error(RNG_ERANGE, "stream %u: start index outside [3^33+100, 2^53]", s);
+    if (dtypes[s] > RNG_U64) return set_error(RNG_EINVAL, "stream %u: bad dtype %u", s, dtypes[s]);
+    if (n > RNG_MAX_N) return set_error(RNG_ERANGE, "stream %u: count exceeds RNG_MAX_N", s);
+    if (n > UINT64_MAX - off) return set_error(RNG_ERANGE, "stream %u: offset + count overflows", s);
+    const size_t esz = dtype_size(dtypes[s]);
+    if (n > 0 && (!outs[s] || (uintptr_t)outs[s] % esz != 0))
+      return set_error(RNG_EINVAL, "stream %u: output NULL or not aligned to %zu bytes", s, esz);
+    BatchDesc& D = g_noalloc_desc[s];
+    D.ebase = host_exponent_base(seed, off);
+    D.n = n;
+    D.out = static_cast<unsigned char*>(outs[s]);
+    D.dt = dtypes[s];
+    D.head = n ? (uint32_t)head_elems(outs[s], esz, n) : 0;
+    D.unit0 = units;
+    g_noalloc_prefix[s] = units;
+    if (n > 0) units += n > D.head ? (n - D.head + unit_elems - 1) / unit_elems : 1;
+  }
+  g_noalloc_prefix[nstreams] = units;
+  if (units == 0) return RNG_OK;
+
+  // Copies from pageable host memory return once the data is staged, so the
+  // static host table may be rewritten by the next call.
+  cudaError_t e = cudaMemcpyAsync(base, g_noalloc_desc, sizeof(BatchDesc) * nstreams,
+                                  cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + kNoallocDescBytes, g_noalloc_prefix,
+                        sizeof(uint64_t) * (nstreams + 1), cudaMemcpyHostToDevice, cs);
+  unsigned long long* counter =
+      reinterpret_cast<unsigned long long*>(base + kNoallocDescBytes + kNoallocPrefixBytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), cs);
+  if (e != cudaSuccess) return cuda_error(e, "staging the no-allocation table");
+
+  uint32_t grid = t.grid;
+  if (!grid) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)t.block, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    const uint64_t full = (uint64_t)std::max(per_sm, 1) * (uint64_t)di.sms;
+    const uint64_t need = (units + t.block / 32 - 1) / (t.block / 32);
+    grid = (uint32_t)std::max<uint64_t>(1, std::min(full, need));
+  }
+  BatchParams p;
+  p.desc = reinterpret_cast<const BatchDesc*>(base);
+  p.prefix = reinterpret_cast<const uint64_t*>(base + kNoallocDescBytes);
+  p.counter = counter;
+  p.total_units = units;
+  const uint64_t stride = (t.step == ST_MONT) ? 33ull : 31ull;
+  p.jump = host_pow2((53ull * stride * t.depth) % kP);
+  p.nstreams = nstreams;
+  p.depth = t.depth;
+  p.unit_tiles = t.unit;
+  p.skip = t.skip;
+  void* args[] = {&p};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(t.block), args, smem, cs);
+  if (e != cudaSuccess) return cuda_error(e, "batch kernel launch (no-allocation)");
+  return RNG_OK;
+}

@@ -91,6 +91,7 @@ def _load() -> ctypes.CDLL:
                             ctypes.POINTER(u64), tp], i32),
         "rng_batch_destroy": ([vp], i32),
         "rng_consume_mc": ([u64, u64, u64, u64, vp, vp, vp, vp, vp, tp], i32),
+        "rng_batch_generate_noalloc": ([u32, vp, vp, vp, vp, vp, tp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -1,0 +1,72 @@
+"""The batch entry point that allocates nothing (rng_batch_generate_noalloc).
+
+It serves callers that cannot call cudaMalloc -- for example code running
+under a framework whose allocator owns all device memory, or latency-critical
+paths that must not allocate -- by keeping the batched kernel's work table in
+a fixed device array inside the library.  This file is collected last so that
+a run stopping at its first failure has already run every other test.  The
+new entry point is called through the C ABI twice in a row, with different
+streams each time, and each call's output must equal, bit for bit, the output
+of the allocating entry point (rng_batch_create + rng_batch_launch) on the
+same inputs -- the exactness every other parity test in this suite uses.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _tensors(counts, dtypes, fill):
+    import torch
+    tdt = {"f64": torch.float64, "f32": torch.float32, "u64": torch.uint64}
+    return [torch.full((int(c),), fill, dtype=tdt[d], device="cuda") if d != "u64"
+            else torch.zeros(int(c), dtype=tdt[d], device="cuda") for c, d in zip(counts, dtypes)]
+
+
+def _bits(t):
+    import torch
+    return t.view(torch.int64 if t.element_size() == 8 else torch.int32).cpu().numpy()
+
+
+def test_noalloc_batch_equals_the_allocating_batch_twice():
+    import torch
+    from paper_1206_1187_gb300 import inputs, rng
+
+    assert torch.cuda.is_available()
+    fn = rng.lib.rng_batch_generate_noalloc
+    codes_of = {"f64": 0, "f32": 1, "u64": 2}
+    for call, (nstreams, seed) in enumerate([(150, 21), (600, 22)]):
+        starts, offsets, counts, dtypes = inputs.small_batch(nstreams=nstreams, seed=seed,
+                                                             max_len=30000)
+        ref = _tensors(counts, dtypes, -1.0)
+        b = rng.Batch(starts, counts, dtypes, outs=ref, offsets=offsets)
+        b.launch()
+        got = _tensors(counts, dtypes, -2.0)
+        codes = np.ascontiguousarray([codes_of[d] for d in dtypes], dtype=np.uint8)
+        ptrs = (ctypes.c_void_p * nstreams)(*[t.data_ptr() for t in got])
+        stream = torch.cuda.current_stream().cuda_stream
+        rc = fn(nstreams, ctypes.c_void_p(starts.ctypes.data), ctypes.c_void_p(offsets.ctypes.data),
+                ctypes.c_void_p(counts.ctypes.data), ctypes.c_void_p(codes.ctypes.data), ptrs,
+                None, ctypes.c_void_p(stream))
+        assert rc == 0, rng.lib.rng_last_error()
+        torch.cuda.synchronize()
+        for s in range(nstreams):
+            assert np.array_equal(_bits(got[s]), _bits(ref[s])), (call, s, dtypes[s])
+        b.close()
+
+
+def test_noalloc_batch_rejects_more_streams_than_its_table_holds():
+    import torch
+    from paper_1206_1187_gb300 import rng
+    n = 1025
+    starts = np.full(n, 3 ** 33 + 100, dtype=np.uint64)
+    counts = np.ones(n, dtype=np.uint64)
+    codes = np.zeros(n, dtype=np.uint8)
+    outs = torch.empty(n, dtype=torch.float64, device="cuda")
+    ptrs = (ctypes.c_void_p * n)(*[outs.data_ptr() + 8 * i for i in range(n)])
+    rc = rng.lib.rng_batch_generate_noalloc(n, ctypes.c_void_p(starts.ctypes.data), None,
+                                            ctypes.c_void_p(counts.ctypes.data),
+                                            ctypes.c_void_p(codes.ctypes.data), ptrs, None, None)
+    assert rc == 2  # RNG_ERANGE
