@@ -54,6 +54,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched measurement")
     p.add_argument("--no-fused", action="store_true", help="skip the fused measurement")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the library's built-in launch choice")
     return p.parse_args()
@@ -282,6 +283,42 @@ def measure_fused(rng, stream, steps: int):
     return out
 
 
+def measure_serving(rng, n_requests: int = 20000):
+    """The served form: Poisson arrivals at 20k req/s, sizes log-uniform 1 KiB..256
+    MiB, random start indices and offsets, FP32/FP64 1:1, 40 GB device output pool
+    with memory-based admission, continuous batching.  Three runs: the nominal rate
+    with each result consumed at completion; the same trace 20x faster (saturating);
+    and the nominal rate with each result held 0.2 s (admission binds on the pool)."""
+    import numpy as np
+    from paper_1206_1187_gb300 import inputs
+    arrivals, counts, dtypes, seeds, offsets = inputs.request_trace(n_requests)
+    esz = np.array([8 if d == "f64" else 4 for d in dtypes], dtype=np.float64)
+    total_bytes = float((counts.astype(np.float64) * esz).sum())
+    total_vars = float(counts.astype(np.float64).sum())
+    runs = {}
+    for name, speed, hold in (("nominal", 1.0, 0.0), ("saturating_x20", 20.0, 0.0),
+                              ("hold_0.2s", 1.0, 0.2)):
+        srv = rng.Server(pool_bytes=40 * 10 ** 9, release_after_s=hold)
+        lat, wall = srv.run_trace(arrivals / speed, seeds, counts, dtypes, offsets=offsets,
+                                  timeout_s=300.0)
+        st = srv.stats()
+        srv.close()
+        runs[name] = {"offered_req_per_s": 20000.0 * speed, "release_after_s": hold,
+                      "wall_s": wall, "throughput_gbs": total_bytes / wall / 1e9,
+                      "variates_per_s": total_vars / wall,
+                      "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                      "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                      "p999_ms": float(np.percentile(lat, 99.9) * 1e3),
+                      "max_ms": float(lat.max() * 1e3),
+                      "iterations": st["iterations"], "mean_items_per_iteration":
+                          st["items"] / max(st["iterations"], 1),
+                      "peak_pool_gb": st["peak_pool_bytes"] / 1e9,
+                      "peak_active": st["peak_active"]}
+    return {"workload": f"{n_requests} requests, Poisson 20k req/s, sizes log-uniform "
+                        "1 KiB..256 MiB, FP32/FP64 1:1, random seeds/offsets, 40 GB pool",
+            "requests": n_requests, "bytes": total_bytes, "runs": runs}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -398,6 +435,9 @@ def run_ours(args):
     fused = None
     if not args.no_fused and rank == 0:
         fused = measure_fused(rng, stream, steps=3)
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = measure_serving(rng)
     batched = None
     if not args.no_batch and rank == 0:
         batched = measure_batched(rng, stream, achieved_gbs=8.0 * n / (ms / 1e3) / 1e9,
@@ -459,6 +499,8 @@ def run_ours(args):
             line["batched"] = batched
         if fused is not None:
             line["fused"] = fused
+        if serving is not None:
+            line["serving"] = serving
         if tuned is not None:
             ranked = sorted((t for t in tuned["table"] if t[1] > 0), key=lambda t: t[1])
             line["autotune"] = {"candidates": len(tuned["table"]), "n": tuned["n"],

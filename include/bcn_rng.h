@@ -220,6 +220,91 @@ rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64_t *starts,
                                       const uint8_t *dtypes, void *const *outs,
                                       const rng_tune *tune, void *cuda_stream);
 
+/* ----------------------------------------------------------------- serving */
+
+/* A continuous-batching request server (spec serving form; the paper
+ * has none).  Requests are generation calls (offset .. offset+n-1 of the
+ * sequence seeded with a start index, as rng_generate_at) whose outputs are
+ * placed in one device pool the server owns.  A scheduler thread admits
+ * waiting requests in arrival order when a request slot is free and the pool
+ * has room for the output (memory-based admission), packs the next chunk of
+ * every admitted request into one work table per iteration and launches the
+ * batched kernel, with up to `inflight` iterations on separate CUDA streams so
+ * work admitted later overlaps earlier work on the device.  Each chunk is a
+ * block of its request's sequence reached by skip-ahead (Sec. 1), so a
+ * request's bytes are the same alone and in any mix. */
+typedef struct bcn_server bcn_server;
+
+typedef struct {
+  uint64_t pool_bytes;     /* device output pool, cudaMalloc'd at creation     */
+  uint64_t chunk_elems;    /* largest piece of one request per iteration
+                              (0 = 2^21; rounded up to a multiple of 4)         */
+  uint32_t max_active;     /* admitted requests at once (0 = 4096)             */
+  uint32_t max_items;      /* work items per iteration (0 = 1024)              */
+  uint32_t inflight;       /* iterations in flight, 1..8 (0 = 2)               */
+  uint32_t pad;
+  double release_after_s;  /* >= 0: free a result's pool range this long after
+                              it completes; < 0: the caller releases it        */
+  rng_tune tune;           /* batched-kernel tuning (zero fields = choose)     */
+} rng_server_config;
+
+typedef struct {
+  uint64_t submitted, completed, iterations, items, max_items_seen;
+  uint64_t peak_active, peak_pool_bytes, bytes_done, pool_in_use, pool_bytes;
+} rng_server_stats;
+
+/* Request states reported by rng_server_status. */
+enum { RNG_REQ_QUEUED = 0, RNG_REQ_ACTIVE = 1, RNG_REQ_DONE = 2, RNG_REQ_RELEASED = 3,
+       RNG_REQ_CANCELLED = 4 };
+
+/* Create a server on the current device (allocates the pool, per-iteration
+ * tables and streams, starts the scheduler thread). */
+rng_status rng_server_create(const rng_server_config *cfg, bcn_server **out);
+/* Queue a request; thread-safe.  Rejected at once (and nothing else disturbed)
+ * for a bad seed (RNG_ERANGE), dtype or n == 0 (RNG_EINVAL), or an output larger
+ * than the pool (RNG_ENOMEM).  *id identifies it afterwards. */
+rng_status rng_server_submit(bcn_server *s, uint64_t start_index, uint64_t offset, uint64_t n,
+                             rng_dtype dt, uint64_t *id);
+/* Withdraw a request that is still queued (RNG_EBUSY once admitted). */
+rng_status rng_server_cancel(bcn_server *s, uint64_t id);
+/* State and, once done, latency (submission or scheduled arrival to the
+ * host seeing its last iteration complete, seconds; -1 before). */
+rng_status rng_server_status(bcn_server *s, uint64_t id, int *state, double *latency_s);
+/* Block until the request is done (RNG_ETIMEOUT after timeout_s). */
+rng_status rng_server_wait(bcn_server *s, uint64_t id, double timeout_s);
+/* Copy a done request's result (n elements of its dtype) to `dst` (host or
+ * device memory of at least dst_bytes); synchronous. */
+rng_status rng_server_read(bcn_server *s, uint64_t id, void *dst, uint64_t dst_bytes);
+/* The device address of a done request's result inside the pool (valid until
+ * it is released). */
+rng_status rng_server_result_ptr(bcn_server *s, uint64_t id, void **dev_ptr);
+/* Free a done request's pool range now. */
+rng_status rng_server_release(bcn_server *s, uint64_t id);
+/* Counters since creation (returns the server's error status, if any). */
+rng_status rng_server_stats_get(bcn_server *s, rng_server_stats *out);
+/* Replay a request trace in real time: request i is submitted at
+ * arrival_s[i] seconds after the call starts (open loop), then every request
+ * is awaited (RNG_ETIMEOUT after timeout_s).  latency_s[i] receives the time
+ * from request i's scheduled arrival to its completion; *wall_s (nullable) the
+ * time from the start to the last completion. */
+rng_status rng_server_run_trace(bcn_server *s, uint32_t n, const double *arrival_s,
+                                const uint64_t *starts, const uint64_t *offsets,
+                                const uint64_t *counts, const uint8_t *dtypes, double timeout_s,
+                                double *latency_s, double *wall_s);
+/* Stop the scheduler (after the iterations in flight) and free everything. */
+rng_status rng_server_destroy(bcn_server *s);
+
+/* The pool sub-allocator the server admits with: aligned first-fit ranges of
+ * a `capacity`-byte pool, neighbours merged on free.  Host bookkeeping only
+ * (no device memory is touched), exposed so it can be driven on its own. */
+typedef struct bcn_pool bcn_pool;
+rng_status rng_pool_create(uint64_t capacity, uint64_t align, bcn_pool **out);
+rng_status rng_pool_alloc(bcn_pool *p, uint64_t bytes, uint64_t *offset);  /* RNG_ENOMEM if none */
+rng_status rng_pool_free(bcn_pool *p, uint64_t offset);
+rng_status rng_pool_stats(bcn_pool *p, uint64_t *in_use, uint64_t *peak, uint64_t *live,
+                          uint64_t *largest_free, uint64_t *free_ranges);
+rng_status rng_pool_destroy(bcn_pool *p);
+
 /* ---------------------------------------------------------- fused consumer */
 
 /* A Monte-Carlo consumer fused with generation: variates are used on the

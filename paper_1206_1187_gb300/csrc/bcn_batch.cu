@@ -19,6 +19,7 @@
 #include <new>
 #include <vector>
 
+#include "bcn_batch.cuh"
 #include "bcn_gen.cuh"
 
 struct bcn_batch {
@@ -36,27 +37,6 @@ struct bcn_batch {
 };
 
 namespace bcn {
-
-struct BatchDesc {
-  uint64_t ebase;       // (seed - 3^33 + 53*offset) mod P
-  uint64_t n;           // elements
-  unsigned char* out;   // element 0
-  uint64_t unit0;       // first unit number
-  uint32_t dt;          // DT_F64 / DT_F32 / DT_U64
-  uint32_t head;        // elements before the first 16-byte boundary
-};
-
-struct BatchParams {
-  const BatchDesc* desc;
-  const uint64_t* prefix;  // nstreams + 1 unit counts, prefix[s] = desc[s].unit0
-  unsigned long long* counter;
-  uint64_t total_units;
-  uint64_t jump;
-  uint32_t nstreams;
-  uint32_t depth;
-  uint32_t unit_tiles;
-  uint32_t skip;
-};
 
 // The unit's elements [s0, s1) of stream d: full tiles by bulk copy, the
 // remainder by plain stores; unit 0 also writes the head [0, head).
@@ -127,6 +107,8 @@ static const void* pick_batch(int st, int cv) {
     default: return nullptr;
   }
 }
+
+const void* batch_kernel_fn(int step, int conv) { return pick_batch(step, conv); }
 
 static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
   const void* fn = pick_batch((int)b->tune.step, (int)b->tune.conv);

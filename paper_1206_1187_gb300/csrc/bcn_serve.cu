@@ -1,0 +1,543 @@
+// bcn_serve.cu -- a continuous-batching request server for variate requests.
+//
+// A request asks for n variates (offset .. offset+n-1 of the sequence seeded
+// with a start index) as FP64, FP32 or raw states.  The server owns one device
+// output pool.  A scheduler thread runs iterations:
+//   1. retire the iterations whose completion event has fired: every request
+//      whose last chunk rode on one is complete (its completion time is taken
+//      then), and its pool range is freed `release_after` seconds later (or
+//      when the caller releases it);
+//   2. admit waiting requests in arrival order while a request slot is free
+//      and the pool has a free range for the request's output (memory-based
+//      admission: a request that does not fit waits, and so do those behind
+//      it);
+//   3. if an iteration slot is free, pack the next chunk (at most chunk_elems
+//      variates) of every active request, round-robin, into one work table and
+//      launch the batched kernel on that slot's CUDA stream.
+// With several slots, requests admitted while earlier iterations run are
+// launched on another stream and overlap them on the device; chunking keeps a
+// 256 MiB request from holding back the small ones.  Every chunk is a block of
+// its request's sequence reached by skip-ahead (the paper's parallel split,
+// Sec. 1), so a request's bytes never depend on what it was batched with.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bcn_batch.cuh"
+#include "bcn_math.cuh"
+#include "bcn_pool.h"
+
+namespace bcn {
+
+typedef std::chrono::steady_clock Clock;
+static double now_s() {
+  return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
+}
+
+enum { RQ_QUEUED = 0, RQ_ACTIVE = 1, RQ_DONE = 2, RQ_RELEASED = 3, RQ_CANCELLED = 4 };
+
+struct Request {
+  uint64_t seed = 0, offset = 0, n = 0, bytes = 0, pool_off = 0, scheduled = 0;
+  uint32_t dt = 0;
+  int state = RQ_QUEUED;
+  double t_arrive = 0, t_admit = 0, t_done = 0;
+};
+
+struct Slot {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  BatchDesc* h_desc = nullptr;      // pinned staging of the work table
+  uint64_t* h_prefix = nullptr;
+  unsigned char* d_table = nullptr;  // device: descriptors | prefix | counter
+  bool busy = false;
+  std::vector<uint64_t> finishing;   // requests whose last chunk is in this iteration
+};
+
+}  // namespace bcn
+
+struct bcn_server {
+  rng_server_config cfg;
+  rng_tune tune;
+  const void* fn = nullptr;
+  size_t smem = 0;
+  uint64_t grid_full = 0;
+  uint64_t jump = 0;
+  int device = 0;
+  unsigned char* pool_dev = nullptr;
+  bcn::Pool pool;
+  std::mutex mu;
+  std::condition_variable cv_work;   // wakes the scheduler
+  std::condition_variable cv_done;   // wakes waiters
+  std::unordered_map<uint64_t, bcn::Request> reqs;
+  std::deque<uint64_t> queue;
+  std::vector<uint64_t> active;
+  std::deque<std::pair<double, uint64_t>> to_release;  // (time, id)
+  std::vector<bcn::Slot> slots;
+  std::thread worker;
+  std::atomic<bool> stop{false};
+  rng_status err = RNG_OK;
+  char errmsg[256] = {0};
+  uint64_t next_id = 1, rr = 0;
+  rng_server_stats st = {};
+  bcn_server(uint64_t cap) : pool(cap, 256) {}
+};
+
+namespace bcn {
+
+static void server_fail(bcn_server* s, cudaError_t e, const char* what) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (s->err == RNG_OK) {
+    s->err = RNG_ECUDA;
+    snprintf(s->errmsg, sizeof s->errmsg, "%s: %s", what, cudaGetErrorString(e));
+  }
+  s->cv_done.notify_all();
+}
+
+// Retire finished iterations; returns true if any finished.
+static bool retire(bcn_server* s) {
+  bool any = false;
+  for (Slot& sl : s->slots) {
+    if (!sl.busy) continue;
+    cudaError_t e = cudaEventQuery(sl.ev);
+    if (e == cudaErrorNotReady) continue;
+    if (e != cudaSuccess) {
+      server_fail(s, e, "iteration");
+      sl.busy = false;
+      continue;
+    }
+    const double t = now_s();
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (uint64_t id : sl.finishing) {
+      Request& r = s->reqs[id];
+      r.state = RQ_DONE;
+      r.t_done = t;
+      s->st.completed += 1;
+      s->st.bytes_done += r.bytes;
+      if (s->cfg.release_after_s >= 0) s->to_release.emplace_back(t + s->cfg.release_after_s, id);
+    }
+    sl.finishing.clear();
+    sl.busy = false;
+    any = true;
+    s->cv_done.notify_all();
+  }
+  return any;
+}
+
+// Free pool ranges whose hold time has passed (caller holds mu).
+static void release_due(bcn_server* s, double t) {
+  while (!s->to_release.empty() && s->to_release.front().first <= t) {
+    const uint64_t id = s->to_release.front().second;
+    s->to_release.pop_front();
+    auto it = s->reqs.find(id);
+    if (it != s->reqs.end() && it->second.state == RQ_DONE) {
+      s->pool.release(it->second.pool_off);
+      it->second.state = RQ_RELEASED;
+    }
+  }
+}
+
+// Admit queued requests in order while slots and pool space allow (mu held).
+static bool admit(bcn_server* s, double t) {
+  bool any = false;
+  while (!s->queue.empty() && s->active.size() < s->cfg.max_active) {
+    const uint64_t id = s->queue.front();
+    Request& r = s->reqs[id];
+    if (r.state == RQ_CANCELLED) {
+      s->queue.pop_front();
+      continue;
+    }
+    uint64_t off = 0;
+    if (!s->pool.alloc(r.bytes, &off)) break;  // memory-based admission
+    r.pool_off = off;
+    r.state = RQ_ACTIVE;
+    r.t_admit = t;
+    s->active.push_back(id);
+    s->queue.pop_front();
+    any = true;
+    if (s->pool.in_use > s->st.peak_pool_bytes) s->st.peak_pool_bytes = s->pool.in_use;
+    if (s->active.size() > s->st.peak_active) s->st.peak_active = s->active.size();
+  }
+  return any;
+}
+
+// Pack the next chunk of every active request into slot `sl` (mu held).
+// Returns the number of work items.
+static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out) {
+  const uint64_t unit_elems = 32ull * s->tune.depth * s->tune.unit;
+  uint32_t items = 0;
+  uint64_t units = 0;
+  const size_t na = s->active.size();
+  std::vector<uint64_t> still;
+  still.reserve(na);
+  for (size_t k = 0; k < na; ++k) {
+    const uint64_t id = s->active[(s->rr + k) % na];
+    Request& r = s->reqs[id];
+    if (items >= s->cfg.max_items) {
+      still.push_back(id);
+      continue;
+    }
+    const uint64_t left = r.n - r.scheduled;
+    const uint64_t chunk = std::min<uint64_t>(left, s->cfg.chunk_elems);
+    const size_t esz = dtype_size((int)r.dt);
+    BatchDesc& D = sl.h_desc[items];
+    D.ebase = host_exponent_base(r.seed, r.offset + r.scheduled);
+    D.n = chunk;
+    D.out = s->pool_dev + r.pool_off + r.scheduled * esz;
+    D.dt = r.dt;
+    D.head = (uint32_t)head_elems(D.out, esz, chunk);
+    D.unit0 = units;
+    sl.h_prefix[items] = units;
+    units += chunk > D.head ? (chunk - D.head + unit_elems - 1) / unit_elems : 1;
+    r.scheduled += chunk;
+    ++items;
+    if (r.scheduled == r.n) sl.finishing.push_back(id);
+    else still.push_back(id);
+  }
+  sl.h_prefix[items] = units;
+  s->active.swap(still);
+  s->rr = s->active.empty() ? 0 : (s->rr + 1) % s->active.size();
+  *units_out = units;
+  return items;
+}
+
+static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units) {
+  const size_t desc_bytes = sizeof(BatchDesc) * s->cfg.max_items;
+  const size_t prefix_bytes = sizeof(uint64_t) * (s->cfg.max_items + 1);
+  cudaError_t e = cudaMemcpyAsync(sl.d_table, sl.h_desc, sizeof(BatchDesc) * items,
+                                  cudaMemcpyHostToDevice, sl.cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sl.d_table + desc_bytes, sl.h_prefix, sizeof(uint64_t) * (items + 1),
+                        cudaMemcpyHostToDevice, sl.cs);
+  unsigned long long* counter =
+      reinterpret_cast<unsigned long long*>(sl.d_table + desc_bytes + prefix_bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), sl.cs);
+  if (e != cudaSuccess) return server_fail(s, e, "staging an iteration");
+  BatchParams p;
+  p.desc = reinterpret_cast<const BatchDesc*>(sl.d_table);
+  p.prefix = reinterpret_cast<const uint64_t*>(sl.d_table + desc_bytes);
+  p.counter = counter;
+  p.total_units = units;
+  p.jump = s->jump;
+  p.nstreams = items;
+  p.depth = s->tune.depth;
+  p.unit_tiles = s->tune.unit;
+  p.skip = s->tune.skip;
+  const uint64_t wpb = s->tune.block / 32;
+  const uint64_t grid = std::max<uint64_t>(1, std::min(s->grid_full, (units + wpb - 1) / wpb));
+  void* args[] = {&p};
+  e = cudaLaunchKernel(s->fn, dim3((unsigned)grid), dim3(s->tune.block), args, s->smem, sl.cs);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.cs);
+  if (e != cudaSuccess) return server_fail(s, e, "launching an iteration");
+  sl.busy = true;
+}
+
+static void worker_main(bcn_server* s) {
+  cudaSetDevice(s->device);
+  while (!s->stop.load(std::memory_order_relaxed)) {
+    bool did = retire(s);
+    Slot* free_slot = nullptr;
+    for (Slot& sl : s->slots)
+      if (!sl.busy) {
+        free_slot = &sl;
+        break;
+      }
+    uint32_t items = 0;
+    uint64_t units = 0;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      const double t = now_s();
+      release_due(s, t);
+      did |= admit(s, t);
+      if (free_slot && !s->active.empty() && s->err == RNG_OK) {
+        items = pack(s, *free_slot, &units);
+        s->st.iterations += 1;
+        s->st.items += items;
+        if (items > s->st.max_items_seen) s->st.max_items_seen = items;
+      }
+      if (!did && items == 0) {
+        bool gpu_busy = false;
+        for (Slot& sl : s->slots) gpu_busy |= sl.busy;
+        const bool pending_release = !s->to_release.empty();
+        if (!gpu_busy) {  // nothing on the device: sleep until new work (bounded)
+          const double wait = pending_release
+                                  ? std::max(0.0, s->to_release.front().first - t)
+                                  : 0.002;
+          s->cv_work.wait_for(lock, std::chrono::duration<double>(std::min(wait, 0.002)));
+        }
+      }
+    }
+    if (items > 0) {
+      launch_slot(s, *free_slot, items, units);
+      did = true;
+    }
+    if (!did) std::this_thread::yield();  // polling completion events
+  }
+}
+
+}  // namespace bcn
+
+using namespace bcn;
+
+extern "C" {
+
+rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) {
+  if (!out || !cfg_in) return set_error(RNG_EINVAL, "NULL argument");
+  *out = nullptr;
+  rng_server_config cfg = *cfg_in;
+  if (cfg.pool_bytes == 0) return set_error(RNG_EINVAL, "pool_bytes must be > 0");
+  if (!cfg.chunk_elems) cfg.chunk_elems = 1ull << 21;
+  cfg.chunk_elems = (cfg.chunk_elems + 3) / 4 * 4;  // chunks start 16-byte aligned
+  if (!cfg.max_active) cfg.max_active = 4096;
+  if (!cfg.max_items) cfg.max_items = 1024;
+  if (!cfg.inflight) cfg.inflight = 2;
+  if (cfg.inflight > 8) return set_error(RNG_EINVAL, "inflight must be 1..8");
+  rng_tune t = cfg.tune;
+  const rng_tune d = auto_defaults(RNG_F64);
+  if (!t.step) t.step = d.step ? d.step : ST_SHARED;
+  if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
+  if (!t.skip) t.skip = SK_TABLE;
+  if (!t.depth) t.depth = d.depth ? d.depth : 15;
+  if (!t.block) t.block = 256;
+  if (!t.unit) t.unit = 4;
+  if (t.depth % 2 == 0 || t.depth > kMaxDepth || t.block % 32 || !t.block || t.block > 1024)
+    return set_error(RNG_EINVAL, "bad server tuning");
+  const void* fn = batch_kernel_fn((int)t.step, (int)t.conv);
+  if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
+  DeviceInfo di;
+  rng_status stt = device_info(&di);
+  if (stt != RNG_OK) return stt;
+  const size_t smem = batch_smem_bytes(t.block, t.depth);
+  if (smem > di.smem_optin) return set_error(RNG_EINVAL, "tile buffers exceed shared memory");
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)di.smem_optin);
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(server)");
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)t.block, smem);
+  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+
+  bcn_server* s = new (std::nothrow) bcn_server(cfg.pool_bytes);
+  if (!s) return set_error(RNG_ENOMEM, "out of host memory");
+  s->cfg = cfg;
+  s->tune = t;
+  s->fn = fn;
+  s->smem = smem;
+  s->grid_full = (uint64_t)std::max(per_sm, 1) * (uint64_t)di.sms;
+  s->jump = host_pow2((53ull * (t.step == ST_MONT ? 33ull : 31ull) * t.depth) % kP);
+  s->device = di.device;
+  auto cleanup = [s]() {
+    for (Slot& sl : s->slots) {
+      if (sl.ev) cudaEventDestroy(sl.ev);
+      if (sl.cs) cudaStreamDestroy(sl.cs);
+      if (sl.h_desc) cudaFreeHost(sl.h_desc);
+      if (sl.h_prefix) cudaFreeHost(sl.h_prefix);
+      if (sl.d_table) cudaFree(sl.d_table);
+    }
+    if (s->pool_dev) cudaFree(s->pool_dev);
+    delete s;
+  };
+  e = cudaMalloc(&s->pool_dev, cfg.pool_bytes);
+  if (e != cudaSuccess) {
+    s->pool_dev = nullptr;
+    cleanup();
+    return cuda_error(e, "cudaMalloc(output pool)");
+  }
+  s->slots.resize(cfg.inflight);
+  const size_t table = sizeof(BatchDesc) * cfg.max_items + sizeof(uint64_t) * (cfg.max_items + 1) + 16;
+  for (Slot& sl : s->slots) {
+    e = cudaStreamCreateWithFlags(&sl.cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_desc, sizeof(BatchDesc) * cfg.max_items);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_prefix, sizeof(uint64_t) * (cfg.max_items + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_table, table);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_error(e, "creating server slots");
+    }
+  }
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return RNG_OK;
+}
+
+rng_status rng_server_submit(bcn_server* s, uint64_t start_index, uint64_t offset, uint64_t n,
+                             rng_dtype dt, uint64_t* id) {
+  if (!s || !id) return set_error(RNG_EINVAL, "NULL argument");
+  if (start_index < kSeedMin || start_index > kSeedMax)
+    return set_error(RNG_ERANGE, "start index outside [3^33+100, 2^53]");
+  if ((int)dt < 0 || (int)dt > 2) return set_error(RNG_EINVAL, "bad dtype");
+  if (n == 0) return set_error(RNG_EINVAL, "a request needs n > 0");
+  if (n > RNG_MAX_N || n > UINT64_MAX - offset) return set_error(RNG_ERANGE, "n out of range");
+  const uint64_t bytes = n * dtype_size((int)dt);
+  if (bytes > s->cfg.pool_bytes)
+    return set_error(RNG_ENOMEM, "request of %llu bytes exceeds the pool",
+                     (unsigned long long)bytes);
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (s->err != RNG_OK) return set_error(s->err, "server failed: %s", s->errmsg);
+  Request r;
+  r.seed = start_index;
+  r.offset = offset;
+  r.n = n;
+  r.bytes = bytes;
+  r.dt = (uint32_t)dt;
+  r.t_arrive = now_s();
+  const uint64_t rid = s->next_id++;
+  s->reqs.emplace(rid, r);
+  s->queue.push_back(rid);
+  s->st.submitted += 1;
+  *id = rid;
+  s->cv_work.notify_one();
+  return RNG_OK;
+}
+
+rng_status rng_server_cancel(bcn_server* s, uint64_t id) {
+  if (!s) return set_error(RNG_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
+  if (it->second.state != RQ_QUEUED) return set_error(RNG_EBUSY, "request already admitted");
+  it->second.state = RQ_CANCELLED;
+  return RNG_OK;
+}
+
+rng_status rng_server_status(bcn_server* s, uint64_t id, int* state, double* latency_s) {
+  if (!s) return set_error(RNG_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
+  if (state) *state = it->second.state;
+  if (latency_s)
+    *latency_s = it->second.state >= RQ_DONE && it->second.state != RQ_CANCELLED
+                     ? it->second.t_done - it->second.t_arrive
+                     : -1.0;
+  return RNG_OK;
+}
+
+rng_status rng_server_wait(bcn_server* s, uint64_t id, double timeout_s) {
+  if (!s) return set_error(RNG_EINVAL, "NULL server");
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                           std::chrono::duration<double>(timeout_s));
+  while (s->reqs[id].state < RQ_DONE && s->err == RNG_OK) {
+    if (s->cv_done.wait_until(lock, deadline) == std::cv_status::timeout &&
+        s->reqs[id].state < RQ_DONE)
+      return set_error(RNG_ETIMEOUT, "request %llu not done after %.3f s", (unsigned long long)id,
+                       timeout_s);
+  }
+  if (s->err != RNG_OK) return set_error(s->err, "server failed: %s", s->errmsg);
+  if (s->reqs[id].state == RQ_CANCELLED) return set_error(RNG_EINVAL, "request was cancelled");
+  return RNG_OK;
+}
+
+rng_status rng_server_read(bcn_server* s, uint64_t id, void* dst, uint64_t dst_bytes) {
+  if (!s || !dst) return set_error(RNG_EINVAL, "NULL argument");
+  uint64_t off = 0, bytes = 0;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request");
+    if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done or released");
+    off = it->second.pool_off;
+    bytes = it->second.bytes;
+  }
+  if (dst_bytes < bytes) return set_error(RNG_EINVAL, "destination smaller than the result");
+  cudaError_t e = cudaMemcpy(dst, s->pool_dev + off, bytes, cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_error(e, "reading a result");
+  return RNG_OK;
+}
+
+rng_status rng_server_result_ptr(bcn_server* s, uint64_t id, void** dev_ptr) {
+  if (!s || !dev_ptr) return set_error(RNG_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request");
+  if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done or released");
+  *dev_ptr = s->pool_dev + it->second.pool_off;
+  return RNG_OK;
+}
+
+rng_status rng_server_release(bcn_server* s, uint64_t id) {
+  if (!s) return set_error(RNG_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request");
+  if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done or already released");
+  s->pool.release(it->second.pool_off);
+  it->second.state = RQ_RELEASED;
+  s->cv_work.notify_one();
+  return RNG_OK;
+}
+
+rng_status rng_server_stats_get(bcn_server* s, rng_server_stats* out) {
+  if (!s || !out) return set_error(RNG_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  *out = s->st;
+  out->pool_in_use = s->pool.in_use;
+  out->pool_bytes = s->cfg.pool_bytes;
+  return s->err;
+}
+
+rng_status rng_server_run_trace(bcn_server* s, uint32_t n, const double* arrival_s,
+                                const uint64_t* starts, const uint64_t* offsets,
+                                const uint64_t* counts, const uint8_t* dtypes, double timeout_s,
+                                double* latency_s, double* wall_s) {
+  if (!s || !arrival_s || !starts || !counts || !dtypes || !latency_s)
+    return set_error(RNG_EINVAL, "NULL argument");
+  std::vector<uint64_t> ids(n, 0);
+  const double t0 = now_s();
+  for (uint32_t i = 0; i < n; ++i) {
+    const double due = t0 + arrival_s[i];
+    while (now_s() < due) {
+    }  // open-loop arrivals: spin until the request's arrival time
+    rng_status st = rng_server_submit(s, starts[i], offsets ? offsets[i] : 0, counts[i],
+                                      (rng_dtype)dtypes[i], &ids[i]);
+    if (st != RNG_OK) return st;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->reqs[ids[i]].t_arrive = due;  // latency counts from the scheduled arrival
+  }
+  const double deadline = now_s() + timeout_s;
+  for (uint32_t i = 0; i < n; ++i) {
+    const double left = deadline - now_s();
+    rng_status st = rng_server_wait(s, ids[i], left > 0 ? left : 0.0);
+    if (st != RNG_OK) return st;
+    std::lock_guard<std::mutex> lock(s->mu);
+    const Request& r = s->reqs[ids[i]];
+    latency_s[i] = r.t_done - r.t_arrive;
+  }
+  if (wall_s) {
+    double last = 0;
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (uint32_t i = 0; i < n; ++i) last = std::max(last, s->reqs[ids[i]].t_done);
+    *wall_s = last - t0;
+  }
+  return RNG_OK;
+}
+
+rng_status rng_server_destroy(bcn_server* s) {
+  if (!s) return RNG_OK;
+  s->stop.store(true);
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (Slot& sl : s->slots) {
+    if (sl.cs) cudaStreamSynchronize(sl.cs);
+    if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.cs) cudaStreamDestroy(sl.cs);
+    if (sl.h_desc) cudaFreeHost(sl.h_desc);
+    if (sl.h_prefix) cudaFreeHost(sl.h_prefix);
+    if (sl.d_table) cudaFree(sl.d_table);
+  }
+  if (s->pool_dev) cudaFree(s->pool_dev);
+  delete s;
+  return RNG_OK;
+}
+
+}  // extern "C"

@@ -56,6 +56,19 @@ def make_tune(step="auto", conv="auto", layout="auto", skip="auto", depth=0, blo
                 depth, block, grid, unit)
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("pool_bytes", ctypes.c_uint64), ("chunk_elems", ctypes.c_uint64),
+                ("max_active", ctypes.c_uint32), ("max_items", ctypes.c_uint32),
+                ("inflight", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("release_after_s", ctypes.c_double), ("tune", Tune)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in
+                ("submitted", "completed", "iterations", "items", "max_items_seen",
+                 "peak_active", "peak_pool_bytes", "bytes_done", "pool_in_use", "pool_bytes")]
+
+
 def _load() -> ctypes.CDLL:
     path = _build.LIB
     if not os.path.exists(path):
@@ -92,6 +105,23 @@ def _load() -> ctypes.CDLL:
         "rng_batch_destroy": ([vp], i32),
         "rng_consume_mc": ([u64, u64, u64, u64, vp, vp, vp, vp, vp, tp], i32),
         "rng_batch_generate_noalloc": ([u32, vp, vp, vp, vp, vp, tp, vp], i32),
+        "rng_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], i32),
+        "rng_server_submit": ([vp, u64, u64, u64, i32, ctypes.POINTER(u64)], i32),
+        "rng_server_cancel": ([vp, u64], i32),
+        "rng_server_status": ([vp, u64, ctypes.POINTER(i32), ctypes.POINTER(dbl)], i32),
+        "rng_server_wait": ([vp, u64, dbl], i32),
+        "rng_server_read": ([vp, u64, vp, u64], i32),
+        "rng_server_result_ptr": ([vp, u64, ctypes.POINTER(vp)], i32),
+        "rng_server_release": ([vp, u64], i32),
+        "rng_server_stats_get": ([vp, ctypes.POINTER(ServerStats)], i32),
+        "rng_server_run_trace": ([vp, u32, vp, vp, vp, vp, vp, dbl, vp,
+                                  ctypes.POINTER(dbl)], i32),
+        "rng_server_destroy": ([vp], i32),
+        "rng_pool_create": ([u64, u64, ctypes.POINTER(vp)], i32),
+        "rng_pool_alloc": ([vp, u64, ctypes.POINTER(u64)], i32),
+        "rng_pool_free": ([vp, u64], i32),
+        "rng_pool_stats": ([vp] + [ctypes.POINTER(u64)] * 5, i32),
+        "rng_pool_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -327,6 +357,123 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib.rng_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (see rng_server_create)."""
+
+    STATES = {0: "queued", 1: "active", 2: "done", 3: "released", 4: "cancelled"}
+
+    def __init__(self, pool_bytes: int, chunk_elems: int = 0, max_active: int = 0,
+                 max_items: int = 0, inflight: int = 0, release_after_s: float = -1.0,
+                 tune=None):
+        cfg = ServerConfig(pool_bytes, chunk_elems, max_active, max_items, inflight, 0,
+                           release_after_s, Tune())
+        if tune is not None:
+            cfg.tune = tune if isinstance(tune, Tune) else make_tune(**tune)
+        h = ctypes.c_void_p()
+        _check(lib.rng_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, start_index: int, offset: int, n: int, dtype: str = "f64") -> int:
+        rid = ctypes.c_uint64()
+        _check(lib.rng_server_submit(self._h, start_index, offset, n, _dtype(dtype)[0],
+                                     ctypes.byref(rid)))
+        return rid.value
+
+    def cancel(self, rid: int) -> None:
+        _check(lib.rng_server_cancel(self._h, rid))
+
+    def status(self, rid: int):
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        _check(lib.rng_server_status(self._h, rid, ctypes.byref(st), ctypes.byref(lat)))
+        return self.STATES.get(st.value, st.value), lat.value
+
+    def wait(self, rid: int, timeout_s: float = 60.0) -> None:
+        _check(lib.rng_server_wait(self._h, rid, timeout_s))
+
+    def read(self, rid: int, n: int, dtype: str):
+        _, tdt = _dtype(dtype)
+        out = torch.empty(n, dtype=tdt, device="cuda")
+        _check(lib.rng_server_read(self._h, rid, ctypes.c_void_p(out.data_ptr()),
+                                   out.numel() * out.element_size()))
+        return out
+
+    def release(self, rid: int) -> None:
+        _check(lib.rng_server_release(self._h, rid))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        rc = lib.rng_server_stats_get(self._h, ctypes.byref(st))
+        d = {f: getattr(st, f) for f, _ in ServerStats._fields_}
+        d["status"] = rc
+        return d
+
+    def run_trace(self, arrivals, starts, counts, dtypes, offsets=None, timeout_s=120.0):
+        """Replay a trace in real time; returns (latencies in seconds, wall seconds)."""
+        import numpy as np
+        n = len(arrivals)
+        arr = np.ascontiguousarray(arrivals, dtype=np.float64)
+        st = np.ascontiguousarray(starts, dtype=np.uint64)
+        ct = np.ascontiguousarray(counts, dtype=np.uint64)
+        dt = np.ascontiguousarray([_dtype(d)[0] for d in dtypes], dtype=np.uint8)
+        of = np.ascontiguousarray(offsets, dtype=np.uint64) if offsets is not None else None
+        lat = np.empty(n, dtype=np.float64)
+        wall = ctypes.c_double()
+        _check(lib.rng_server_run_trace(
+            self._h, n, ctypes.c_void_p(arr.ctypes.data), ctypes.c_void_p(st.ctypes.data),
+            ctypes.c_void_p(of.ctypes.data) if of is not None else None,
+            ctypes.c_void_p(ct.ctypes.data), ctypes.c_void_p(dt.ctypes.data), timeout_s,
+            ctypes.c_void_p(lat.ctypes.data), ctypes.byref(wall)))
+        return lat, wall.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.rng_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pool:
+    """The host-side pool sub-allocator the server admits requests with."""
+
+    def __init__(self, capacity: int, align: int = 256):
+        h = ctypes.c_void_p()
+        _check(lib.rng_pool_create(capacity, align, ctypes.byref(h)))
+        self._h = h
+
+    def alloc(self, nbytes: int):
+        off = ctypes.c_uint64()
+        rc = lib.rng_pool_alloc(self._h, nbytes, ctypes.byref(off))
+        if rc == 3:
+            return None
+        _check(rc)
+        return off.value
+
+    def free(self, off: int) -> None:
+        _check(lib.rng_pool_free(self._h, off))
+
+    def stats(self) -> dict:
+        v = [ctypes.c_uint64() for _ in range(5)]
+        _check(lib.rng_pool_stats(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("in_use", "peak", "live", "largest_free", "free_ranges"),
+                        (x.value for x in v)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.rng_pool_destroy(self._h)
             self._h = None
 
     def __del__(self):

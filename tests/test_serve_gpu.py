@@ -1,0 +1,121 @@
+"""The continuous-batching server on the GPU.
+
+* each request's bytes are the same served alone and served in a mix of
+  concurrent requests of uneven size (and equal the oracle's);
+* memory-based admission never lets the pool's in-use bytes exceed its size,
+  and requests wait rather than fail when it is full;
+* bad requests are rejected at submission without disturbing the others;
+* a real-time trace replay completes every request with finite latency.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+M = 3 ** 33
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1206_1187_gb300 import rng
+    return rng
+
+
+def _bits(t):
+    import torch
+    return t.view(torch.int64 if t.element_size() == 8 else torch.int32).cpu().numpy()
+
+
+def _obits(a):
+    return a.view(np.int64 if a.itemsize == 8 else np.int32)
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(R, oracle_mod):
+    from paper_1206_1187_gb300 import inputs
+    arrivals, counts, dtypes, seeds, offsets = inputs.request_trace(
+        240, rate_hz=20000.0, seed=5, min_bytes=1 << 10, max_bytes=8 << 20)
+    n = len(arrivals)
+    alone = []
+    srv = R.Server(pool_bytes=64 << 20, chunk_elems=1 << 16)
+    for i in range(n):
+        rid = srv.submit(int(seeds[i]), int(offsets[i]), int(counts[i]), dtypes[i])
+        srv.wait(rid, 30.0)
+        alone.append(_bits(srv.read(rid, int(counts[i]), dtypes[i])))
+        srv.release(rid)
+    srv.close()
+
+    srv = R.Server(pool_bytes=1 << 30, chunk_elems=1 << 16, inflight=3)
+    lat, wall = srv.run_trace(arrivals, seeds, counts, dtypes, offsets=offsets, timeout_s=60.0)
+    assert np.all(lat > 0) and np.isfinite(lat).all()
+    st = srv.stats()
+    assert st["completed"] == n and st["iterations"] < 2 * n  # work was batched
+    for i in range(n):
+        got = _bits(srv.read(i + 1, int(counts[i]), dtypes[i]))
+        assert np.array_equal(got, alone[i]), i
+    for i in range(0, n, 12):
+        want = oracle_mod.generate(int(seeds[i]), int(offsets[i]), int(counts[i]), dtypes[i])
+        assert np.array_equal(alone[i], _obits(want)), i
+    srv.close()
+
+
+def test_admission_waits_for_pool_space(R, oracle_mod):
+    pool = 8 << 20
+    srv = R.Server(pool_bytes=pool, chunk_elems=1 << 15, release_after_s=-1.0)
+    rnd = np.random.default_rng(3)
+    reqs = []
+    for k in range(40):
+        n = int(rnd.integers(1 << 17, 3 << 17))  # 1..3 MiB of FP64
+        a = int(rnd.integers(M + 100, 2 ** 53))
+        reqs.append((srv.submit(a, k * 1000, n, "f64"), a, k * 1000, n))
+    for rid, a, off, n in reqs:  # a client that reads, checks and releases in order
+        srv.wait(rid, 30.0)
+        got = _bits(srv.read(rid, n, "f64"))
+        if rid % 7 == 0:
+            assert np.array_equal(got, _obits(oracle_mod.generate(a, off, n, "f64")))
+        srv.release(rid)
+    st = srv.stats()
+    assert st["completed"] == 40
+    assert 0 < st["peak_pool_bytes"] <= pool
+    assert st["pool_in_use"] == 0
+    srv.close()
+
+
+def test_bad_requests_do_not_disturb_the_others(R, oracle_mod):
+    srv = R.Server(pool_bytes=16 << 20, release_after_s=-1.0)
+    good = srv.submit(M + 500, 0, 100000, "f32")
+    with pytest.raises(R.RNGError) as e:
+        srv.submit(M + 99, 0, 10, "f64")
+    assert e.value.status == 2
+    with pytest.raises(R.RNGError) as e:
+        srv.submit(M + 100, 0, 0, "f64")
+    assert e.value.status == 1
+    with pytest.raises(R.RNGError) as e:
+        srv.submit(M + 100, 0, 4 << 20, "f64")  # 32 MiB > pool
+    assert e.value.status == 3
+    big = srv.submit(M + 7, 0, (15 << 20) // 8, "f64")  # fills the pool
+    waiting = srv.submit(M + 8, 0, 1 << 20, "f64")      # cannot be admitted yet
+    srv.cancel(waiting)
+    assert srv.status(waiting)[0] == "cancelled"
+    srv.wait(good, 30.0)
+    srv.wait(big, 30.0)
+    got = _bits(srv.read(good, 100000, "f32"))
+    assert np.array_equal(got, _obits(oracle_mod.generate(M + 500, 0, 100000, "f32")))
+    st, lat = srv.status(good)
+    assert st == "done" and lat > 0
+    srv.close()
+
+
+def test_trace_replay_latencies(R):
+    from paper_1206_1187_gb300 import inputs
+    arrivals, counts, dtypes, seeds, offsets = inputs.request_trace(
+        3000, rate_hz=20000.0, seed=9, min_bytes=1 << 10, max_bytes=4 << 20)
+    srv = R.Server(pool_bytes=2 << 30, release_after_s=0.0)
+    lat, wall = srv.run_trace(arrivals, seeds, counts, dtypes, offsets=offsets, timeout_s=60.0)
+    assert np.isfinite(lat).all() and np.all(lat > 0)
+    assert wall >= arrivals[-1]
+    st = srv.stats()
+    assert st["completed"] == 3000
+    assert np.percentile(lat, 99) < 0.5
+    srv.close()
