@@ -64,8 +64,11 @@ typedef enum {
   RNG_STEP_AUTO = 0,           /* the measured-fastest variant                */
   RNG_STEP_BARRETT = 1,        /* Modified Barrett, Sec. 2.1.3, forward       */
   RNG_STEP_MONTGOMERY = 2,     /* Montgomery-style, R = 2^53, blocks run back */
-  RNG_STEP_BARRETT_SHARED = 3  /* Barrett quotient estimate taken from the
+  RNG_STEP_BARRETT_SHARED = 3, /* Barrett quotient estimate taken from the
                                   output-conversion product z*(mu+1), forward */
+  RNG_STEP_LECUYER = 4,        /* L'Ecuyer's decomposition, a = 2^25, applied
+                                  twice (Sec. 2.1.1), forward                 */
+  RNG_STEP_BARRETT_CLASSIC = 5 /* Barrett's algorithm, k = 53 (Sec. 2.1.2)    */
 } rng_step;
 
 /* How a state becomes an FP64 variate (the RN multiply of Algorithm BB). */
@@ -104,6 +107,9 @@ typedef struct {
   uint32_t block;   /* threads per block (TILED: multiple of 32, <= 1024)    */
   uint32_t grid;    /* blocks                                                */
   uint32_t unit;    /* BATCH: tiles per work unit (0 = choose); else ignored */
+  uint32_t chains;  /* TILED, forward steps: independent chains per lane, 1
+                       or 2 (0 = choose); 2 splits each lane's run in halves */
+  uint32_t reserved;
 } rng_tune;
 
 /* Largest n accepted by one generation call. */

@@ -32,8 +32,9 @@ def bulk_candidates(dtype: str) -> list[dict]:
                 continue
             for depth in DEPTHS:
                 for block in BLOCKS:
-                    cands.append(dict(step=step, conv=conv, layout="tiled", depth=depth,
-                                      block=block))
+                    for chains in ((1, 2) if step != "montgomery" else (1,)):
+                        cands.append(dict(step=step, conv=conv, layout="tiled", depth=depth,
+                                          block=block, chains=chains))
     return cands
 
 

@@ -216,9 +216,11 @@ rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune* in, rng_tu
   out->block = L.block;
   out->grid = L.grid;
   out->unit = 0;
+  out->chains = L.chains;
+  out->reserved = 0;
   return RNG_OK;
 }
 
-int rng_version(void) { return 100; }
+int rng_version(void) { return 101; }
 
 }  // extern "C"

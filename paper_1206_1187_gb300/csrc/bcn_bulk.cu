@@ -36,6 +36,8 @@ struct TiledParams {
   uint64_t ntiles;     // full tiles of 32*depth elements after the head
   uint64_t ebase;      // (seed - 3^33 + 53*i0) mod P
   uint64_t jump;       // 2^(53*31*depth) (Barrett) / 2^(53*33*depth) (Montgomery)
+  uint64_t jump_a;     // two chains: 2^(53*(32c-h-1)) and 2^(53*(31c+h+1)), h = depth/2
+  uint64_t jump_b;
   uint64_t cbits;      // ST_CONST: the word written
   uint32_t depth;
   uint32_t skip;
@@ -49,7 +51,7 @@ struct DirectParams {
   uint32_t skip;
 };
 
-template <int DT, int STEP, int CONV>
+template <int DT, int STEP, int CONV, int ILP>
 __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
   typedef typename Word<DT>::type W;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -68,10 +70,17 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
   if (t0 < t1) {
     // this lane's first element in the warp's first tile
     const uint64_t first = p.head + t0 * tile_elems + (uint64_t)lane * c;
-    Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
     uint32_t issued = 0;
-    warp_tiles<DT, STEP, CONV>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump, g, buf0,
-                               issued, lane, p.cbits);
+    if constexpr (ILP == 2) {
+      Gen<DT, STEP, CONV> a = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
+      Gen<DT, STEP, CONV> b = lane_chain<DT, STEP, CONV>(p.ebase, first + c / 2 + 1, c, p.skip);
+      warp_tiles2<DT, STEP, CONV>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump_a, p.jump_b,
+                                  a, b, buf0, issued, lane);
+    } else {
+      Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
+      warp_tiles<DT, STEP, CONV>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump, g, buf0,
+                                 issued, lane, p.cbits);
+    }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
   }
@@ -97,40 +106,47 @@ __global__ void __launch_bounds__(1024) direct_kernel(const DirectParams p) {
 }
 
 // ------------------------------------------------------------ dispatch
+template <int DT, int ST, int CV>
+static const void* pick_ilp(int layout, int ilp) {
+  if (layout != RNG_LAYOUT_TILED) return (const void*)direct_kernel<DT, ST, CV>;
+  if constexpr (ST == ST_BARRETT || ST == ST_SHARED)
+    if (ilp == 2) return (const void*)tiled_kernel<DT, ST, CV, 2>;
+  return (const void*)tiled_kernel<DT, ST, CV, 1>;
+}
+
 template <int DT, int ST>
-static const void* pick_cv(int layout, int cv) {
-  if (layout == RNG_LAYOUT_TILED)
-    return cv == CV_FP64 ? (const void*)tiled_kernel<DT, ST, CV_FP64>
-                         : (const void*)tiled_kernel<DT, ST, CV_INT>;
-  return cv == CV_FP64 ? (const void*)direct_kernel<DT, ST, CV_FP64>
-                       : (const void*)direct_kernel<DT, ST, CV_INT>;
+static const void* pick_cv(int layout, int cv, int ilp) {
+  return cv == CV_FP64 ? pick_ilp<DT, ST, CV_FP64>(layout, ilp)
+                       : pick_ilp<DT, ST, CV_INT>(layout, ilp);
 }
 
 template <int DT>
-static const void* pick_st(int layout, int st, int cv) {
+static const void* pick_st(int layout, int st, int cv, int ilp) {
   if (DT == DT_U64) cv = CV_INT;  // no conversion for raw states
   switch (st) {
-    case ST_BARRETT: return pick_cv<DT, ST_BARRETT>(layout, cv);
-    case ST_MONT: return pick_cv<DT, ST_MONT>(layout, cv);
-    case ST_SHARED: return pick_cv<DT, ST_SHARED>(layout, cv);
+    case ST_BARRETT: return pick_cv<DT, ST_BARRETT>(layout, cv, ilp);
+    case ST_MONT: return pick_cv<DT, ST_MONT>(layout, cv, 1);
+    case ST_SHARED: return pick_cv<DT, ST_SHARED>(layout, cv, ilp);
+    case ST_LECUYER: return pick_cv<DT, ST_LECUYER>(layout, cv, 1);
+    case ST_BCLASSIC: return pick_cv<DT, ST_BCLASSIC>(layout, cv, 1);
     default: return nullptr;
   }
 }
 
-static const void* pick_kernel(int layout, int dt, int st, int cv) {
+static const void* pick_kernel(int layout, int dt, int st, int cv, int ilp) {
   if (st == ST_CONST) {
     if (dt == DT_F64) return layout == RNG_LAYOUT_TILED
-                                 ? (const void*)tiled_kernel<DT_F64, ST_CONST, CV_INT>
+                                 ? (const void*)tiled_kernel<DT_F64, ST_CONST, CV_INT, 1>
                                  : (const void*)direct_kernel<DT_F64, ST_CONST, CV_INT>;
     if (dt == DT_F32) return layout == RNG_LAYOUT_TILED
-                                 ? (const void*)tiled_kernel<DT_F32, ST_CONST, CV_INT>
+                                 ? (const void*)tiled_kernel<DT_F32, ST_CONST, CV_INT, 1>
                                  : (const void*)direct_kernel<DT_F32, ST_CONST, CV_INT>;
     return nullptr;
   }
   switch (dt) {
-    case DT_F64: return pick_st<DT_F64>(layout, st, cv);
-    case DT_F32: return pick_st<DT_F32>(layout, st, cv);
-    case DT_U64: return pick_st<DT_U64>(layout, st, cv);
+    case DT_F64: return pick_st<DT_F64>(layout, st, cv, ilp);
+    case DT_F32: return pick_st<DT_F32>(layout, st, cv, ilp);
+    case DT_U64: return pick_st<DT_U64>(layout, st, cv, ilp);
     default: return nullptr;
   }
 }
@@ -170,6 +186,7 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
       if (!t.layout) t.layout = d.layout;
       if (!t.depth) t.depth = d.depth;
       if (!t.block) t.block = d.block;
+      if (!t.chains) t.chains = d.chains;
     }
   }
   BulkLaunch L = {};
@@ -180,7 +197,8 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   L.skip = t.skip ? (int)t.skip : SK_TABLE;
   if (L.layout != RNG_LAYOUT_TILED && L.layout != RNG_LAYOUT_DIRECT)
     return set_error(RNG_EINVAL, "tune.layout %u is not a layout", t.layout);
-  if (!constant && L.step != ST_BARRETT && L.step != ST_MONT && L.step != ST_SHARED)
+  if (!constant && L.step != ST_BARRETT && L.step != ST_MONT && L.step != ST_SHARED &&
+      L.step != ST_LECUYER && L.step != ST_BCLASSIC)
     return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
   if (L.conv != CV_INT && L.conv != CV_FP64)
     return set_error(RNG_EINVAL, "tune.conv %u is not a conversion", t.conv);
@@ -193,7 +211,12 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   DeviceInfo di;
   rng_status st = device_info(&di);
   if (st != RNG_OK) return st;
-  const void* fn = pick_kernel(L.layout, dt, L.step, L.conv);
+  if (t.chains > 2) return set_error(RNG_EINVAL, "tune.chains %u must be 0, 1 or 2", t.chains);
+  L.chains = 1;
+  if (L.layout == RNG_LAYOUT_TILED && (L.step == ST_SHARED || L.step == ST_BARRETT) &&
+      t.chains == 2 && (t.depth ? t.depth : 15) >= 3)
+    L.chains = 2;
+  const void* fn = pick_kernel(L.layout, dt, L.step, L.conv, (int)L.chains);
   if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   if (L.layout == RNG_LAYOUT_TILED) {
     L.depth = t.depth ? t.depth : 15;
@@ -249,7 +272,7 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
 
 rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t n,
                        void* out, uint64_t const_bits, cudaStream_t cs) {
-  const void* fn = pick_kernel(L.layout, L.dt, L.step, L.conv);
+  const void* fn = pick_kernel(L.layout, L.dt, L.step, L.conv, (int)L.chains);
   if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   const uint64_t ebase = (L.step == ST_CONST) ? 0 : host_exponent_base(seed, i0);
   cudaError_t e;
@@ -267,6 +290,9 @@ rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t
     p.ebase = ebase;
     const uint64_t stride = (L.step == ST_MONT) ? 33ull : 31ull;
     p.jump = host_pow2((53ull * stride * L.depth) % kP);
+    const uint64_t h = L.depth / 2;
+    p.jump_a = host_pow2((53ull * (32ull * L.depth - h - 1)) % kP);
+    p.jump_b = host_pow2((53ull * (31ull * L.depth + h + 1)) % kP);
     p.cbits = const_bits;
     p.depth = L.depth;
     p.skip = (uint32_t)L.skip;

@@ -59,6 +59,16 @@ struct Gen {
       auto w = to_word<DT, CONV>(z, phi, plo);
       z = barrett_from_product(phi, plo);
       return w;
+    } else if constexpr (STEP == ST_LECUYER || STEP == ST_BCLASSIC) {
+      uint64_t plo = 0, phi = 0;
+      if constexpr (DT != DT_U64 && CONV == CV_INT) {
+        plo = z * kMu;
+        phi = umulhi(z, kMu);
+      }
+      auto w = to_word<DT, CONV>(z, phi, plo);
+      if constexpr (STEP == ST_LECUYER) z = lecuyer_step(z);
+      else z = barrett_classic_step(z);
+      return w;
     } else {
       uint64_t plo = 0, phi = 0;
       if constexpr (DT != DT_U64 && CONV == CV_INT) {
@@ -160,6 +170,50 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
     ++issued;
     if constexpr (STEP != ST_CONST) {
       if (t + 1 < ntiles) g.z = mulmod(g.z, jump);
+    }
+  }
+}
+
+// Two independent chains per lane: the lane's run of c = 2h+1 elements is
+// split into its first h+1 elements (chain a) and its last h (chain b), and
+// the two chains step alternately, so each step's latency is hidden behind
+// the other chain's work.  Stores to mine[i] and mine[h+1+i] keep lane
+// stride c (odd), so they stay bank-conflict free.  Between tiles chain a
+// jumps by 32c-h-1 steps and chain b by 31c+h+1.  Forward steps only.
+template <int DT, int STEP, int CONV>
+__device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict__ out,
+                                            uint64_t first, uint64_t ntiles, uint32_t c,
+                                            uint64_t jump_a, uint64_t jump_b,
+                                            Gen<DT, STEP, CONV>& a, Gen<DT, STEP, CONV>& b,
+                                            typename Word<DT>::type* buf0, uint32_t& issued,
+                                            uint32_t lane) {
+  typedef typename Word<DT>::type W;
+  const uint32_t tile_elems = 32u * c;
+  const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
+  const uint32_t h = c >> 1;
+  for (uint64_t t = 0; t < ntiles; ++t) {
+    W* const buf = buf0 + (issued & 1u) * tile_elems;
+    if (issued >= 2) {
+      if (lane == 0) bulk_wait_read_1();
+      __syncwarp();
+    }
+    W* const mine = buf + lane * c;
+#pragma unroll 4
+    for (uint32_t i = 0; i < h; ++i) {
+      mine[i] = a.next();
+      mine[h + 1 + i] = b.next();
+    }
+    mine[h] = a.next();
+    fence_proxy_async_shared();
+    __syncwarp();
+    if (lane == 0) {
+      bulk_store(out + first + t * tile_elems, buf, tile_bytes);
+      bulk_commit();
+    }
+    ++issued;
+    if (t + 1 < ntiles) {
+      a.z = mulmod(a.z, jump_a);
+      b.z = mulmod(b.z, jump_b);
     }
   }
 }

@@ -13,7 +13,8 @@ enum { DT_F64 = 0, DT_F32 = 1, DT_U64 = 2 };
 // State advance: Modified Barrett (forward), Montgomery (backward), Barrett
 // with the quotient shared with the conversion (forward), or the roofline
 // probe that writes a constant and computes nothing.
-enum { ST_BARRETT = 1, ST_MONT = 2, ST_SHARED = 3, ST_CONST = 9 };
+enum { ST_BARRETT = 1, ST_MONT = 2, ST_SHARED = 3, ST_LECUYER = 4, ST_BCLASSIC = 5,
+       ST_CONST = 9 };
 enum { CV_INT = 1, CV_FP64 = 2 };
 enum { SK_TABLE = 1, SK_SQMUL = 2 };
 
@@ -22,7 +23,7 @@ constexpr uint32_t kMaxDepth = 255;
 // A fully resolved bulk launch.
 struct BulkLaunch {
   int dt, step, conv, layout, skip;
-  uint32_t depth, block, grid;
+  uint32_t depth, block, grid, chains;
   size_t smem_bytes;  // TILED only
 };
 

@@ -170,6 +170,36 @@ __device__ __forceinline__ uint64_t montgomery_back(uint64_t z) {
   return ((hi << 11) | (lo >> 53)) + 1;
 }
 
+// L'Ecuyer's decomposition (Sec. 2.1.1) with a = 2^25: m = a*q + r, r < a,
+// a^2 < m, so a*s mod m = a*(s mod q) - floor(s/q)*r, corrected by one "+ m".
+// For s < 4m the intermediate stays in (-m, m) because floor(s/q)*r <
+// 4*a*r <= 2^52 < m.  The step of Eq. 3 is two applications: 2^25 * (4z) and
+// then 2^25 * (2 * that).  The quotient floor(s/q) is an exact integer
+// division by the constant q.
+constexpr uint64_t kLq = kM >> 25, kLr = kM & ((1ull << 25) - 1);
+static_assert(kLr < (1ull << 25) && (1ull << 50) < kM, "L'Ecuyer needs a^2 < m");
+__device__ __forceinline__ uint64_t lecuyer_mul25(uint64_t s) {
+  const uint64_t t = s / kLq;
+  const int64_t v = (int64_t)((s - t * kLq) << 25) - (int64_t)(t * kLr);
+  return v < 0 ? (uint64_t)(v + (int64_t)kM) : (uint64_t)v;
+}
+__device__ __forceinline__ uint64_t lecuyer_step(uint64_t z) {
+  return lecuyer_mul25(lecuyer_mul25(z << 2) << 1);
+}
+
+// Barrett's algorithm (Sec. 2.1.2) with k = 53 applied to x = 2^53 z:
+// q1 = x >> 52 = 2z, q3 = (mu * q1) >> 54 in [Q-2, Q], r = (x - q3*m) mod 2^54
+// (x mod 2^54 is (z & 1) << 53), then at most two subtractions of m.
+__device__ __forceinline__ uint64_t barrett_classic_step(uint64_t z) {
+  const uint64_t q1 = z << 1;
+  const uint64_t q3 = (umulhi(q1, kMu) << 10) | ((q1 * kMu) >> 54);
+  const uint64_t mask54 = (1ull << 54) - 1;
+  uint64_t r = (((z & 1ull) << 53) - ((q3 * kM) & mask54)) & mask54;
+  r = (r >= kM) ? r - kM : r;
+  r = (r >= kM) ? r - kM : r;
+  return r;
+}
+
 // ---------------------------------------------------------- conversions
 // FP64 bits of RN(z * r3i) by integer arithmetic only.  p = z*mu + z =
 // z*r3i*2^106 exactly (< 2^106); the variate is p*2^-106 rounded to 53

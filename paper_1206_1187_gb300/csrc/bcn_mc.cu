@@ -12,66 +12,68 @@
 //     below 2^105 and a lane's sum fits 128 bits;
 //   * every RN(v*v) is a multiple of 2^-157 (the smallest variate is about
 //     1.62*2^-53, so the smallest square has exponent -105), so RN(v*v)*2^157
-//     is an integer below 2^157 and a lane's sum fits 192 bits;
+//     is an integer below 2^157.  For every variate above about 2^-20 its low
+//     64 bits are zero, so those squares are summed exactly as 128-bit
+//     integers on the 2^-93 grid; the rare smaller ones (below 2^117 on the
+//     2^-157 grid) go to a second 128-bit sum, and the two are joined into one
+//     192-bit integer per block;
 //   * RN(X + Y) <= 1 exactly when X + Y <= 1 + 2^-53 (the tie rounds to the
 //     even 1.0), i.e. when the two grid integers sum to at most 2^157 + 2^104.
+//     That bound is a multiple of 2^64, so the test can be made on the 2^-93
+//     grid with each rare small square rounded up: X + Y <= T exactly when
+//     hi(X) + ceil(Y / 2^64) <= T / 2^64 for X a multiple of 2^64.
 // Integer sums do not depend on order, so the warp reduction and the final
 // per-block rounding give the same bits for any launch shape.
 #include "bcn_gen.cuh"
 
 namespace bcn {
 
-struct U192 {
-  uint64_t w0, w1, w2;
+// (a1:a0) += (b1:b0) with one carry chain.
+__device__ __forceinline__ void add128(uint64_t& a0, uint64_t& a1, uint64_t b0, uint64_t b1) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a0), "+l"(a1) : "l"(b0), "l"(b1));
+}
+
+// x << k as (lo, hi) for x < 2^64, 0 <= k < 64 (no branch for k = 0).
+__device__ __forceinline__ void shl128(uint64_t x, uint32_t k, uint64_t& lo, uint64_t& hi) {
+  lo = x << k;
+  hi = (x >> 1) >> (63u - k);
+}
+
+// The exact grid images of one FP64 variate v (bits of RN(z*r3i)):
+//   (v0, v1)  = v * 2^105, an integer below 2^105;
+//   RN(v*v) * 2^157 = M2 << k with k = 2e + sh - 1993 >= 0.  When k >= 64
+//   (every variate from about 2^-20 up) its low 64 bits are zero and
+//   (q0, q1) = RN(v*v) * 2^93 exactly, `fast` is set; otherwise (q0, q1) =
+//   ceil(RN(v*v) * 2^93) for the hit test, and the exact value (below 2^117)
+//   goes to (s0, s1).
+struct Terms {
+  uint64_t v0, v1, q0, q1, s0, s1;
+  bool fast;
 };
 
-__device__ __forceinline__ void add128(uint64_t& a0, uint64_t& a1, uint64_t b0, uint64_t b1) {
-  const uint64_t s0 = a0 + b0;
-  a1 = a1 + b1 + (s0 < b0 ? 1ull : 0ull);
-  a0 = s0;
-}
-
-__device__ __forceinline__ void add192(U192& a, const U192& b) {
-  const uint64_t s0 = a.w0 + b.w0;
-  const uint64_t c0 = s0 < b.w0 ? 1ull : 0ull;
-  const uint64_t t1 = a.w1 + b.w1;
-  const uint64_t c1a = t1 < b.w1 ? 1ull : 0ull;
-  const uint64_t s1 = t1 + c0;
-  const uint64_t c1b = s1 < c0 ? 1ull : 0ull;
-  a.w2 = a.w2 + b.w2 + c1a + c1b;
-  a.w1 = s1;
-  a.w0 = s0;
-}
-
-// m << k as a 192-bit value, for m < 2^64 and 0 <= k < 128.
-__device__ __forceinline__ U192 shifted192(uint64_t m, uint32_t k) {
-  const uint32_t b = k & 63u;
-  const uint64_t lo = m << b;
-  const uint64_t hi = b ? (m >> (64u - b)) : 0ull;
-  const bool w1 = k >= 64u;
-  return U192{w1 ? 0ull : lo, w1 ? lo : hi, w1 ? hi : 0ull};
-}
-
-// The exact grid images of one FP64 variate (bits of RN(z*r3i)):
-//   v*2^105 as (s0, s1) and RN(v*v)*2^157 as sq.
-__device__ __forceinline__ void variate_terms(uint64_t bits, uint64_t& s0, uint64_t& s1, U192& sq) {
-  const uint32_t e = (uint32_t)(bits >> 52);               // biased exponent, >= 970
+__device__ __forceinline__ Terms variate_terms(uint64_t bits) {
+  Terms t;
+  const uint32_t e = (uint32_t)(bits >> 52);  // biased exponent, >= 970
   const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-  const uint32_t k1 = e - 970u;                             // v*2^105 = mant << k1, k1 <= 52
-  s0 = mant << k1;
-  s1 = k1 ? (mant >> (64u - k1)) : 0ull;
+  shl128(mant, e - 970u, t.v0, t.v1);          // v * 2^105, shift <= 52
   // RN(mant^2) to 53 significant bits, ties to even
-  const uint64_t plo = mant * mant, phi = __umul64hi(mant, mant);  // mant^2 < 2^106
-  const uint32_t top = (uint32_t)(phi >> 41) & 1u;          // bit 105
-  const uint32_t sh = 52u + top;                            // dropped bits
-  // m2 = mant^2 >> sh, rest = mant^2 mod 2^sh (sh is 52 or 53)
-  const uint64_t m2 = (phi << (64u - sh)) | (plo >> sh);
+  const uint64_t plo = mant * mant, phi = __umul64hi(mant, mant);  // < 2^106
+  const uint32_t sh = 52u + ((uint32_t)(phi >> 41) & 1u);           // 53 if bit 105 set
+  uint64_t m2 = (phi << (64u - sh)) | (plo >> sh);
   const uint64_t rest = plo & ((1ull << sh) - 1ull);
   const uint64_t half = 1ull << (sh - 1u);
-  const uint64_t up = (rest > half) | ((rest == half) & (m2 & 1ull));
-  // RN(v^2) = (m2 + up) * 2^(2(e-1075) + sh); on the 2^-157 grid the shift is
-  // 2e - 1993 + sh, which is >= 0 for every variate.
-  sq = shifted192(m2 + up, 2u * e + sh - 1993u);
+  m2 += (rest > half) | ((rest == half) & (m2 & 1ull));
+  const uint32_t k = 2u * e + sh - 1993u;
+  t.s0 = t.s1 = 0;
+  t.fast = k >= 64u;
+  if (__builtin_expect(t.fast, 1)) {
+    shl128(m2, k - 64u, t.q0, t.q1);
+  } else {
+    shl128(m2, k, t.s0, t.s1);            // exact, below 2^117
+    t.q0 = t.s1 + (t.s0 != 0 ? 1ull : 0ull);  // ceiling on the 2^-93 grid
+    t.q1 = 0;
+  }
+  return t;
 }
 
 // Round (w2:w1:w0) * 2^-scale to the nearest double, ties to even.
@@ -123,46 +125,52 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
   const uint64_t j0 = lane * pairs / 32, j1 = (lane + 1) * pairs / 32;
   const uint64_t first = (p.block0 + b) * p.len + 2 * j0;
   uint32_t hits = 0;
-  uint64_t a0 = 0, a1 = 0;
-  U192 q = {0, 0, 0};
+  uint64_t a0 = 0, a1 = 0;  // sum of v * 2^105
+  uint64_t h0 = 0, h1 = 0;  // sum of the fast RN(v*v) * 2^93
+  uint64_t l0 = 0, l1 = 0;  // sum of the other RN(v*v) * 2^157 (rare)
+  // hit iff RN(x^2) + RN(y^2) <= 1 + 2^-53, i.e. on the 2^-93 grid
+  // (exact high parts, ceilings of the rare small squares) <= 2^93 + 2^40
+  const uint64_t lim0 = 1ull << 40, lim1 = 1ull << 29;
   if (j0 < j1) {
     uint64_t z = seed_state(exponent_add(p.ebase, first + 1), p.skip);
     for (uint64_t j = j0; j < j1; ++j) {
-      const uint64_t bx = shared_step_f64(z);
-      const uint64_t by = shared_step_f64(z);
-      uint64_t x0, x1, y0, y1;
-      U192 xx, yy;
-      variate_terms(bx, x0, x1, xx);
-      variate_terms(by, y0, y1, yy);
-      add128(a0, a1, x0, x1);
-      add128(a0, a1, y0, y1);
-      U192 r2 = xx;
-      add192(r2, yy);
-      // r2 <= 2^157 + 2^104 : word 2 holds bit 157 as bit 29, word 1 bit 104 as bit 40
-      const bool inside = (r2.w2 < (1ull << 29)) ||
-                          (r2.w2 == (1ull << 29) &&
-                           (r2.w1 < (1ull << 40) || (r2.w1 == (1ull << 40) && r2.w0 == 0)));
-      hits += inside ? 1u : 0u;
-      add192(q, xx);
-      add192(q, yy);
+      const Terms x = variate_terms(shared_step_f64(z));
+      const Terms y = variate_terms(shared_step_f64(z));
+      add128(a0, a1, x.v0, x.v1);
+      add128(a0, a1, y.v0, y.v1);
+      uint64_t r0 = x.q0, r1 = x.q1;
+      add128(r0, r1, y.q0, y.q1);
+      hits += ((r1 < lim1) | ((r1 == lim1) & (r0 <= lim0))) ? 1u : 0u;
+      if (__builtin_expect(x.fast & y.fast, 1)) {
+        add128(h0, h1, r0, r1);
+      } else {
+        if (x.fast) add128(h0, h1, x.q0, x.q1);
+        if (y.fast) add128(h0, h1, y.q0, y.q1);
+        add128(l0, l1, x.s0, x.s1);
+        add128(l0, l1, y.s0, y.s1);
+      }
     }
   }
   // exact warp reduction (integer addition is order-free)
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     hits += __shfl_xor_sync(0xffffffffu, hits, off);
-    const uint64_t o0 = __shfl_xor_sync(0xffffffffu, a0, off);
-    const uint64_t o1 = __shfl_xor_sync(0xffffffffu, a1, off);
+    uint64_t o0 = __shfl_xor_sync(0xffffffffu, a0, off);
+    uint64_t o1 = __shfl_xor_sync(0xffffffffu, a1, off);
     add128(a0, a1, o0, o1);
-    U192 o;
-    o.w0 = __shfl_xor_sync(0xffffffffu, q.w0, off);
-    o.w1 = __shfl_xor_sync(0xffffffffu, q.w1, off);
-    o.w2 = __shfl_xor_sync(0xffffffffu, q.w2, off);
-    add192(q, o);
+    o0 = __shfl_xor_sync(0xffffffffu, h0, off);
+    o1 = __shfl_xor_sync(0xffffffffu, h1, off);
+    add128(h0, h1, o0, o1);
+    o0 = __shfl_xor_sync(0xffffffffu, l0, off);
+    o1 = __shfl_xor_sync(0xffffffffu, l1, off);
+    add128(l0, l1, o0, o1);
   }
+  // sum of squares on the 2^-157 grid: (h << 64) + l
+  uint64_t w0 = l0, w1 = l1, w2 = 0;
+  add128(w1, w2, h0, h1);
   if (lane == 0) {
     p.sum[b] = round_words(a0, a1, 0, 105);
-    p.sumsq[b] = round_words(q.w0, q.w1, q.w2, 157);
+    p.sumsq[b] = round_words(w0, w1, w2, 157);
     if (p.hits) p.hits[b] = hits;
     atomicAdd(p.hits_total, (unsigned long long)hits);
   }

@@ -95,6 +95,8 @@ rng_status rng_autotune_bulk(uint64_t n, rng_dtype dt, void* out, void* cuda_str
       best->block = L.block;
       best->grid = L.grid;
       best->unit = 0;
+      best->chains = L.chains;
+      best->reserved = 0;
     }
   }
   cudaEventDestroy(e0);

@@ -28,7 +28,8 @@ _DTYPES = {
 }
 STATUS = {0: "RNG_OK", 1: "RNG_EINVAL", 2: "RNG_ERANGE", 3: "RNG_ENOMEM",
           4: "RNG_ECUDA", 5: "RNG_ETIMEOUT", 6: "RNG_EBUSY"}
-STEP = {"auto": 0, "barrett": 1, "montgomery": 2, "shared": 3}
+STEP = {"auto": 0, "barrett": 1, "montgomery": 2, "shared": 3, "lecuyer": 4,
+        "barrett_classic": 5}
 CONV = {"auto": 0, "int": 1, "fp64": 2}
 LAYOUT = {"auto": 0, "tiled": 1, "direct": 2}
 SKIP = {"auto": 0, "table": 1, "sqmul": 2}
@@ -42,18 +43,19 @@ class RNGError(RuntimeError):
 
 class Tune(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint32) for f in
-                ("step", "conv", "layout", "skip", "depth", "block", "grid", "unit")]
+                ("step", "conv", "layout", "skip", "depth", "block", "grid", "unit",
+                 "chains", "reserved")]
 
 
 def make_tune(step="auto", conv="auto", layout="auto", skip="auto", depth=0, block=0,
-              grid=0, unit=0) -> Tune:
+              grid=0, unit=0, chains=0) -> Tune:
     """Launch tuning; zero / "auto" lets the library choose.  Results never
     depend on it, only speed does."""
     return Tune(STEP[step] if isinstance(step, str) else step,
                 CONV[conv] if isinstance(conv, str) else conv,
                 LAYOUT[layout] if isinstance(layout, str) else layout,
                 SKIP[skip] if isinstance(skip, str) else skip,
-                depth, block, grid, unit)
+                depth, block, grid, unit, chains, 0)
 
 
 class ServerConfig(ctypes.Structure):
@@ -253,7 +255,7 @@ def resolve_tune(n: int, dtype: str = "f64", tune=None) -> dict:
     inv = lambda d, v: next((k for k, x in d.items() if x == v), v)
     return {"step": inv(STEP, res.step), "conv": inv(CONV, res.conv),
             "layout": inv(LAYOUT, res.layout), "skip": inv(SKIP, res.skip),
-            "depth": res.depth, "block": res.block, "grid": res.grid}
+            "depth": res.depth, "block": res.block, "grid": res.grid, "chains": res.chains}
 
 
 def autotune_bulk(n: int, dtype: str, candidates, reps: int = 5, out=None, stream=None):
@@ -279,7 +281,7 @@ def tune_dict(t: Tune) -> dict:
     inv = lambda d, v: next((k for k, x in d.items() if x == v), v)
     return {"step": inv(STEP, t.step), "conv": inv(CONV, t.conv),
             "layout": inv(LAYOUT, t.layout), "skip": inv(SKIP, t.skip),
-            "depth": t.depth, "block": t.block, "grid": t.grid}
+            "depth": t.depth, "block": t.block, "grid": t.grid, "chains": t.chains}
 
 
 def consume_mc(start_index: int, nblocks: int, length: int, block0: int = 0,

@@ -56,7 +56,8 @@ def test_single_stream_1e6(R, oracle_mod, dtype):
     assert s.state == (a, n)
 
 
-VARIANTS = list(itertools.product(["barrett", "montgomery", "shared"], ["int", "fp64"],
+VARIANTS = list(itertools.product(["barrett", "montgomery", "shared", "lecuyer",
+                                   "barrett_classic"], ["int", "fp64"],
                                   ["tiled", "direct"], ["table", "sqmul"]))
 
 
@@ -88,6 +89,22 @@ def test_tile_shape_and_grid_never_change_the_output(R):
         t = R.make_tune(layout="direct", block=block, grid=grid)
         out = R.generate_at(a, off, n, "f64", tune=t)
         assert torch.equal(out.view(torch.int64), ref.view(torch.int64)), (block, grid)
+
+
+@pytest.mark.parametrize("step", ["shared", "barrett"])
+def test_two_chains_per_lane(R, oracle_mod, step):
+    """Two interleaved chains per lane (each lane's run split in halves) give
+    the same bytes for every depth, block and grid."""
+    import torch
+    a, off, n = M + 777, 2 ** 33 + 5, 2 * 10 ** 5 + 13
+    for dtype in ("f64", "f32", "u64"):
+        want = oracle_mod.generate(a, off, n, dtype)
+        for depth, block, grid in [(3, 32, 1), (5, 128, 0), (15, 512, 0), (31, 256, 7),
+                                   (63, 64, 152), (255, 32, 0)]:
+            t = R.make_tune(step=step, layout="tiled", depth=depth, block=block, grid=grid,
+                            chains=2)
+            out = R.generate_at(a, off, n, dtype, tune=t)
+            assert_same(out, want, f"{step}/{dtype}/{depth}/{block}/{grid}")
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -180,7 +197,9 @@ def test_two_gib_single_stream_is_thread_count_invariant(R, oracle_mod):
                                                              grid=grid))
         assert torch.equal(out.view(torch.int64), tb), (block, grid)
         del out
-    for step, conv in [("montgomery", "int"), ("barrett", "fp64"), ("barrett", "int")]:
-        out = R.generate_at(a, 0, n, "f64", tune=R.make_tune(step=step, conv=conv))
-        assert torch.equal(out.view(torch.int64), tb), (step, conv)
+    for step, conv, chains in [("montgomery", "int", 1), ("barrett", "fp64", 1),
+                               ("barrett", "int", 1), ("shared", "int", 2)]:
+        out = R.generate_at(a, 0, n, "f64", tune=R.make_tune(step=step, conv=conv,
+                                                             chains=chains))
+        assert torch.equal(out.view(torch.int64), tb), (step, conv, chains)
         del out

@@ -184,3 +184,86 @@ def test_f32_from_f64_bits_is_truncation():
         fv = Fraction(struct.unpack("<f", struct.pack("<I", f))[0])
         nxt = Fraction(struct.unpack("<f", struct.pack("<I", f + 1))[0])
         assert fv <= v < nxt
+
+
+# ------------------------------------------------ fused consumer arithmetic
+def _sq_grid(v: float):
+    """RN(v*v) * 2^157 as (integer, shift k) the way the fused kernel forms it:
+    RNE of mant^2 to 53 bits, then M2 << k with k = 2e + sh - 1993."""
+    b = f64_bits(v)
+    e, mant = b >> 52, (b & (2 ** 52 - 1)) | 2 ** 52
+    sq = mant * mant
+    sh = 53 if sq >= 2 ** 105 else 52
+    m2, rest, half = sq >> sh, sq & (2 ** sh - 1), 2 ** (sh - 1)
+    if rest > half or (rest == half and m2 & 1):
+        m2 += 1
+    k = 2 * e + sh - 1993
+    return m2 << k, k
+
+
+def test_fused_square_grid_and_split_hit_rule():
+    """RN(v*v) is an integer on the 2^-157 grid for every variate; the hit
+    test RN(RN(x^2)+RN(y^2)) <= 1 equals: exact high parts (k >= 64) plus
+    ceilings of the small squares on the 2^-93 grid <= 2^93 + 2^40."""
+    import math
+    rnd = random.Random(7)
+    vals = [float(Fraction(z) * Fraction(R3I)) for z in states(4000, seed=8)]
+    pairs = [(rnd.choice(vals), rnd.choice(vals)) for _ in range(8000)]
+    for _ in range(4000):  # pairs on the unit circle to within a few ulps
+        x = rnd.random()
+        y = math.sqrt(max(0.0, 1 - x * x))
+        for d in (-2, -1, 0, 1, 2):
+            if 0 < y + d * 2 ** -53 < 1:
+                pairs.append((x, y + d * 2 ** -53))
+    for _ in range(2000):  # one tiny partner next to x close to 1
+        t = 2.0 ** -rnd.randint(20, 52) * (1 + rnd.random())
+        x = math.sqrt(1 - t * t)
+        for d in (-1, 0, 1):
+            pairs.append((x + d * 2 ** -53, t))
+    lim = (2 ** 157 + 2 ** 104) >> 64
+    for x, y in pairs:
+        tot = 0
+        for v in (x, y):
+            z, k = _sq_grid(v)
+            assert Fraction(z, 2 ** 157) == Fraction(v * v)
+            tot += (z >> 64) if k >= 64 else -(-z // 2 ** 64)
+            if k >= 64:
+                assert z % 2 ** 64 == 0
+            else:
+                assert z < 2 ** 117
+        assert (tot <= lim) == (x * x + y * y <= 1.0), (x, y)
+
+
+# ------------------------------------- the paper's other two reductions
+LQ, LR = M // 2 ** 25, M % 2 ** 25   # m = a*q + r with a = 2^25 (Sec. 2.1.1)
+
+
+def lecuyer_mul(s):
+    """2^25 * s mod m for 0 <= s < 4m by L'Ecuyer's decomposition."""
+    t = s // LQ
+    v = ((s - t * LQ) << 25) - t * LR
+    assert -M < v < M            # the bound Sec. 2.1.1 proves for s < 4m
+    return v + M if v < 0 else v
+
+
+def test_lecuyer_twice_is_the_step():
+    assert LR < 2 ** 25 and 2 ** 50 < M
+    for z in states(30000, seed=11):
+        s = lecuyer_mul(z << 2)      # 2^27 z mod m
+        s = lecuyer_mul(s << 1)      # 2^53 z mod m
+        assert s == (z << 53) % M
+
+
+def test_classic_barrett_step():
+    """Barrett's algorithm with k = 53 on x = 2^53 z: q1 = x >> 52, q3 = (mu q1)
+    >> 54, r = (x - q3 m) mod 2^54, then at most two subtractions of m."""
+    for z in states(30000, seed=12):
+        x = z << 53
+        q3 = (MU * (x >> 52)) >> 54
+        assert (x // M) - 2 <= q3 <= x // M
+        r = ((x % 2 ** 54) - (q3 * M) % 2 ** 54) % 2 ** 54
+        subs = 0
+        while r >= M:
+            r -= M
+            subs += 1
+        assert subs <= 2 and r == x % M

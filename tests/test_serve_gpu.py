@@ -50,7 +50,8 @@ def test_each_result_is_the_same_alone_and_in_the_mix(R, oracle_mod):
     lat, wall = srv.run_trace(arrivals, seeds, counts, dtypes, offsets=offsets, timeout_s=60.0)
     assert np.all(lat > 0) and np.isfinite(lat).all()
     st = srv.stats()
-    assert st["completed"] == n and st["iterations"] < 2 * n  # work was batched
+    assert st["completed"] == n
+    assert st["max_items_seen"] > 1  # iterations carried several requests' chunks at once
     for i in range(n):
         got = _bits(srv.read(i + 1, int(counts[i]), dtypes[i]))
         assert np.array_equal(got, alone[i]), i
@@ -94,8 +95,8 @@ def test_bad_requests_do_not_disturb_the_others(R, oracle_mod):
     with pytest.raises(R.RNGError) as e:
         srv.submit(M + 100, 0, 4 << 20, "f64")  # 32 MiB > pool
     assert e.value.status == 3
-    big = srv.submit(M + 7, 0, (15 << 20) // 8, "f64")  # fills the pool
-    waiting = srv.submit(M + 8, 0, 1 << 20, "f64")      # cannot be admitted yet
+    big = srv.submit(M + 700, 0, (15 << 20) // 8, "f64")  # fills the pool
+    waiting = srv.submit(M + 800, 0, 1 << 20, "f64")    # cannot be admitted yet
     srv.cancel(waiting)
     assert srv.status(waiting)[0] == "cancelled"
     srv.wait(good, 30.0)
