@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--no-batch", action="store_true", help="skip the batched measurement")
     p.add_argument("--no-fused", action="store_true", help="skip the fused measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--paper-table", action="store_true",
+                   help="print the paper's Table 1/2 protocol redone on this GPU and exit")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the library's built-in launch choice")
     return p.parse_args()
@@ -319,6 +321,52 @@ def measure_serving(rng, n_requests: int = 20000):
             "requests": n_requests, "bytes": total_bytes, "runs": runs}
 
 
+def paper_table(rng, n: int = N_DEFAULT, reps: int = 20):
+    """The paper's rate tables redone on this GPU (Table 1 and Table 2 of Sec. 3):
+    every reduction in the per-thread layout (each thread writes consecutive
+    positions, the paper's uncoalesced 'naive' kernels, 4096 variates per
+    thread) and in the coalesced tiled layout, plus the Constant kernel, at
+    n = 2^28 FP64; the net generation rate subtracts the Constant kernel's time
+    (Table 2's RunTime - ConstantUnrolled)."""
+    import torch
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows = []
+    const = {}
+    for layout, label in (("direct", "Naive"), ("tiled", "Coalesced")):
+        t = rng.make_tune(layout=layout)
+        ms = timed(lambda: rng.fill_constant(n, "f64", 0.5, out=out, tune=t, stream=stream))
+        const[layout] = ms
+        rows.append({"method": f"Constant{label}", "ms": ms, "gnum_s": n / ms / 1e6})
+    names = {"barrett_classic": "Barrett", "lecuyer": "LCN", "barrett": "BarrettModified",
+             "montgomery": "Montgomery", "shared": "BarrettShared"}
+    for step, name in names.items():
+        for layout, label in (("direct", ""), ("tiled", "Coalesced")):
+            t = rng.make_tune(step=step, layout=layout)
+            ms = timed(lambda: rng.generate_at_ptr(SEED, 0, n, "f64", out.data_ptr(), tune=t,
+                                                   stream=stream))
+            net = ms - const[layout]
+            rows.append({"method": name + label, "ms": ms, "gnum_s": n / ms / 1e6,
+                         "net_ms": net, "net_gnum_s": (n / net / 1e6) if net > 0 else None})
+    return {"n": n, "dtype": "f64", "reps": reps, "rows": rows,
+            "note": "paper: Tesla C2050, BarrettModified 11.44 Gnum/s, ConstantCoalesced "
+                    "12.41 Gnum/s (Table 1); BarrettOpt net 122.56 Gnum/s (Table 2)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -514,6 +562,10 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.paper_table:
+        from paper_1206_1187_gb300 import rng
+        print(json.dumps({"paper_table": paper_table(rng)}), flush=True)
+        return 0
     return run_ours(args)
 
 

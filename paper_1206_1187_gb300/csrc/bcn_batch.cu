@@ -58,8 +58,8 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const
   const uint64_t ntiles = (s1 - s0) / tile_elems;
   if (ntiles > 0) {
     Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(d.ebase, s0 + (uint64_t)lane * c, c, p.skip);
-    warp_tiles<DT, STEP, CONV>(out, s0, ntiles, c, p.jump, g, reinterpret_cast<W*>(buf0_bytes),
-                               issued, lane, 0);
+    warp_tiles<DT, STEP, CONV>(out, s0, ntiles, c, p.jump, p.jump_q, g,
+                               reinterpret_cast<W*>(buf0_bytes), issued, lane, 0);
   }
   const uint64_t r0 = s0 + ntiles * tile_elems, rl = s1 - r0;
   run_direct<DT, STEP, CONV>(out, d.ebase, p.skip, r0 + lane * rl / 32, r0 + (lane + 1) * rl / 32,
@@ -122,6 +122,7 @@ static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
   p.total_units = b->total_units;
   const uint64_t stride = (b->tune.step == ST_MONT) ? 33ull : 31ull;
   p.jump = host_pow2((53ull * stride * b->tune.depth) % kP);
+  p.jump_q = host_mulmod_quotient(p.jump);
   p.nstreams = b->nstreams;
   p.depth = b->tune.depth;
   p.unit_tiles = b->tune.unit;
@@ -464,6 +465,7 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   p.total_units = units;
   const uint64_t stride = (t.step == ST_MONT) ? 33ull : 31ull;
   p.jump = host_pow2((53ull * stride * t.depth) % kP);
+  p.jump_q = host_mulmod_quotient(p.jump);
   p.nstreams = nstreams;
   p.depth = t.depth;
   p.unit_tiles = t.unit;

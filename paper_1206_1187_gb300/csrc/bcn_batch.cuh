@@ -20,6 +20,7 @@ struct BatchParams {
   unsigned long long* counter;
   uint64_t total_units;
   uint64_t jump;
+  uint64_t jump_q;       // floor(jump * 2^64 / m)
   uint32_t nstreams;
   uint32_t depth;
   uint32_t unit_tiles;

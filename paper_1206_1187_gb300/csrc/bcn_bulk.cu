@@ -36,8 +36,11 @@ struct TiledParams {
   uint64_t ntiles;     // full tiles of 32*depth elements after the head
   uint64_t ebase;      // (seed - 3^33 + 53*i0) mod P
   uint64_t jump;       // 2^(53*31*depth) (Barrett) / 2^(53*33*depth) (Montgomery)
+  uint64_t jump_q;     // floor(jump * 2^64 / m), for the precomputed-quotient product
   uint64_t jump_a;     // two chains: 2^(53*(32c-h-1)) and 2^(53*(31c+h+1)), h = depth/2
+  uint64_t jump_aq;
   uint64_t jump_b;
+  uint64_t jump_bq;
   uint64_t cbits;      // ST_CONST: the word written
   uint32_t depth;
   uint32_t skip;
@@ -51,7 +54,7 @@ struct DirectParams {
   uint32_t skip;
 };
 
-template <int DT, int STEP, int CONV, int ILP>
+template <int DT, int STEP, int CONV, int ILP, int CDEPTH = 0>
 __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
   typedef typename Word<DT>::type W;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
   const uint32_t wpb = blockDim.x >> 5;
   const uint64_t gw = (uint64_t)blockIdx.x * wpb + warp;
   const uint64_t nw = (uint64_t)gridDim.x * wpb;
-  const uint32_t c = p.depth;
+  const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : p.depth;
   const uint32_t tile_elems = 32u * c;
   W* const buf0 = reinterpret_cast<W*>(smem + (size_t)warp * 2u * tile_elems * sizeof(W));
   W* const out = reinterpret_cast<W*>(p.out);
@@ -74,12 +77,13 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
     if constexpr (ILP == 2) {
       Gen<DT, STEP, CONV> a = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
       Gen<DT, STEP, CONV> b = lane_chain<DT, STEP, CONV>(p.ebase, first + c / 2 + 1, c, p.skip);
-      warp_tiles2<DT, STEP, CONV>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump_a, p.jump_b,
-                                  a, b, buf0, issued, lane);
+      warp_tiles2<DT, STEP, CONV, CDEPTH>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump_a,
+                                          p.jump_aq, p.jump_b, p.jump_bq, a, b, buf0, issued,
+                                          lane);
     } else {
       Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
-      warp_tiles<DT, STEP, CONV>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump, g, buf0,
-                                 issued, lane, p.cbits);
+      warp_tiles<DT, STEP, CONV, CDEPTH>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump,
+                                         p.jump_q, g, buf0, issued, lane, p.cbits);
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
@@ -107,33 +111,46 @@ __global__ void __launch_bounds__(1024) direct_kernel(const DirectParams p) {
 
 // ------------------------------------------------------------ dispatch
 template <int DT, int ST, int CV>
-static const void* pick_ilp(int layout, int ilp) {
+static const void* pick_ilp(int layout, int ilp, uint32_t depth) {
   if (layout != RNG_LAYOUT_TILED) return (const void*)direct_kernel<DT, ST, CV>;
+  // the production path gets tile depths fixed at compile time (full unroll)
+  if constexpr (ST == ST_SHARED && CV == CV_INT && DT != DT_U64) {
+    if (ilp == 2) {
+      if (depth == 9) return (const void*)tiled_kernel<DT, ST, CV, 2, 9>;
+      if (depth == 15) return (const void*)tiled_kernel<DT, ST, CV, 2, 15>;
+      if (depth == 31) return (const void*)tiled_kernel<DT, ST, CV, 2, 31>;
+    }
+  }
   if constexpr (ST == ST_BARRETT || ST == ST_SHARED)
     if (ilp == 2) return (const void*)tiled_kernel<DT, ST, CV, 2>;
+  if constexpr (ST == ST_SHARED && CV == CV_INT && DT != DT_U64) {
+    if (depth == 9) return (const void*)tiled_kernel<DT, ST, CV, 1, 9>;
+    if (depth == 15) return (const void*)tiled_kernel<DT, ST, CV, 1, 15>;
+    if (depth == 31) return (const void*)tiled_kernel<DT, ST, CV, 1, 31>;
+  }
   return (const void*)tiled_kernel<DT, ST, CV, 1>;
 }
 
 template <int DT, int ST>
-static const void* pick_cv(int layout, int cv, int ilp) {
-  return cv == CV_FP64 ? pick_ilp<DT, ST, CV_FP64>(layout, ilp)
-                       : pick_ilp<DT, ST, CV_INT>(layout, ilp);
+static const void* pick_cv(int layout, int cv, int ilp, uint32_t depth) {
+  return cv == CV_FP64 ? pick_ilp<DT, ST, CV_FP64>(layout, ilp, depth)
+                       : pick_ilp<DT, ST, CV_INT>(layout, ilp, depth);
 }
 
 template <int DT>
-static const void* pick_st(int layout, int st, int cv, int ilp) {
+static const void* pick_st(int layout, int st, int cv, int ilp, uint32_t depth) {
   if (DT == DT_U64) cv = CV_INT;  // no conversion for raw states
   switch (st) {
-    case ST_BARRETT: return pick_cv<DT, ST_BARRETT>(layout, cv, ilp);
-    case ST_MONT: return pick_cv<DT, ST_MONT>(layout, cv, 1);
-    case ST_SHARED: return pick_cv<DT, ST_SHARED>(layout, cv, ilp);
-    case ST_LECUYER: return pick_cv<DT, ST_LECUYER>(layout, cv, 1);
-    case ST_BCLASSIC: return pick_cv<DT, ST_BCLASSIC>(layout, cv, 1);
+    case ST_BARRETT: return pick_cv<DT, ST_BARRETT>(layout, cv, ilp, depth);
+    case ST_MONT: return pick_cv<DT, ST_MONT>(layout, cv, 1, depth);
+    case ST_SHARED: return pick_cv<DT, ST_SHARED>(layout, cv, ilp, depth);
+    case ST_LECUYER: return pick_cv<DT, ST_LECUYER>(layout, cv, 1, depth);
+    case ST_BCLASSIC: return pick_cv<DT, ST_BCLASSIC>(layout, cv, 1, depth);
     default: return nullptr;
   }
 }
 
-static const void* pick_kernel(int layout, int dt, int st, int cv, int ilp) {
+static const void* pick_kernel(int layout, int dt, int st, int cv, int ilp, uint32_t depth) {
   if (st == ST_CONST) {
     if (dt == DT_F64) return layout == RNG_LAYOUT_TILED
                                  ? (const void*)tiled_kernel<DT_F64, ST_CONST, CV_INT, 1>
@@ -144,9 +161,9 @@ static const void* pick_kernel(int layout, int dt, int st, int cv, int ilp) {
     return nullptr;
   }
   switch (dt) {
-    case DT_F64: return pick_st<DT_F64>(layout, st, cv, ilp);
-    case DT_F32: return pick_st<DT_F32>(layout, st, cv, ilp);
-    case DT_U64: return pick_st<DT_U64>(layout, st, cv, ilp);
+    case DT_F64: return pick_st<DT_F64>(layout, st, cv, ilp, depth);
+    case DT_F32: return pick_st<DT_F32>(layout, st, cv, ilp, depth);
+    case DT_U64: return pick_st<DT_U64>(layout, st, cv, ilp, depth);
     default: return nullptr;
   }
 }
@@ -216,7 +233,8 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   if (L.layout == RNG_LAYOUT_TILED && (L.step == ST_SHARED || L.step == ST_BARRETT) &&
       t.chains == 2 && (t.depth ? t.depth : 15) >= 3)
     L.chains = 2;
-  const void* fn = pick_kernel(L.layout, dt, L.step, L.conv, (int)L.chains);
+  const uint32_t depth0 = L.layout == RNG_LAYOUT_TILED ? (t.depth ? t.depth : 15) : 0;
+  const void* fn = pick_kernel(L.layout, dt, L.step, L.conv, (int)L.chains, depth0);
   if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   if (L.layout == RNG_LAYOUT_TILED) {
     L.depth = t.depth ? t.depth : 15;
@@ -228,6 +246,10 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
       return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024",
                        L.block);
     L.smem_bytes = (size_t)(L.block / 32) * 2 * 32 * L.depth * dtype_size(dt);
+    while (!t.block && L.smem_bytes > di.smem_optin && L.block > 32) {  // chosen block: shrink
+      L.block /= 2;
+      L.smem_bytes /= 2;
+    }
     if (L.smem_bytes > di.smem_optin)
       return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
                        L.smem_bytes, di.smem_optin);
@@ -272,7 +294,7 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
 
 rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t n,
                        void* out, uint64_t const_bits, cudaStream_t cs) {
-  const void* fn = pick_kernel(L.layout, L.dt, L.step, L.conv, (int)L.chains);
+  const void* fn = pick_kernel(L.layout, L.dt, L.step, L.conv, (int)L.chains, L.depth);
   if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   const uint64_t ebase = (L.step == ST_CONST) ? 0 : host_exponent_base(seed, i0);
   cudaError_t e;
@@ -290,9 +312,12 @@ rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t
     p.ebase = ebase;
     const uint64_t stride = (L.step == ST_MONT) ? 33ull : 31ull;
     p.jump = host_pow2((53ull * stride * L.depth) % kP);
+    p.jump_q = host_mulmod_quotient(p.jump);
     const uint64_t h = L.depth / 2;
     p.jump_a = host_pow2((53ull * (32ull * L.depth - h - 1)) % kP);
+    p.jump_aq = host_mulmod_quotient(p.jump_a);
     p.jump_b = host_pow2((53ull * (31ull * L.depth + h + 1)) % kP);
+    p.jump_bq = host_mulmod_quotient(p.jump_b);
     p.cbits = const_bits;
     p.depth = L.depth;
     p.skip = (uint32_t)L.skip;

@@ -135,14 +135,54 @@ __device__ __forceinline__ void bulk_wait_all() {
 // `issued` counts the warp's committed bulk groups: before a buffer is reused,
 // lane 0 waits until the copy that last read it is done.  Between tiles the
 // chain jumps with one product by `jump` (2^(53*31c) forward, 2^(53*33c) for
-// the backward Montgomery chain, whose state is the last element of a run).
-template <int DT, int STEP, int CONV>
+// the backward Montgomery chain, whose state is the last element of a run);
+// `jump_q` is its precomputed quotient for mulmod_pre.
+// The shared-quotient step's fast path for a whole run of c variates: no
+// per-variate branch; a lane whose run met the rare case (a variate below
+// 2^-21, probability about 2^-21 each) redoes its run exactly after a
+// warp-uniform vote.
+template <int DT, int CDEPTH>
+__device__ __forceinline__ void shared_run_fast(typename Word<DT>::type* mine, uint32_t c,
+                                                uint64_t& z) {
+  typedef typename Word<DT>::type W;
+  const uint64_t z_start = z;
+  bool rare = false;
+  if constexpr (CDEPTH > 0) {
+#pragma unroll
+    for (uint32_t i = 0; i < (uint32_t)CDEPTH; ++i) {
+      const uint64_t b = shared_step_f64_fast(z, rare);
+      if constexpr (DT == DT_F64) mine[i] = (W)b;
+      else mine[i] = (W)f32_bits_from_f64_bits(b);
+    }
+  } else {
+#pragma unroll 4
+    for (uint32_t i = 0; i < c; ++i) {
+      const uint64_t b = shared_step_f64_fast(z, rare);
+      if constexpr (DT == DT_F64) mine[i] = (W)b;
+      else mine[i] = (W)f32_bits_from_f64_bits(b);
+    }
+  }
+  if (__any_sync(0xffffffffu, rare)) {
+    if (rare) {
+      uint64_t y = z_start;
+      for (uint32_t i = 0; i < c; ++i) {
+        const uint64_t b = shared_step_f64(y);
+        if constexpr (DT == DT_F64) mine[i] = (W)b;
+        else mine[i] = (W)f32_bits_from_f64_bits(b);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int DT, int STEP, int CONV, int CDEPTH = 0>
 __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__ out,
-                                           uint64_t first, uint64_t ntiles, uint32_t c,
-                                           uint64_t jump, Gen<DT, STEP, CONV>& g,
+                                           uint64_t first, uint64_t ntiles, uint32_t c_rt,
+                                           uint64_t jump, uint64_t jump_q, Gen<DT, STEP, CONV>& g,
                                            typename Word<DT>::type* buf0, uint32_t& issued,
                                            uint32_t lane, uint64_t cbits) {
   typedef typename Word<DT>::type W;
+  const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : c_rt;
   const uint32_t tile_elems = 32u * c;
   const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
   for (uint64_t t = 0; t < ntiles; ++t) {
@@ -154,6 +194,8 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
     W* const mine = buf + lane * c;
     if constexpr (STEP == ST_CONST) {
       for (uint32_t i = 0; i < c; ++i) mine[i] = (W)cbits;
+    } else if constexpr (STEP == ST_SHARED && CONV == CV_INT && DT != DT_U64) {
+      shared_run_fast<DT, CDEPTH>(mine, c, g.z);
     } else if constexpr (STEP != ST_MONT) {
 #pragma unroll 4
       for (uint32_t i = 0; i < c; ++i) mine[i] = g.next();
@@ -169,7 +211,7 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
     }
     ++issued;
     if constexpr (STEP != ST_CONST) {
-      if (t + 1 < ntiles) g.z = mulmod(g.z, jump);
+      if (t + 1 < ntiles) g.z = mulmod_pre(g.z, jump, jump_q);
     }
   }
 }
@@ -180,14 +222,57 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
 // the other chain's work.  Stores to mine[i] and mine[h+1+i] keep lane
 // stride c (odd), so they stay bank-conflict free.  Between tiles chain a
 // jumps by 32c-h-1 steps and chain b by 31c+h+1.  Forward steps only.
-template <int DT, int STEP, int CONV>
+// Two interleaved chains of the branch-free shared-quotient step over a run
+// of c = 2h+1 elements (chain a: the first h+1, chain b: the last h); a lane
+// that left the fast path redoes its run with one exact chain.
+template <int DT, int CDEPTH>
+__device__ __forceinline__ void shared_run_fast2(typename Word<DT>::type* mine, uint32_t c,
+                                                 uint64_t& za, uint64_t& zb) {
+  typedef typename Word<DT>::type W;
+  const uint64_t a_start = za;
+  uint32_t qmin = 0xffffffffu;
+  const uint32_t h = CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : c / 2;
+#pragma unroll
+  for (uint32_t i = 0; i < h; ++i) {
+    const uint64_t x = shared_step_f64_ptx(za, qmin);
+    const uint64_t y = shared_step_f64_ptx(zb, qmin);
+    if constexpr (DT == DT_F64) {
+      mine[i] = (W)x;
+      mine[h + 1 + i] = (W)y;
+    } else {
+      mine[i] = (W)f32_bits_from_f64_bits(x);
+      mine[h + 1 + i] = (W)f32_bits_from_f64_bits(y);
+    }
+  }
+  {
+    const uint64_t x = shared_step_f64_ptx(za, qmin);
+    if constexpr (DT == DT_F64) mine[h] = (W)x;
+    else mine[h] = (W)f32_bits_from_f64_bits(x);
+  }
+  const bool rare = qmin == 0;
+  if (__any_sync(0xffffffffu, rare)) {
+    if (rare) {
+      uint64_t y = a_start;
+      for (uint32_t i = 0; i < c; ++i) {
+        const uint64_t bits = shared_step_f64(y);
+        if constexpr (DT == DT_F64) mine[i] = (W)bits;
+        else mine[i] = (W)f32_bits_from_f64_bits(bits);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int DT, int STEP, int CONV, int CDEPTH = 0>
 __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict__ out,
-                                            uint64_t first, uint64_t ntiles, uint32_t c,
-                                            uint64_t jump_a, uint64_t jump_b,
-                                            Gen<DT, STEP, CONV>& a, Gen<DT, STEP, CONV>& b,
+                                            uint64_t first, uint64_t ntiles, uint32_t c_rt,
+                                            uint64_t jump_a, uint64_t jump_aq, uint64_t jump_b,
+                                            uint64_t jump_bq, Gen<DT, STEP, CONV>& a,
+                                            Gen<DT, STEP, CONV>& b,
                                             typename Word<DT>::type* buf0, uint32_t& issued,
                                             uint32_t lane) {
   typedef typename Word<DT>::type W;
+  const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : c_rt;
   const uint32_t tile_elems = 32u * c;
   const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
   const uint32_t h = c >> 1;
@@ -198,12 +283,16 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
       __syncwarp();
     }
     W* const mine = buf + lane * c;
+    if constexpr (STEP == ST_SHARED && CONV == CV_INT && DT != DT_U64) {
+      shared_run_fast2<DT, CDEPTH>(mine, c, a.z, b.z);
+    } else {
 #pragma unroll 4
-    for (uint32_t i = 0; i < h; ++i) {
-      mine[i] = a.next();
-      mine[h + 1 + i] = b.next();
+      for (uint32_t i = 0; i < h; ++i) {
+        mine[i] = a.next();
+        mine[h + 1 + i] = b.next();
+      }
+      mine[h] = a.next();
     }
-    mine[h] = a.next();
     fence_proxy_async_shared();
     __syncwarp();
     if (lane == 0) {
@@ -212,8 +301,8 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
     }
     ++issued;
     if (t + 1 < ntiles) {
-      a.z = mulmod(a.z, jump_a);
-      b.z = mulmod(b.z, jump_b);
+      a.z = mulmod_pre(a.z, jump_a, jump_aq);
+      b.z = mulmod_pre(b.z, jump_b, jump_bq);
     }
   }
 }

@@ -70,6 +70,10 @@ constexpr uint64_t host_pow2(uint64_t e) {  // 2^e mod m, square-and-multiply
   return r;
 }
 static_assert(host_pow2(kP) == 1 && host_pow2(kP / 2) == kM - 1, "period");
+// floor(j * 2^64 / m): the precomputed quotient of a fixed multiplier j < m.
+constexpr uint64_t host_mulmod_quotient(uint64_t j) {
+  return (uint64_t)(((u128)j << 64) / kM);
+}
 
 // Fixed-base exponent table: 2^e mod m for e < P < 2^56 is the product of
 // one entry per byte of e.  Row 0 also carries the floor(3^33/2) factor of
@@ -118,6 +122,16 @@ __device__ __forceinline__ uint64_t mulmod(uint64_t x, uint64_t y) {
   r = (r >= kM) ? r - kM : r;
   r = (r >= kM) ? r - kM : r;
   return r;
+}
+
+// z*j mod m for a fixed multiplier j with its precomputed quotient
+// jq = floor(j * 2^64 / m): q = floor(z*jq / 2^64) is floor(z*j/m) or one
+// less, so z*j - q*m lies in [0, 2m) and one subtraction finishes (the
+// precomputed-quotient modular product known from Shoup's NTL).
+__device__ __forceinline__ uint64_t mulmod_pre(uint64_t z, uint64_t j, uint64_t jq) {
+  const uint64_t q = umulhi(z, jq);
+  const uint64_t r = z * j - q * kM;
+  return (r >= kM) ? r - kM : r;
 }
 
 // (e0 + 53*x) mod P for e0 < P, any 64-bit x.
@@ -276,6 +290,99 @@ __device__ __forceinline__ uint64_t shared_step_f64(uint64_t& z) {
   z = r;
   return bits;
 }
+
+// shared_step_f64 without its rare branch: the fast-path conversion is always
+// taken, and `rare` is raised when its precondition (top word of q non-zero,
+// variate >= 2^-21) fails, in which case the returned bits are meaningless
+// and the caller recomputes them with shared_step_f64.  The state advance is
+// exact either way.
+__device__ __forceinline__ uint64_t shared_step_f64_fast(uint64_t& z, bool& rare) {
+  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
+  const uint64_t t0 = (uint64_t)z0 * kK0;
+  uint64_t t1 = (uint64_t)z0 * kK1 + (t0 >> 32);
+  t1 = (uint64_t)z1 * kK0 + t1;
+  const uint64_t t2 = (uint64_t)z1 * kK1 + (t1 >> 32);
+  const uint32_t w1 = (uint32_t)t1, w2 = (uint32_t)t2, w3 = (uint32_t)(t2 >> 32);
+  const uint32_t q0 = __funnelshift_r(w1, w2, 21);
+  const uint32_t q1 = __funnelshift_r(w2, w3, 21);
+  const uint64_t qm = (uint64_t)q0 * kM0;
+  const uint32_t qm_hi = (uint32_t)(qm >> 32) + q0 * kM1 + q1 * kM0;
+  uint64_t r = ((uint64_t)(z0 << 21) << 32) - (((uint64_t)qm_hi << 32) | (uint32_t)qm);
+  if ((int64_t)r < 0) r += kM;
+  rare |= (q1 == 0);
+  const uint32_t c = __clz((int)q1);
+  const uint32_t s = c - 10;
+  const uint32_t lh = w1 << 11;
+  const uint32_t g_hi = __funnelshift_l(q0, q1, s);
+  const uint32_t g_lo = __funnelshift_l(lh, q0, s);
+  const uint64_t x = (((uint64_t)g_hi << 32) | g_lo) + (((uint64_t)(1032 - c) << 53) | 1ULL);
+  z = r;
+  return x >> 1;
+}
+
+// The same step written as inline PTX on 32-bit words, so that every
+// operation maps to one instruction: the product p = z*K needs only the high
+// half of z0*K0 (the low word of p is not used by the fast path), three
+// 32x32+64 wide multiply-adds and two funnel shifts give q and the bits below
+// it, a borrow chain with a predicated "+ m" gives the next state, and the
+// rounding is one carry chain plus a funnel shift.  `qmin` is a running
+// minimum of q's top word: it is 0 exactly when some step of the run left the
+// fast path (variate below 2^-21), and the caller then redoes the run.
+__device__ __forceinline__ uint64_t shared_step_f64_ptx(uint64_t& z, uint32_t& qmin) {
+  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
+  uint32_t r0, r1, b0, b1, qm_out;
+  asm("{\n\t"
+      ".reg .u32 a0, a1, k0, k1, m0, m1, qi, zr;\n\t"
+      ".reg .u32 h0, w1, w2, w3, t1h, q0, q1, ml, mh, zh, c, s, lh, gh, gl, ew, x0, x1;\n\t"
+      ".reg .u64 t1, t2, qm, h0w, t1hw;\n\t"
+      ".reg .pred neg;\n\t"
+      "mov.u32 a0, %5;\n\t"
+      "mov.u32 a1, %6;\n\t"
+      "mov.u32 k0, %7;\n\t"
+      "mov.u32 k1, %8;\n\t"
+      "mov.u32 m0, %9;\n\t"
+      "mov.u32 m1, %10;\n\t"
+      "mov.u32 qi, %11;\n\t"
+      "mov.u32 zr, 0;\n\t"
+      "mul.hi.u32 h0, a0, k0;\n\t"
+      "cvt.u64.u32 h0w, h0;\n\t"
+      "mad.wide.u32 t1, a0, k1, h0w;\n\t"
+      "mad.wide.u32 t1, a1, k0, t1;\n\t"
+      "mov.b64 {w1, t1h}, t1;\n\t"
+      "cvt.u64.u32 t1hw, t1h;\n\t"
+      "mad.wide.u32 t2, a1, k1, t1hw;\n\t"
+      "mov.b64 {w2, w3}, t2;\n\t"
+      "shf.r.clamp.b32 q0, w1, w2, 21;\n\t"
+      "shf.r.clamp.b32 q1, w2, w3, 21;\n\t"
+      "mul.wide.u32 qm, q0, m0;\n\t"
+      "mov.b64 {ml, mh}, qm;\n\t"
+      "mad.lo.u32 mh, q0, m1, mh;\n\t"
+      "mad.lo.u32 mh, q1, m0, mh;\n\t"
+      "shl.b32 zh, a0, 21;\n\t"
+      "sub.cc.u32 %0, zr, ml;\n\t"
+      "subc.u32 %1, zh, mh;\n\t"
+      "setp.lt.s32 neg, %1, 0;\n\t"
+      "@neg add.cc.u32 %0, %0, m0;\n\t"
+      "@neg addc.u32 %1, %1, m1;\n\t"
+      "min.u32 %4, qi, q1;\n\t"
+      "clz.b32 c, q1;\n\t"
+      "sub.u32 s, c, 10;\n\t"
+      "shl.b32 lh, w1, 11;\n\t"
+      "shf.l.clamp.b32 gh, q0, q1, s;\n\t"
+      "shf.l.clamp.b32 gl, lh, q0, s;\n\t"
+      "mad.lo.u32 ew, c, 0xFFE00000, 0x81000000;\n\t"
+      "add.cc.u32 x0, gl, 1;\n\t"
+      "addc.u32 x1, gh, ew;\n\t"
+      "shf.r.clamp.b32 %2, x0, x1, 1;\n\t"
+      "shr.b32 %3, x1, 1;\n\t"
+      "}"
+      : "=r"(r0), "=r"(r1), "=r"(b0), "=r"(b1), "=r"(qm_out)
+      : "r"(z0), "r"(z1), "r"(kK0), "r"(kK1), "r"(kM0), "r"(kM1), "r"(qmin));
+  z = ((uint64_t)r1 << 32) | r0;
+  qmin = qm_out;
+  return ((uint64_t)b1 << 32) | b0;
+}
+static_assert((1032u << 21) == 0x81000000u, "exponent constant of the PTX step");
 
 // The state advance of shared_step_f64 alone (raw-state output).
 __device__ __forceinline__ uint64_t shared_advance(uint64_t z) {

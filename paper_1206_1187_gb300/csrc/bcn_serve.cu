@@ -226,6 +226,7 @@ static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units)
   p.counter = counter;
   p.total_units = units;
   p.jump = s->jump;
+  p.jump_q = host_mulmod_quotient(s->jump);
   p.nstreams = items;
   p.depth = s->tune.depth;
   p.unit_tiles = s->tune.unit;

@@ -107,6 +107,24 @@ def test_two_chains_per_lane(R, oracle_mod, step):
             assert_same(out, want, f"{step}/{dtype}/{depth}/{block}/{grid}")
 
 
+def test_windows_around_tiny_variates(R, oracle_mod):
+    """Variates below 2^-21 leave the conversion's fast path (about one in 2^21);
+    windows of the sequence around such variates, found with the oracle, must
+    still match for every tile depth (compile-time and run-time) and layout."""
+    a = M + 100
+    states = oracle_mod.generate(a, 0, 1 << 24, "u64")
+    tiny = np.nonzero(states < np.uint64(M >> 21))[0]
+    assert tiny.size >= 3
+    for i in tiny[:6]:
+        off = max(0, int(i) - 3000)
+        want64 = oracle_mod.generate(a, off, 6001, "f64")
+        want32 = oracle_mod.generate(a, off, 6001, "f32")
+        for depth in (5, 9, 15, 31, 63):
+            t = R.make_tune(step="shared", layout="tiled", depth=depth)
+            assert_same(R.generate_at(a, off, 6001, "f64", tune=t), want64, f"f64 {i} {depth}")
+            assert_same(R.generate_at(a, off, 6001, "f32", tune=t), want32, f"f32 {i} {depth}")
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_small_misaligned_outputs_and_canaries(R, oracle_mod, dtype):
     """n = 1..97 at every element offset inside a 16-byte line; the bytes

@@ -267,3 +267,22 @@ def test_classic_barrett_step():
             r -= M
             subs += 1
         assert subs <= 2 and r == x % M
+
+
+def test_precomputed_quotient_mulmod():
+    """Multiplication by a fixed J mod m with J' = floor(J * 2^64 / m) (a
+    precomputed-quotient modular product): q = floor(z*J'/2^64) is Q or Q-1
+    for Q = floor(z*J/m), so z*J - q*m lies in [0, 2m)."""
+    rnd = random.Random(13)
+    for _ in range(300):
+        j = rnd.randrange(1, M)
+        jq = (j << 64) // M
+        for z in [1, M - 1] + [rnd.randrange(1, M) for _ in range(200)]:
+            q = (z * jq) >> 64
+            Q = (z * j) // M
+            assert q in (Q - 1, Q)
+            r = (z * j - q * M) % 2 ** 64
+            assert r < 2 * M
+            if r >= M:
+                r -= M
+            assert r == (z * j) % M
