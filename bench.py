@@ -80,18 +80,18 @@ def load_peaks():
 
 
 def profiled_traffic(tag: str):
-    return profiled_value("traffic_bytes_per_launch", tag)
+    return profiled_value("traffic_bytes_per_launch", tag, "tiled")
 
 
-def profiled_value(key: str, tag: str):
+def profiled_value(key: str, tag: str, kernel: str = "tiled"):
     """A counter-derived number recorded in profiles/ for the current sources.
 
     A summary line reads `<key>[<tag>]: <value> digest <hex>`; the value is
-    used only if <hex> matches the library's current source digest (a changed
-    kernel invalidates its counters)."""
+    used only if <hex> matches the digest of the sources `kernel` is built
+    from (a changed kernel invalidates its counters)."""
     try:
         from paper_1206_1187_gb300 import _build
-        digest = _build._inputs_digest([])[:16]
+        digest = _build.kernel_digest(kernel)
     except Exception:
         return None
     pat = re.compile(re.escape(key) + r"\[" + re.escape(tag) +
@@ -273,7 +273,7 @@ def measure_fused(rng, stream, steps: int):
                        "of squares, nothing stored",
            "launches": steps, "ms_per_launch": ms, "variates_per_s": variates / (ms / 1e3),
            "pi_estimate": pi_est}
-    ipv = profiled_value("inst_per_variate", "mc_2e36")
+    ipv = profiled_value("inst_per_variate", "mc_2e36", "mc")
     if ipv is not None:  # integer-issue roofline: 4 schedulers x 32 lanes per SM per clock
         clk = 2.07e9
         peak = 152 * 4 * 32 * clk

@@ -53,6 +53,26 @@ def _inputs_digest(extra_flags: list[str]) -> str:
     return h.hexdigest()
 
 
+# The sources each kernel is compiled from, for per-kernel digests (a
+# profiler counter recorded for a kernel stays valid while these are unchanged).
+KERNEL_SOURCES = {
+    "tiled": ["bcn_bulk.cu", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
+    "batch": ["bcn_batch.cu", "bcn_batch.cuh", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
+    "mc": ["bcn_mc.cu", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
+}
+
+
+def kernel_digest(kernel: str) -> str:
+    """16 hex digits identifying the sources and flags one kernel is built from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    h.update(" ".join(f for f in NVCC_FLAGS if not os.path.isabs(f)).encode())  # no paths
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     """Compile and link the library if any source changed; return its path."""
     extra_flags = list(extra_flags or [])

@@ -133,9 +133,14 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
   const uint64_t lim0 = 1ull << 40, lim1 = 1ull << 29;
   if (j0 < j1) {
     uint64_t z = seed_state(exponent_add(p.ebase, first + 1), p.skip);
-    for (uint64_t j = j0; j < j1; ++j) {
-      const Terms x = variate_terms(shared_step_f64(z));
-      const Terms y = variate_terms(shared_step_f64(z));
+    // One pair of variates into the accumulators; `exact` selects the
+    // conversion with its own rare-case branch, else the branch-free one
+    // that only lowers qmin when it cannot be trusted.
+    auto pair = [&](bool exact, uint32_t& qmin) {
+      const uint64_t bx = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
+      const uint64_t by = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
+      const Terms x = variate_terms(bx);
+      const Terms y = variate_terms(by);
       add128(a0, a1, x.v0, x.v1);
       add128(a0, a1, y.v0, y.v1);
       uint64_t r0 = x.q0, r1 = x.q1;
@@ -149,7 +154,25 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
         add128(l0, l1, x.s0, x.s1);
         add128(l0, l1, y.s0, y.s1);
       }
+    };
+    // Chunks of kChunk pairs with the branch-free conversion; a lane whose
+    // chunk met a variate below 2^-21 (about one chunk in 2^14) restores the
+    // chunk's starting point and redoes it exactly.
+    constexpr uint32_t kChunk = 64;
+    uint64_t j = j0;
+    for (; j + kChunk <= j1; j += kChunk) {
+      const uint64_t zs = z, sa0 = a0, sa1 = a1, sh0 = h0, sh1 = h1, sl0 = l0, sl1 = l1;
+      const uint32_t shits = hits;
+      uint32_t qmin = 0xffffffffu;
+#pragma unroll 4
+      for (uint32_t k = 0; k < kChunk; ++k) pair(false, qmin);
+      if (__builtin_expect(qmin == 0, 0)) {
+        z = zs; a0 = sa0; a1 = sa1; h0 = sh0; h1 = sh1; l0 = sl0; l1 = sl1; hits = shits;
+        uint32_t unused = 0;
+        for (uint32_t k = 0; k < kChunk; ++k) pair(true, unused);
+      }
     }
+    for (uint32_t unused = 0; j < j1; ++j) pair(true, unused);
   }
   // exact warp reduction (integer addition is order-free)
 #pragma unroll

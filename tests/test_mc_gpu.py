@@ -55,6 +55,22 @@ def test_block_offset_and_launch_shape(R, oracle_mod):
     assert np.array_equal(ref[3].view(np.int64), o2.view(np.int64))
 
 
+def test_blocks_holding_tiny_variates(R, oracle_mod):
+    """Blocks that contain variates below 2^-21 (which leave the branch-free
+    conversion and force the exact redo of their chunk) still match."""
+    a, length = M + 100, 4096
+    states = oracle_mod.generate(a, 0, 1 << 24, "u64")
+    tiny = np.nonzero(states < np.uint64(M >> 21))[0]
+    blocks = sorted({int(i) // length for i in tiny})
+    assert len(blocks) >= 3
+    for b in blocks[:5]:
+        total, hits, s1, s2 = _run(R, a, 3, length, block0=b - 1)
+        oh, o1, o2 = oracle_mod.mc(a, length, np.arange(b - 1, b + 2))
+        assert np.array_equal(hits, oh.astype(np.int64)), b
+        assert np.array_equal(s1.view(np.int64), o1.view(np.int64)), b
+        assert np.array_equal(s2.view(np.int64), o2.view(np.int64)), b
+
+
 def test_bad_arguments(R):
     with pytest.raises(R.RNGError):
         R.consume_mc(M + 100, 4, 7)      # odd length
