@@ -211,10 +211,12 @@ def measure_batched(rng, stream, achieved_gbs: float, steps: int):
     and FP32 alternating, one persistent launch replayed as a CUDA graph."""
     import torch
     from paper_1206_1187_gb300 import inputs
+    from paper_1206_1187_gb300 import autotune
+    tuned = autotune.tune_batch()  # measured batch-plan tuning, cached per GPU model
     starts, counts, dtypes = inputs.batch_streams()
     tdt = {"f64": torch.float64, "f32": torch.float32}
     outs = [torch.empty(int(c), dtype=tdt[d], device="cuda") for c, d in zip(counts, dtypes)]
-    b = rng.Batch(starts, counts, dtypes, outs=outs)
+    b = rng.Batch(starts, counts, dtypes, outs=outs, tune=tuned["best"])
     info = b.info()
     for _ in range(3):
         b.graph_launch(stream)

@@ -1,0 +1,58 @@
+// bcn_device.cuh -- the alpha_{2,3} generator as a device-side object for your
+// own kernels: a 64-bit state per thread, positioned anywhere in a sequence by
+// skip-ahead, producing the same variates as the library's bulk calls.
+//
+// The paper points out the generator's advantage for simulations running on
+// the GPU: independent subsequences per thread with only a 64-bit state and no
+// shared memory (Sec. 2).  Typical use:
+//
+//   #include "bcn_device.cuh"
+//   __global__ void sim(uint64_t seed, ...) {
+//     bcn_device::Stream g = bcn_device::make_stream(seed, my_first_variate);
+//     for (...) { double u = bcn_device::next_f64(g); ... }
+//   }
+//
+// Variate i of the sequence seeded with start index a (Algorithm BB) is
+// RN(z * r3i) for z = 2^((a - 3^33 + 53*(i+1)) mod P) * floor(3^33/2) mod 3^33,
+// exactly as rng_generate_at writes it, so results do not depend on how the
+// work is split over threads.  Compile with nvcc for sm_103a with this
+// directory on the include path.  The start index must satisfy Algorithm BB,
+// step 1 (3^33+100 <= a <= 2^53); nothing is checked on the device.
+#pragma once
+#include <cstdint>
+
+#include "bcn_math.cuh"
+
+namespace bcn_device {
+
+struct Stream {
+  uint64_t z;  // state of the next variate
+};
+
+// A generator positioned at variate `offset` (0-based) of the sequence seeded
+// with `start_index`: one fixed-base exponentiation (six modular products).
+__device__ inline Stream make_stream(uint64_t start_index, uint64_t offset) {
+  const uint64_t e0 = (start_index - bcn::kM) % bcn::kP;
+  Stream s;
+  s.z = bcn::seed_state_table(bcn::exponent_add(e0, offset + 1));
+  return s;
+}
+
+// The next variate as a double in (0,1): RN(z * r3i), exactly.
+__device__ inline double next_f64(Stream& s) {
+  return __longlong_as_double((long long)bcn::shared_step_f64(s.z));
+}
+
+// The next variate as a float in (0,1): the double variate rounded toward zero.
+__device__ inline float next_f32(Stream& s) {
+  return __uint_as_float(bcn::f32_bits_from_f64_bits(bcn::shared_step_f64(s.z)));
+}
+
+// The next raw state z in [1, 3^33).
+__device__ inline uint64_t next_state(Stream& s) {
+  const uint64_t z = s.z;
+  s.z = bcn::shared_advance(z);
+  return z;
+}
+
+}  // namespace bcn_device

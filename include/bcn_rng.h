@@ -109,7 +109,9 @@ typedef struct {
   uint32_t unit;    /* BATCH: tiles per work unit (0 = choose); else ignored */
   uint32_t chains;  /* TILED, forward steps: independent chains per lane, 1
                        or 2 (0 = choose); 2 splits each lane's run in halves */
-  uint32_t reserved;
+  uint32_t buffers; /* TILED: shared-memory tile buffers per warp, 1 or 2 (0 =
+                       choose); 1 halves the shared memory, so more warps fit,
+                       at the cost of waiting for each tile's copy to be read */
 } rng_tune;
 
 /* Largest n accepted by one generation call. */
@@ -330,6 +332,16 @@ rng_status rng_pool_destroy(bcn_pool *p);
 rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblocks, uint64_t len,
                           uint64_t *hits_total, uint64_t *hits, double *sum, double *sumsq,
                           void *cuda_stream, const rng_tune *tune);
+
+/* Run a kernel written only against the device-side API (bcn_device.cuh):
+ * `threads` threads each create their own generator at their first variate
+ * and write variates offset .. offset+n-1 of the sequence seeded with
+ * start_index, as FP64 to out_f64 and FP32 to out_f32 (caller-owned device
+ * arrays of n elements).  Exposes the device API to the same checks as every
+ * other path.  Asynchronous on `cuda_stream`. */
+rng_status rng_device_api_check(uint64_t start_index, uint64_t offset, uint64_t n,
+                                double *out_f64, float *out_f32, uint32_t threads,
+                                void *cuda_stream);
 
 /* -------------------------------------------------------------- autotune */
 

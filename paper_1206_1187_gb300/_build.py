@@ -44,7 +44,8 @@ def _sources() -> list[str]:
 def _inputs_digest(extra_flags: list[str]) -> str:
     h = hashlib.sha256()
     files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
-        glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
+        glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h"))) + \
+        sorted(glob.glob(os.path.join(INCLUDE, "*.cuh")))
     for f in files:
         h.update(f.encode())
         with open(f, "rb") as fh:
@@ -62,11 +63,16 @@ KERNEL_SOURCES = {
 }
 
 
+def _source_path(name: str) -> str:
+    p = os.path.join(CSRC, name)
+    return p if os.path.exists(p) else os.path.join(INCLUDE, name)
+
+
 def kernel_digest(kernel: str) -> str:
     """16 hex digits identifying the sources and flags one kernel is built from."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(CSRC, name), "rb") as fh:
+        with open(_source_path(name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
     h.update(" ".join(f for f in NVCC_FLAGS if not os.path.isabs(f)).encode())  # no paths

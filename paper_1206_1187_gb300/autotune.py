@@ -33,8 +33,11 @@ def bulk_candidates(dtype: str) -> list[dict]:
             for depth in DEPTHS:
                 for block in BLOCKS:
                     for chains in ((1, 2) if step != "montgomery" else (1,)):
-                        cands.append(dict(step=step, conv=conv, layout="tiled", depth=depth,
-                                          block=block, chains=chains))
+                        # one tile buffer per warp only pays where tiles are deep
+                        for buffers in ((1, 2) if depth >= 15 and step == "shared" else (2,)):
+                            cands.append(dict(step=step, conv=conv, layout="tiled",
+                                              depth=depth, block=block, chains=chains,
+                                              buffers=buffers))
     return cands
 
 
@@ -80,4 +83,54 @@ def tune_bulk(dtype: str = "f64", n: int = 1 << 26, reps: int = 5, candidates=No
         b = dict(entry["best"])
         b.pop("grid", None)
         rng.set_auto_tune(dtype, b)
+    return entry
+
+
+BATCH_DEPTHS = (15, 31)
+BATCH_BLOCKS = (128, 256, 512)
+BATCH_UNITS = (4, 16, 64)
+
+
+def batch_candidates() -> list[dict]:
+    return [dict(step="shared", conv="int", depth=d, block=b, chains=c, unit=u)
+            for d in BATCH_DEPTHS for b in BATCH_BLOCKS for c in (1, 2) for u in BATCH_UNITS]
+
+
+def tune_batch(nstreams: int = 512, reps: int = 3, use_cache: bool = True) -> dict:
+    """Time batch-plan tunings on a representative batch (the batched workload's
+    generator, lengths log-uniform 10^3..10^6) and return
+    {"best": tuning, "table": [[candidate, ms], ...]}; cached per GPU model."""
+    from . import inputs
+    key = f"{torch.cuda.get_device_name(torch.cuda.current_device())}|batch|{nstreams}" \
+          f"|v{rng.version()}"
+    with _lock:
+        cache = _load_cache() if use_cache else {}
+        if key in cache:
+            return cache[key]
+        starts, counts, dtypes = inputs.batch_streams(nstreams=nstreams, len_hi=1e6)
+        tdt = {"f64": torch.float64, "f32": torch.float32}
+        outs = [torch.empty(int(c), dtype=tdt[d], device="cuda") for c, d in zip(counts, dtypes)]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        table = []
+        for cand in batch_candidates():
+            try:
+                b = rng.Batch(starts, counts, dtypes, outs=outs, tune=cand)
+            except rng.RNGError:
+                table.append([cand, -1.0])
+                continue
+            b.launch()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                b.launch()
+            e1.record()
+            torch.cuda.synchronize()
+            table.append([cand, e0.elapsed_time(e1) / reps])
+            b.close()
+        ranked = sorted((t for t in table if t[1] > 0), key=lambda t: t[1])
+        entry = {"best": ranked[0][0], "table": table, "nstreams": nstreams}
+        if use_cache:
+            cache[key] = entry
+            _store_cache(cache)
     return entry

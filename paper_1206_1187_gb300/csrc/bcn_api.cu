@@ -217,10 +217,10 @@ rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune* in, rng_tu
   out->grid = L.grid;
   out->unit = 0;
   out->chains = L.chains;
-  out->reserved = 0;
+  out->buffers = L.buffers;
   return RNG_OK;
 }
 
-int rng_version(void) { return 101; }
+int rng_version(void) { return 102; }
 
 }  // extern "C"

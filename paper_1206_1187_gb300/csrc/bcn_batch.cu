@@ -40,13 +40,13 @@ namespace bcn {
 
 // The unit's elements [s0, s1) of stream d: full tiles by bulk copy, the
 // remainder by plain stores; unit 0 also writes the head [0, head).
-template <int DT, int STEP, int CONV>
+template <int DT, int STEP, int CONV, int ILP, int CDEPTH>
 __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const BatchParams& p,
                                            unsigned char* buf0_bytes, uint32_t& issued,
                                            uint32_t lane) {
   typedef typename Word<DT>::type W;
   W* const out = reinterpret_cast<W*>(d.out);
-  const uint32_t c = p.depth;
+  const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : p.depth;
   const uint64_t tile_elems = 32ull * c;
   const uint64_t unit_elems = tile_elems * p.unit_tiles;
   const uint64_t s0 = d.head + k * unit_elems;
@@ -57,16 +57,25 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const
   if (s0 >= s1) return;
   const uint64_t ntiles = (s1 - s0) / tile_elems;
   if (ntiles > 0) {
-    Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(d.ebase, s0 + (uint64_t)lane * c, c, p.skip);
-    warp_tiles<DT, STEP, CONV>(out, s0, ntiles, c, p.jump, p.jump_q, g,
-                               reinterpret_cast<W*>(buf0_bytes), issued, lane, 0);
+    const uint64_t first = s0 + (uint64_t)lane * c;
+    if constexpr (ILP == 2) {
+      Gen<DT, STEP, CONV> a = lane_chain<DT, STEP, CONV>(d.ebase, first, c, p.skip);
+      Gen<DT, STEP, CONV> b = lane_chain<DT, STEP, CONV>(d.ebase, first + c / 2 + 1, c, p.skip);
+      warp_tiles2<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.jump_a, p.jump_aq, p.jump_b,
+                                          p.jump_bq, a, b, reinterpret_cast<W*>(buf0_bytes),
+                                          issued, lane);
+    } else {
+      Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(d.ebase, first, c, p.skip);
+      warp_tiles<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.jump, p.jump_q, g,
+                                         reinterpret_cast<W*>(buf0_bytes), issued, lane, 0);
+    }
   }
   const uint64_t r0 = s0 + ntiles * tile_elems, rl = s1 - r0;
   run_direct<DT, STEP, CONV>(out, d.ebase, p.skip, r0 + lane * rl / 32, r0 + (lane + 1) * rl / 32,
                              0);
 }
 
-template <int STEP, int CONV>
+template <int STEP, int CONV, int ILP, int CDEPTH>
 __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31;
@@ -88,30 +97,56 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams p) {
     }
     const BatchDesc d = p.desc[lo];
     const uint64_t k = u - d.unit0;
-    if (d.dt == DT_F64) batch_unit<DT_F64, STEP, CONV>(d, k, p, buf0, issued, lane);
-    else if (d.dt == DT_F32) batch_unit<DT_F32, STEP, CONV>(d, k, p, buf0, issued, lane);
-    else batch_unit<DT_U64, STEP, CONV>(d, k, p, buf0, issued, lane);
+    if (d.dt == DT_F64) batch_unit<DT_F64, STEP, CONV, ILP, CDEPTH>(d, k, p, buf0, issued, lane);
+    else if (d.dt == DT_F32) batch_unit<DT_F32, STEP, CONV, ILP, CDEPTH>(d, k, p, buf0, issued, lane);
+    else batch_unit<DT_U64, STEP, CONV, ILP, 0>(d, k, p, buf0, issued, lane);
   }
   if (lane == 0) bulk_wait_all();
   __syncwarp();
 }
 
-static const void* pick_batch(int st, int cv) {
+static const void* pick_batch(int st, int cv, int ilp, uint32_t depth) {
+  if (st == ST_SHARED && cv == CV_INT) {  // the production path: fixed depths
+    if (ilp == 2) {
+      if (depth == 15) return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 15>;
+      if (depth == 31) return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 31>;
+      return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 0>;
+    }
+    if (depth == 15) return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 15>;
+    if (depth == 31) return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 31>;
+    return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 0>;
+  }
   switch (st) {
-    case ST_SHARED: return cv == CV_FP64 ? (const void*)batch_kernel<ST_SHARED, CV_FP64>
-                                         : (const void*)batch_kernel<ST_SHARED, CV_INT>;
-    case ST_BARRETT: return cv == CV_FP64 ? (const void*)batch_kernel<ST_BARRETT, CV_FP64>
-                                          : (const void*)batch_kernel<ST_BARRETT, CV_INT>;
-    case ST_MONT: return cv == CV_FP64 ? (const void*)batch_kernel<ST_MONT, CV_FP64>
-                                       : (const void*)batch_kernel<ST_MONT, CV_INT>;
+    case ST_SHARED: return (const void*)batch_kernel<ST_SHARED, CV_FP64, 1, 0>;
+    case ST_BARRETT:
+      if (ilp == 2) return cv == CV_FP64 ? (const void*)batch_kernel<ST_BARRETT, CV_FP64, 2, 0>
+                                         : (const void*)batch_kernel<ST_BARRETT, CV_INT, 2, 0>;
+      return cv == CV_FP64 ? (const void*)batch_kernel<ST_BARRETT, CV_FP64, 1, 0>
+                           : (const void*)batch_kernel<ST_BARRETT, CV_INT, 1, 0>;
+    case ST_MONT: return cv == CV_FP64 ? (const void*)batch_kernel<ST_MONT, CV_FP64, 1, 0>
+                                       : (const void*)batch_kernel<ST_MONT, CV_INT, 1, 0>;
     default: return nullptr;
   }
 }
 
-const void* batch_kernel_fn(int step, int conv) { return pick_batch(step, conv); }
+const void* batch_kernel_fn(int step, int conv, int chains, uint32_t depth) {
+  return pick_batch(step, conv, chains, depth);
+}
+
+void batch_fill_jumps(BatchParams& p, int step, uint32_t depth) {
+  const uint64_t stride = (step == ST_MONT) ? 33ull : 31ull;
+  p.jump = host_pow2((53ull * stride * depth) % kP);
+  p.jump_q = host_mulmod_quotient(p.jump);
+  const uint64_t h = depth / 2;
+  p.jump_a = host_pow2((53ull * (32ull * depth - h - 1)) % kP);
+  p.jump_aq = host_mulmod_quotient(p.jump_a);
+  p.jump_b = host_pow2((53ull * (31ull * depth + h + 1)) % kP);
+  p.jump_bq = host_mulmod_quotient(p.jump_b);
+}
 
 static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
-  const void* fn = pick_batch((int)b->tune.step, (int)b->tune.conv);
+  const void* fn = pick_batch((int)b->tune.step, (int)b->tune.conv, (int)b->tune.chains,
+                              b->tune.depth);
   if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
   unsigned char* base = static_cast<unsigned char*>(b->dev);
   BatchParams p;
@@ -120,9 +155,7 @@ static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
   p.counter = reinterpret_cast<unsigned long long*>(base + sizeof(BatchDesc) * b->nstreams +
                                                     sizeof(uint64_t) * (b->nstreams + 1));
   p.total_units = b->total_units;
-  const uint64_t stride = (b->tune.step == ST_MONT) ? 33ull : 31ull;
-  p.jump = host_pow2((53ull * stride * b->tune.depth) % kP);
-  p.jump_q = host_mulmod_quotient(p.jump);
+  batch_fill_jumps(p, (int)b->tune.step, b->tune.depth);
   p.nstreams = b->nstreams;
   p.depth = b->tune.depth;
   p.unit_tiles = b->tune.unit;
@@ -155,10 +188,11 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   if (!t.step) t.step = d.step ? d.step : ST_SHARED;
   if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
   if (!t.skip) t.skip = SK_TABLE;
-  if (!t.depth) t.depth = d.depth ? d.depth : 15;
+  if (!t.depth) t.depth = 15;
   if (!t.block) t.block = 256;
   if (!t.unit) t.unit = 16;  // tiles per work unit
   t.layout = RNG_LAYOUT_TILED;
+  t.chains = batch_chains(t);
   if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
     return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
   if (t.conv != CV_INT && t.conv != CV_FP64)
@@ -237,7 +271,7 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
     delete b;
     return cuda_error(e, "uploading the batch plan");
   }
-  const void* fn = pick_batch((int)t.step, (int)t.conv);
+  const void* fn = pick_batch((int)t.step, (int)t.conv, (int)t.chains, t.depth);
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin);
   if (e != cudaSuccess) {
     cudaFree(b->dev);
@@ -372,9 +406,10 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   if (!t.step) t.step = d.step ? d.step : ST_SHARED;
   if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
   if (!t.skip) t.skip = SK_TABLE;
-  if (!t.depth) t.depth = d.depth ? d.depth : 15;
+  if (!t.depth) t.depth = 15;
   if (!t.block) t.block = 256;
   if (!t.unit) t.unit = 16;
+  t.chains = batch_chains(t);
   if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
     return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
   if (t.conv != CV_INT && t.conv != CV_FP64)
@@ -396,7 +431,7 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
     return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
                      smem, di.smem_optin);
   const uint64_t unit_elems = 32ull * t.depth * t.unit;
-  const void* fn = pick_batch((int)t.step, (int)t.conv);
+  const void* fn = pick_batch((int)t.step, (int)t.conv, (int)t.chains, t.depth);
   if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
   cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
 
@@ -463,9 +498,7 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   p.prefix = reinterpret_cast<const uint64_t*>(base + kNoallocDescBytes);
   p.counter = counter;
   p.total_units = units;
-  const uint64_t stride = (t.step == ST_MONT) ? 33ull : 31ull;
-  p.jump = host_pow2((53ull * stride * t.depth) % kP);
-  p.jump_q = host_mulmod_quotient(p.jump);
+  batch_fill_jumps(p, (int)t.step, t.depth);
   p.nstreams = nstreams;
   p.depth = t.depth;
   p.unit_tiles = t.unit;

@@ -21,15 +21,27 @@ struct BatchParams {
   uint64_t total_units;
   uint64_t jump;
   uint64_t jump_q;       // floor(jump * 2^64 / m)
+  uint64_t jump_a, jump_aq, jump_b, jump_bq;  // two chains per lane
   uint32_t nstreams;
   uint32_t depth;
   uint32_t unit_tiles;
   uint32_t skip;
 };
 
-// The batched kernel for a step variant and conversion (nullptr if none), and
-// the dynamic shared memory one block of it needs.
-const void* batch_kernel_fn(int step, int conv);
+// The batched kernel for a step variant, conversion, chains per lane and tile
+// depth (nullptr if none), and the dynamic shared memory one block needs.
+const void* batch_kernel_fn(int step, int conv, int chains, uint32_t depth);
+
+// Chains per lane a batched launch uses for this tuning (2 only for the forward
+// steps with depth >= 3; 0 in the tuning means 2 for the shared step).
+inline uint32_t batch_chains(const rng_tune& t) {
+  const bool forward = (t.step == ST_SHARED && t.conv != CV_FP64) || t.step == ST_BARRETT;
+  const uint32_t want = t.chains ? t.chains : (t.step == ST_SHARED ? 2u : 1u);
+  return (forward && want == 2 && t.depth >= 3) ? 2u : 1u;
+}
+
+// Fill the tile-jump multipliers (and their precomputed quotients) of p.
+void batch_fill_jumps(BatchParams& p, int step, uint32_t depth);
 inline size_t batch_smem_bytes(uint32_t block, uint32_t depth) {
   return (size_t)(block / 32) * 2 * 32 * depth * 8;
 }

@@ -44,6 +44,7 @@ struct TiledParams {
   uint64_t cbits;      // ST_CONST: the word written
   uint32_t depth;
   uint32_t skip;
+  uint32_t nbuf;       // tile buffers per warp (1 or 2)
 };
 
 struct DirectParams {
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
   const uint64_t nw = (uint64_t)gridDim.x * wpb;
   const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : p.depth;
   const uint32_t tile_elems = 32u * c;
-  W* const buf0 = reinterpret_cast<W*>(smem + (size_t)warp * 2u * tile_elems * sizeof(W));
+  W* const buf0 = reinterpret_cast<W*>(smem + (size_t)warp * p.nbuf * tile_elems * sizeof(W));
   W* const out = reinterpret_cast<W*>(p.out);
 
   const uint64_t t0 = gw * p.ntiles / nw;
@@ -79,11 +80,11 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
       Gen<DT, STEP, CONV> b = lane_chain<DT, STEP, CONV>(p.ebase, first + c / 2 + 1, c, p.skip);
       warp_tiles2<DT, STEP, CONV, CDEPTH>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump_a,
                                           p.jump_aq, p.jump_b, p.jump_bq, a, b, buf0, issued,
-                                          lane);
+                                          lane, p.nbuf);
     } else {
       Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
       warp_tiles<DT, STEP, CONV, CDEPTH>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump,
-                                         p.jump_q, g, buf0, issued, lane, p.cbits);
+                                         p.jump_q, g, buf0, issued, lane, p.cbits, p.nbuf);
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
@@ -204,6 +205,7 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
       if (!t.depth) t.depth = d.depth;
       if (!t.block) t.block = d.block;
       if (!t.chains) t.chains = d.chains;
+      if (!t.buffers) t.buffers = d.buffers;
     }
   }
   BulkLaunch L = {};
@@ -245,7 +247,9 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
     if (L.block % 32 != 0 || L.block == 0 || L.block > 1024)
       return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024",
                        L.block);
-    L.smem_bytes = (size_t)(L.block / 32) * 2 * 32 * L.depth * dtype_size(dt);
+    if (t.buffers > 2) return set_error(RNG_EINVAL, "tune.buffers %u must be 0, 1 or 2", t.buffers);
+    L.buffers = t.buffers ? t.buffers : 2;
+    L.smem_bytes = (size_t)(L.block / 32) * L.buffers * 32 * L.depth * dtype_size(dt);
     while (!t.block && L.smem_bytes > di.smem_optin && L.block > 32) {  // chosen block: shrink
       L.block /= 2;
       L.smem_bytes /= 2;
@@ -321,6 +325,7 @@ rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t
     p.cbits = const_bits;
     p.depth = L.depth;
     p.skip = (uint32_t)L.skip;
+    p.nbuf = L.buffers;
     void* args[] = {&p};
     e = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.block), args, L.smem_bytes, cs);
   } else {

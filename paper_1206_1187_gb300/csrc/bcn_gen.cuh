@@ -124,6 +124,21 @@ __device__ __forceinline__ void bulk_commit() {
 __device__ __forceinline__ void bulk_wait_read_1() {
   asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
 }
+__device__ __forceinline__ void bulk_wait_read_0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// Before a warp refills a tile buffer: with two buffers, the copy committed
+// two tiles ago (the last reader of this buffer) must be done reading; with
+// one buffer, the previous copy must be.
+__device__ __forceinline__ void wait_buffer_free(uint32_t issued, uint32_t nbuf, uint32_t lane) {
+  if (issued >= nbuf) {
+    if (lane == 0) {
+      if (nbuf == 1) bulk_wait_read_0();
+      else bulk_wait_read_1();
+    }
+    __syncwarp();
+  }
+}
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
@@ -180,17 +195,14 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
                                            uint64_t first, uint64_t ntiles, uint32_t c_rt,
                                            uint64_t jump, uint64_t jump_q, Gen<DT, STEP, CONV>& g,
                                            typename Word<DT>::type* buf0, uint32_t& issued,
-                                           uint32_t lane, uint64_t cbits) {
+                                           uint32_t lane, uint64_t cbits, uint32_t nbuf = 2) {
   typedef typename Word<DT>::type W;
   const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : c_rt;
   const uint32_t tile_elems = 32u * c;
   const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
   for (uint64_t t = 0; t < ntiles; ++t) {
-    W* const buf = buf0 + (issued & 1u) * tile_elems;
-    if (issued >= 2) {  // the copy that last read this buffer must be done
-      if (lane == 0) bulk_wait_read_1();
-      __syncwarp();
-    }
+    W* const buf = buf0 + (issued % nbuf) * tile_elems;
+    wait_buffer_free(issued, nbuf, lane);
     W* const mine = buf + lane * c;
     if constexpr (STEP == ST_CONST) {
       for (uint32_t i = 0; i < c; ++i) mine[i] = (W)cbits;
@@ -270,18 +282,15 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
                                             uint64_t jump_bq, Gen<DT, STEP, CONV>& a,
                                             Gen<DT, STEP, CONV>& b,
                                             typename Word<DT>::type* buf0, uint32_t& issued,
-                                            uint32_t lane) {
+                                            uint32_t lane, uint32_t nbuf = 2) {
   typedef typename Word<DT>::type W;
   const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : c_rt;
   const uint32_t tile_elems = 32u * c;
   const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
   const uint32_t h = c >> 1;
   for (uint64_t t = 0; t < ntiles; ++t) {
-    W* const buf = buf0 + (issued & 1u) * tile_elems;
-    if (issued >= 2) {
-      if (lane == 0) bulk_wait_read_1();
-      __syncwarp();
-    }
+    W* const buf = buf0 + (issued % nbuf) * tile_elems;
+    wait_buffer_free(issued, nbuf, lane);
     W* const mine = buf + lane * c;
     if constexpr (STEP == ST_SHARED && CONV == CV_INT && DT != DT_U64) {
       shared_run_fast2<DT, CDEPTH>(mine, c, a.z, b.z);

@@ -23,7 +23,7 @@ constexpr uint32_t kMaxDepth = 255;
 // A fully resolved bulk launch.
 struct BulkLaunch {
   int dt, step, conv, layout, skip;
-  uint32_t depth, block, grid, chains;
+  uint32_t depth, block, grid, chains, buffers;
   size_t smem_bytes;  // TILED only
 };
 

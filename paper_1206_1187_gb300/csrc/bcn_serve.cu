@@ -69,7 +69,6 @@ struct bcn_server {
   const void* fn = nullptr;
   size_t smem = 0;
   uint64_t grid_full = 0;
-  uint64_t jump = 0;
   int device = 0;
   unsigned char* pool_dev = nullptr;
   bcn::Pool pool;
@@ -225,8 +224,7 @@ static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units)
   p.prefix = reinterpret_cast<const uint64_t*>(sl.d_table + desc_bytes);
   p.counter = counter;
   p.total_units = units;
-  p.jump = s->jump;
-  p.jump_q = host_mulmod_quotient(s->jump);
+  batch_fill_jumps(p, (int)s->tune.step, s->tune.depth);
   p.nstreams = items;
   p.depth = s->tune.depth;
   p.unit_tiles = s->tune.unit;
@@ -305,12 +303,13 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
   if (!t.step) t.step = d.step ? d.step : ST_SHARED;
   if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
   if (!t.skip) t.skip = SK_TABLE;
-  if (!t.depth) t.depth = d.depth ? d.depth : 15;
+  if (!t.depth) t.depth = 15;
   if (!t.block) t.block = 256;
   if (!t.unit) t.unit = 4;
+  t.chains = batch_chains(t);
   if (t.depth % 2 == 0 || t.depth > kMaxDepth || t.block % 32 || !t.block || t.block > 1024)
     return set_error(RNG_EINVAL, "bad server tuning");
-  const void* fn = batch_kernel_fn((int)t.step, (int)t.conv);
+  const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, t.depth);
   if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
   DeviceInfo di;
   rng_status stt = device_info(&di);
@@ -331,7 +330,6 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
   s->fn = fn;
   s->smem = smem;
   s->grid_full = (uint64_t)std::max(per_sm, 1) * (uint64_t)di.sms;
-  s->jump = host_pow2((53ull * (t.step == ST_MONT ? 33ull : 31ull) * t.depth) % kP);
   s->device = di.device;
   auto cleanup = [s]() {
     for (Slot& sl : s->slots) {

@@ -96,7 +96,7 @@ rng_status rng_autotune_bulk(uint64_t n, rng_dtype dt, void* out, void* cuda_str
       best->grid = L.grid;
       best->unit = 0;
       best->chains = L.chains;
-      best->reserved = 0;
+      best->buffers = L.buffers;
     }
   }
   cudaEventDestroy(e0);

@@ -44,18 +44,18 @@ class RNGError(RuntimeError):
 class Tune(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint32) for f in
                 ("step", "conv", "layout", "skip", "depth", "block", "grid", "unit",
-                 "chains", "reserved")]
+                 "chains", "buffers")]
 
 
 def make_tune(step="auto", conv="auto", layout="auto", skip="auto", depth=0, block=0,
-              grid=0, unit=0, chains=0) -> Tune:
+              grid=0, unit=0, chains=0, buffers=0) -> Tune:
     """Launch tuning; zero / "auto" lets the library choose.  Results never
     depend on it, only speed does."""
     return Tune(STEP[step] if isinstance(step, str) else step,
                 CONV[conv] if isinstance(conv, str) else conv,
                 LAYOUT[layout] if isinstance(layout, str) else layout,
                 SKIP[skip] if isinstance(skip, str) else skip,
-                depth, block, grid, unit, chains, 0)
+                depth, block, grid, unit, chains, buffers)
 
 
 class ServerConfig(ctypes.Structure):
@@ -107,6 +107,7 @@ def _load() -> ctypes.CDLL:
         "rng_batch_destroy": ([vp], i32),
         "rng_consume_mc": ([u64, u64, u64, u64, vp, vp, vp, vp, vp, tp], i32),
         "rng_batch_generate_noalloc": ([u32, vp, vp, vp, vp, vp, tp, vp], i32),
+        "rng_device_api_check": ([u64, u64, u64, vp, vp, u32, vp], i32),
         "rng_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], i32),
         "rng_server_submit": ([vp, u64, u64, u64, i32, ctypes.POINTER(u64)], i32),
         "rng_server_cancel": ([vp, u64], i32),
@@ -255,7 +256,8 @@ def resolve_tune(n: int, dtype: str = "f64", tune=None) -> dict:
     inv = lambda d, v: next((k for k, x in d.items() if x == v), v)
     return {"step": inv(STEP, res.step), "conv": inv(CONV, res.conv),
             "layout": inv(LAYOUT, res.layout), "skip": inv(SKIP, res.skip),
-            "depth": res.depth, "block": res.block, "grid": res.grid, "chains": res.chains}
+            "depth": res.depth, "block": res.block, "grid": res.grid, "chains": res.chains,
+            "buffers": res.buffers}
 
 
 def autotune_bulk(n: int, dtype: str, candidates, reps: int = 5, out=None, stream=None):
@@ -281,7 +283,8 @@ def tune_dict(t: Tune) -> dict:
     inv = lambda d, v: next((k for k, x in d.items() if x == v), v)
     return {"step": inv(STEP, t.step), "conv": inv(CONV, t.conv),
             "layout": inv(LAYOUT, t.layout), "skip": inv(SKIP, t.skip),
-            "depth": t.depth, "block": t.block, "grid": t.grid, "chains": t.chains}
+            "depth": t.depth, "block": t.block, "grid": t.grid, "chains": t.chains,
+            "buffers": t.buffers}
 
 
 def consume_mc(start_index: int, nblocks: int, length: int, block0: int = 0,
@@ -309,6 +312,16 @@ def consume_mc_into(start_index: int, nblocks: int, length: int, total, hits, s1
                               ctypes.c_void_p(hits.data_ptr()) if hits is not None else None,
                               ctypes.c_void_p(s1.data_ptr()), ctypes.c_void_p(s2.data_ptr()),
                               ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
+
+
+def device_api_check(start_index: int, offset: int, n: int, threads: int = 4096, stream=None):
+    """Variates from a kernel written against bcn_device.cuh: (f64, f32) tensors."""
+    f64 = torch.empty(n, dtype=torch.float64, device="cuda")
+    f32 = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib.rng_device_api_check(start_index, offset, n, ctypes.c_void_p(f64.data_ptr()),
+                                    ctypes.c_void_p(f32.data_ptr()), threads,
+                                    ctypes.c_void_p(_stream_handle(stream))))
+    return f64, f32
 
 
 class Batch:

@@ -82,7 +82,10 @@ def test_tuning_and_graph_never_change_the_bytes(R):
                  dict(depth=31, block=256, unit=64, step="barrett"),
                  dict(depth=15, block=512, unit=2, step="montgomery"),
                  dict(depth=9, block=64, unit=5, grid=3, skip="sqmul"),
-                 dict(depth=15, block=256, unit=16, conv="fp64")]:
+                 dict(depth=15, block=256, unit=16, conv="fp64"),
+                 dict(depth=15, block=128, unit=8, chains=1),
+                 dict(depth=31, block=128, unit=4, chains=2),
+                 dict(depth=21, block=64, unit=3, chains=2, step="barrett")]:
         pool, offs, outs = _pool_outputs(counts, dtypes, np.random.default_rng(6))
         b = R.Batch(starts, counts, dtypes, outs=outs, offsets=offsets, tune=tune)
         b.launch()

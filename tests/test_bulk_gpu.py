@@ -82,9 +82,12 @@ def test_tile_shape_and_grid_never_change_the_output(R):
                                      (63, 128, 152, "montgomery"), (127, 64, 0, "barrett"),
                                      (255, 32, 5, "montgomery"), (9, 96, 1000, "barrett"),
                                      (5, 128, 0, "shared"), (63, 64, 77, "shared")]:
-        t = R.make_tune(step=step, layout="tiled", depth=depth, block=block, grid=grid)
-        out = R.generate_at(a, off, n, "f64", tune=t)
-        assert torch.equal(out.view(torch.int64), ref.view(torch.int64)), (depth, block, grid)
+        for buffers in (1, 2):
+            t = R.make_tune(step=step, layout="tiled", depth=depth, block=block, grid=grid,
+                            buffers=buffers)
+            out = R.generate_at(a, off, n, "f64", tune=t)
+            assert torch.equal(out.view(torch.int64), ref.view(torch.int64)), (depth, block,
+                                                                               grid, buffers)
     for block, grid in [(1, 1), (7, 3), (1024, 1), (33, 17)]:
         t = R.make_tune(layout="direct", block=block, grid=grid)
         out = R.generate_at(a, off, n, "f64", tune=t)
@@ -123,6 +126,16 @@ def test_windows_around_tiny_variates(R, oracle_mod):
             t = R.make_tune(step="shared", layout="tiled", depth=depth)
             assert_same(R.generate_at(a, off, 6001, "f64", tune=t), want64, f"f64 {i} {depth}")
             assert_same(R.generate_at(a, off, 6001, "f32", tune=t), want32, f"f32 {i} {depth}")
+
+
+def test_device_side_api_matches_the_oracle(R, oracle_mod):
+    """A kernel written only against include/bcn_device.cuh (per-thread
+    generators positioned by skip-ahead) gives the oracle's variates."""
+    for a, off, n, threads in [(M + 100, 0, 100003, 1000), (2 ** 53, 2 ** 50 + 7, 4097, 1),
+                               (M + 12345, 123, 250000, 65536)]:
+        f64, f32 = R.device_api_check(a, off, n, threads=threads)
+        assert_same(f64, oracle_mod.generate(a, off, n, "f64"), f"f64 {a} {threads}")
+        assert_same(f32, oracle_mod.generate(a, off, n, "f32"), f"f32 {a} {threads}")
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
