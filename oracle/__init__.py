@@ -26,6 +26,13 @@ M = 3 ** 33
 SEED_MIN = M + 100
 SEED_MAX = 2 ** 53
 
+# The larger-modulus variant (Sec. 1): 3^40, seeds [3^40+100, 2^64-1],
+# period 2*3^39.
+M40 = 3 ** 40
+SEED_MIN40 = M40 + 100
+SEED_MAX40 = 2 ** 64 - 1
+P40 = 2 * 3 ** 39
+
 _lock = threading.Lock()
 _lib = None
 
@@ -75,6 +82,18 @@ def _load():
     lib.oracle_exact_sum.argtypes = [vp, u64, vp]
     lib.oracle_generate_mt.restype = i32
     lib.oracle_generate_mt.argtypes = [u64, u64, u64, i32, vp, i32]
+    lib.oracle40_seed_state.restype = u64
+    lib.oracle40_seed_state.argtypes = [u64, u64]
+    lib.oracle40_step.restype = u64
+    lib.oracle40_step.argtypes = [u64]
+    lib.oracle40_to_f64.restype = ctypes.c_double
+    lib.oracle40_to_f64.argtypes = [u64]
+    lib.oracle40_to_f32.restype = ctypes.c_float
+    lib.oracle40_to_f32.argtypes = [u64]
+    lib.oracle40_generate.restype = i32
+    lib.oracle40_generate.argtypes = [u64, u64, u64, i32, vp]
+    lib.oracle40_at.restype = i32
+    lib.oracle40_at.argtypes = [u64, vp, u64, i32, vp]
     _lib = lib
     return lib
 
@@ -156,3 +175,40 @@ def exact_sum(values) -> float:
     _check(_load().oracle_exact_sum(_ptr(values), values.size, _ptr(out)),
            "oracle_exact_sum")
     return float(out[0])
+
+
+# ---------------------------------------------------------------- modulus 3^40
+def seed_state40(a: int, j: int = 0) -> int:
+    """Eq. 2 with modulus 3^40 for the seed index a + 53*j; 0 if a < 3^40+100."""
+    return int(_load().oracle40_seed_state(a, j))
+
+
+def step40(z: int) -> int:
+    """Eq. 3 with modulus 3^40 once: 2^53 z mod 3^40."""
+    return int(_load().oracle40_step(z))
+
+
+def to_f64_40(z: int) -> float:
+    """z / 3^40 rounded toward zero, by binary long division."""
+    return float(_load().oracle40_to_f64(z))
+
+
+def to_f32_40(z: int) -> np.float32:
+    return np.float32(_load().oracle40_to_f32(z))
+
+
+def generate40(a: int, j: int, n: int, dtype: str = "f64") -> np.ndarray:
+    """Variates j .. j+n-1 of seed a under the 3^40 modulus, in order."""
+    npdt, code = _DTYPES[dtype]
+    out = np.empty(n, dtype=npdt)
+    _check(_load().oracle40_generate(a, j, n, code, _ptr(out)), "oracle40_generate")
+    return out
+
+
+def at40(a: int, idx, dtype: str = "f64") -> np.ndarray:
+    """Variates at arbitrary positions under the 3^40 modulus, each from Eq. 2."""
+    idx = np.ascontiguousarray(idx, dtype=np.uint64)
+    npdt, code = _DTYPES[dtype]
+    out = np.empty(idx.size, dtype=npdt)
+    _check(_load().oracle40_at(a, _ptr(idx), idx.size, code, _ptr(out)), "oracle40_at")
+    return out

@@ -280,3 +280,118 @@ int oracle_generate_mt(uint64_t a, uint64_t j, uint64_t n, int dtype, void *out,
   free(tids);
   return rc;
 }
+
+/* ==================================================================
+ * The larger-modulus variant.  Sec. 1 notes that a modulus as large as 3^40
+ * lengthens the period, at the price of 128-bit integer arithmetic; the
+ * paper gives no further detail.  Readings taken here:
+ *   - Eq. 2 and Eq. 3 with 3^40 in place of 3^33:
+ *       z_0 = 2^(a - 3^40) * floor(3^40 / 2)  mod 3^40,
+ *       z_k = 2^53 * z_(k-1)  mod 3^40,
+ *     with the same "step, then emit" order, so variate i of seed a has the
+ *     state 2^(a - 3^40 + 53*(i+1)) * floor(3^40/2) mod 3^40.
+ *   - Seeds a in [3^40 + 100, 2^64 - 1]: the binary digits of alpha_{2,3}
+ *     at positions n in [3^40+100, 3^41-100] come from the mod-3^40 LCG, and
+ *     the seed is a 64-bit integer (2^64 - 1 < 3^41 - 100).
+ *   - The period is 2*3^39 (2 is a primitive root modulo every power of 3).
+ *   - The FP64 variate is the exact quotient z / 3^40 rounded toward zero:
+ *     its 53 significant binary digits, from the first nonzero one, are
+ *     consecutive binary digits of alpha_{2,3} (Sec. 1: the variates carry
+ *     53-bit segments of alpha's expansion).  States reach 2^64, so (double)z
+ *     is no longer exact and the multiply-by-reciprocal form of Fig. 4 would
+ *     round twice; rounding to nearest instead would return 1.0 for the
+ *     states above 3^40 (1 - 2^-54) and leave the open interval (0,1) of
+ *     Algorithm BB.  It is formed here by binary long division.
+ *   - The FP32 variate is the FP64 variate rounded toward zero, as for 3^33
+ *     (equal to z / 3^40 rounded toward zero to float).
+ * ================================================================== */
+#define ORACLE40_M 12157665459056928801ULL   /* 3^40 */
+#define ORACLE40_H 6078832729528464400ULL    /* floor(3^40 / 2) */
+#define ORACLE40_SEED_MIN (ORACLE40_M + 100ULL)
+
+/* x*y mod 3^40 for x, y < 2^64: exact 128-bit product, then %. */
+static uint64_t mulmod40(uint64_t x, uint64_t y) {
+  return (uint64_t)(((u128)x * (u128)y) % (u128)ORACLE40_M);
+}
+
+static uint64_t pow2mod40(u128 e) {
+  uint64_t result = 1, base = 2;
+  while (e != 0) {
+    if (e & 1) result = mulmod40(result, base);
+    base = mulmod40(base, base);
+    e >>= 1;
+  }
+  return result;
+}
+
+/* Eq. 2 (modulus 3^40) for the seed index a + 53*j; 0 for a seed below
+ * 3^40 + 100. */
+uint64_t oracle40_seed_state(uint64_t a, uint64_t j) {
+  if (a < ORACLE40_SEED_MIN) return 0;
+  u128 e = (u128)(a - ORACLE40_M) + (u128)53 * (u128)j;
+  return mulmod40(pow2mod40(e), ORACLE40_H);
+}
+
+/* Eq. 3 (modulus 3^40) once: 2^53 z mod 3^40 (z < 2^64, so z*2^53 < 2^117). */
+uint64_t oracle40_step(uint64_t z) {
+  return (uint64_t)(((u128)z << 53) % (u128)ORACLE40_M);
+}
+
+/* z / 3^40 rounded toward zero, for a state z in [1, 3^40 - 1], by binary
+ * long division: each step doubles the remainder and takes out 3^40 when it
+ * fits, which yields the next binary digit of z / 3^40.  The 53 digits from
+ * the leading one are the significand.  Returns -1.0 for a value that is not
+ * a state. */
+double oracle40_to_f64(uint64_t z) {
+  if (z == 0 || z >= ORACLE40_M) return -1.0;
+  u128 r = z;
+  int k = 0, lead = 0, nbits = 0;
+  uint64_t mant = 0;
+  while (nbits < 53) {
+    r <<= 1;
+    ++k;
+    int bit = r >= (u128)ORACLE40_M;
+    if (bit) r -= ORACLE40_M;
+    if (nbits == 0 && !bit) continue;  /* leading zero digits */
+    if (nbits == 0) lead = k;          /* the leading one has value 2^-lead */
+    mant = (mant << 1) | (uint64_t)bit;
+    ++nbits;
+  }
+  /* mant's digits have values 2^-lead .. 2^-(lead+52); the rest is dropped */
+  return ldexp((double)mant, -(lead + 52));
+}
+
+float oracle40_to_f32(uint64_t z) {
+  double v = oracle40_to_f64(z);
+  float f = (float)v;
+  if ((double)f > v) f = nextafterf(f, 0.0f);
+  return f;
+}
+
+/* Variates j .. j+n-1 of seed a under the 3^40 modulus, in order.
+ * dtype 0 = f64, 1 = f32, 2 = state. */
+int oracle40_generate(uint64_t a, uint64_t j, uint64_t n, int dtype, void *out) {
+  uint64_t z = oracle40_seed_state(a, j);
+  if (z == 0 || dtype < 0 || dtype > 2) return -1;
+  for (uint64_t k = 0; k < n; ++k) {
+    z = oracle40_step(z);
+    if (dtype == 0) ((double *)out)[k] = oracle40_to_f64(z);
+    else if (dtype == 1) ((float *)out)[k] = oracle40_to_f32(z);
+    else ((uint64_t *)out)[k] = z;
+  }
+  return 0;
+}
+
+/* Variates at arbitrary positions, each straight from Eq. 2 (modulus 3^40). */
+int oracle40_at(uint64_t a, const uint64_t *idx, uint64_t n, int dtype, void *out) {
+  if (dtype < 0 || dtype > 2) return -1;
+  for (uint64_t k = 0; k < n; ++k) {
+    uint64_t z0 = oracle40_seed_state(a, idx[k]);
+    if (z0 == 0) return -1;
+    uint64_t z = oracle40_step(z0);
+    if (dtype == 0) ((double *)out)[k] = oracle40_to_f64(z);
+    else if (dtype == 1) ((float *)out)[k] = oracle40_to_f32(z);
+    else ((uint64_t *)out)[k] = z;
+  }
+  return 0;
+}
