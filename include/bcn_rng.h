@@ -140,6 +140,19 @@ rng_status rng_generate(bcn_stream *s, uint64_t n, rng_dtype dt, void *out);
 rng_status rng_generate_tuned(bcn_stream *s, uint64_t n, rng_dtype dt, void *out,
                               const rng_tune *tune);
 
+/* The stream's next n variates written to HOST memory `host_out` (n
+ * elements of dt; page-locked memory gives the full transfer rate, pageable
+ * memory works but each copy is staged).  Chunks of `chunk_bytes` (0 = 64 MiB)
+ * are generated into `nbuf` (0 = 4, at most 8) rotating device staging
+ * buffers, each on its own CUDA stream, and copied from there, so generation
+ * and the device-to-host copies overlap.  The staging buffers are allocated on
+ * the first call (and again if chunk_bytes or nbuf change) and kept until
+ * rng_destroy.  Ordered after the work already queued on the stream's CUDA
+ * stream; synchronous: returns when the data is in host memory.  Advances
+ * count by n. */
+rng_status rng_generate_to_host(bcn_stream *s, uint64_t n, rng_dtype dt, void *host_out,
+                                uint64_t chunk_bytes, uint32_t nbuf);
+
 /* Advance the count by k without generating (skip-ahead, Sec. 1; O(1)). */
 rng_status rng_skip(bcn_stream *s, uint64_t k);
 

@@ -15,6 +15,12 @@ struct bcn_stream {
   uint64_t seed;
   uint64_t count;
   cudaStream_t cs;
+  // staging for rng_generate_to_host, created on first use
+  int staging_device = -1;
+  uint32_t nstage = 0;
+  size_t stage_bytes = 0;
+  void* stage[8] = {};
+  cudaStream_t stage_cs[8] = {};
 };
 
 namespace bcn {
@@ -112,12 +118,101 @@ rng_status rng_create(uint64_t start_index, bcn_stream** out) {
   s->seed = start_index;
   s->count = 0;
   s->cs = nullptr;
+  s->nstage = 0;
   *out = s;
   return RNG_OK;
 }
 
+static void release_staging(bcn_stream* s) {
+  for (uint32_t i = 0; i < s->nstage; ++i) {
+    if (s->stage_cs[i]) {
+      cudaStreamSynchronize(s->stage_cs[i]);
+      cudaStreamDestroy(s->stage_cs[i]);
+    }
+    if (s->stage[i]) cudaFree(s->stage[i]);
+    s->stage[i] = nullptr;
+    s->stage_cs[i] = nullptr;
+  }
+  s->nstage = 0;
+  s->stage_bytes = 0;
+  s->staging_device = -1;
+}
+
 rng_status rng_destroy(bcn_stream* s) {
+  if (s) release_staging(s);
   delete s;
+  return RNG_OK;
+}
+
+// rng_generate_to_host: the next n variates into host memory.  Chunks of the
+// call are generated into `nbuf` rotating device staging buffers, each with
+// its own CUDA stream, and copied to the host from there; the generation of one
+// chunk overlaps the copies of the others.  Synchronous: returns when the data
+// is in host memory.
+rng_status rng_generate_to_host(bcn_stream* s, uint64_t n, rng_dtype dt, void* host_out,
+                                uint64_t chunk_bytes, uint32_t nbuf) {
+  if (!s) return set_error(RNG_EINVAL, "stream is NULL");
+  bool empty = false;
+  rng_status st = check_bulk(s->seed, n, (int)dt, host_out, &empty);
+  if (st != RNG_OK || empty) return st;
+  if (n > UINT64_MAX - s->count) return set_error(RNG_ERANGE, "count would pass 2^64-1");
+  if (chunk_bytes > (1ull << 40)) return set_error(RNG_EINVAL, "chunk_bytes above 2^40");
+  if (!chunk_bytes) chunk_bytes = 64ull << 20;
+  if (!nbuf) nbuf = 4;
+  if (nbuf > 8) return set_error(RNG_EINVAL, "at most 8 staging buffers");
+  const size_t esz = dtype_size((int)dt);
+  chunk_bytes = (chunk_bytes + 255) / 256 * 256;
+  if (chunk_bytes < esz * 32) chunk_bytes = 256;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (s->nstage != nbuf || s->stage_bytes != chunk_bytes || s->staging_device != dev) {
+    release_staging(s);
+    for (uint32_t i = 0; i < nbuf; ++i) {
+      e = cudaMalloc(&s->stage[i], chunk_bytes);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stage_cs[i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        s->nstage = i + 1;
+        release_staging(s);
+        return cuda_error(e, "allocating host-transfer staging");
+      }
+    }
+    s->nstage = nbuf;
+    s->stage_bytes = chunk_bytes;
+    s->staging_device = dev;
+  }
+  // work ordered after what the caller already queued on the stream's CUDA stream
+  cudaEvent_t start = nullptr;
+  e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(start, s->cs);
+  for (uint32_t i = 0; i < nbuf && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(s->stage_cs[i], start, 0);
+  if (start) cudaEventDestroy(start);
+  if (e != cudaSuccess) return cuda_error(e, "ordering host transfer");
+  const uint64_t per = chunk_bytes / esz;
+  BulkLaunch L;
+  bool resolved = false;
+  uint64_t done = 0;
+  for (uint64_t k = 0; done < n; ++k) {
+    const uint64_t cnt = (n - done < per) ? n - done : per;
+    const uint32_t b = (uint32_t)(k % nbuf);
+    if (!resolved || cnt != per) {
+      st = resolve_bulk(cnt, (int)dt, nullptr, &L, false);
+      if (st != RNG_OK) return st;
+      resolved = cnt == per;
+    }
+    st = launch_bulk(L, s->seed, s->count + done, cnt, s->stage[b], 0, s->stage_cs[b]);
+    if (st != RNG_OK) return st;
+    e = cudaMemcpyAsync(static_cast<unsigned char*>(host_out) + done * esz, s->stage[b],
+                        cnt * esz, cudaMemcpyDeviceToHost, s->stage_cs[b]);
+    if (e != cudaSuccess) return cuda_error(e, "device-to-host copy");
+    done += cnt;
+  }
+  for (uint32_t i = 0; i < nbuf; ++i) {
+    e = cudaStreamSynchronize(s->stage_cs[i]);
+    if (e != cudaSuccess) return cuda_error(e, "host transfer");
+  }
+  s->count += n;
   return RNG_OK;
 }
 

@@ -88,6 +88,7 @@ def _load() -> ctypes.CDLL:
         "rng_generate": ([vp, u64, i32, vp], i32),
         "rng_generate_tuned": ([vp, u64, i32, vp, tp], i32),
         "rng_skip": ([vp, u64], i32),
+        "rng_generate_to_host": ([vp, u64, i32, vp, u64, u32], i32),
         "rng_get_state": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i32),
         "rng_set_state": ([vp, u64, u64], i32),
         "rng_sync": ([vp], i32),
@@ -207,6 +208,20 @@ class Stream:
         code, _ = _dtype(dtype)
         self._bind(stream)
         _check(lib.rng_generate_tuned(self._h, n, code, ctypes.c_void_p(ptr), _tune_ptr(tune)))
+
+    def generate_to_host(self, n: int, dtype: str = "f64", out=None, chunk_bytes: int = 0,
+                         nbuf: int = 0, stream=None):
+        """The next n variates into a host tensor (page-locked if `out` is None),
+        generation and device-to-host copies pipelined; synchronous."""
+        code, tdt = _dtype(dtype)
+        if out is None:
+            out = torch.empty(n, dtype=tdt, pin_memory=True)
+        elif out.dtype != tdt or out.is_cuda or not out.is_contiguous() or out.numel() < n:
+            raise ValueError(f"out must be a contiguous host {tdt} tensor with >= {n} elements")
+        self._bind(stream)
+        _check(lib.rng_generate_to_host(self._h, n, code, ctypes.c_void_p(out.data_ptr()),
+                                        chunk_bytes, nbuf))
+        return out
 
     def skip(self, k: int) -> None:
         _check(lib.rng_skip(self._h, k))

@@ -178,6 +178,29 @@ def test_stream_calls_concatenate(R, oracle_mod):
     assert torch.equal(s2.generate(1000, "f64").view(torch.int64), cont.view(torch.int64))
 
 
+def test_generate_to_host_pipelines_chunks(R, oracle_mod):
+    """Host output through rotating device staging buffers: any chunk size and
+    buffer count give the oracle's variates and advance the count."""
+    import torch
+    a = M + 2024
+    for dtype in ("f64", "f32"):
+        for n, chunk, nbuf in [(1, 0, 0), (100003, 4096, 3), (1 << 21, 1 << 20, 8),
+                               (777777, 256, 1)]:
+            s = R.Stream(a)
+            s.skip(12345)
+            out = s.generate_to_host(n, dtype, chunk_bytes=chunk, nbuf=nbuf)
+            assert not out.is_cuda
+            want = oracle_mod.generate(a, 12345, n, dtype)
+            assert np.array_equal(host_bits(out.numpy()), host_bits(want)), (dtype, n, chunk)
+            assert s.state == (a, 12345 + n)
+            nxt = s.generate(1000, dtype)
+            assert_same(nxt, oracle_mod.generate(a, 12345 + n, 1000, dtype), "after host call")
+    pageable = torch.empty(5000, dtype=torch.float64)
+    s = R.Stream(a)
+    s.generate_to_host(5000, "f64", out=pageable)
+    assert np.array_equal(host_bits(pageable.numpy()), host_bits(oracle_mod.generate(a, 0, 5000, "f64")))
+
+
 def test_offsets_across_the_period_and_far_out(R, oracle_mod):
     a = 2 ** 53
     for off in (P - 50, P, 2 * P - 7, 2 ** 60 + 11, 2 ** 64 - 5000):
