@@ -241,9 +241,36 @@ rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64_t *starts,
                                       const uint8_t *dtypes, void *const *outs,
                                       const rng_tune *tune, void *cuda_stream);
 
+/* ------------------------------------------------ modulus 3^40 variant */
+
+/* The larger-modulus generator that Sec. 1 sketches: Eq. 2 and Eq. 3 with
+ * 3^40 in place of 3^33, i.e.
+ *   z_0 = 2^(a - 3^40) floor(3^40/2) mod 3^40,  z_k = 2^53 z_(k-1) mod 3^40,
+ * period 2*3^39 (about 8.1e18), states up to 3^40 - 1 > 2^63 (128-bit
+ * products inside).  Variate i of seed a has the state
+ * 2^(a - 3^40 + 53(i+1)) floor(3^40/2) mod 3^40 (step, then emit).
+ *   - start_index: in [3^40 + 100, 2^64 - 1], else RNG_ERANGE.
+ *   - RNG_F64: z / 3^40 rounded toward zero (its 53 significant bits are
+ *     consecutive binary digits of alpha_{2,3}; every value is in (0,1),
+ *     down to 3^-40).  RNG_F32: that value rounded toward zero to float.
+ *     RNG_U64: the state z.
+ *   - Writes variates offset .. offset+n-1 to the caller-owned device array
+ *     `out` (aligned to the element size), asynchronously on `cuda_stream`
+ *     (NULL = the legacy default stream).  n = 0 is a no-op; n > RNG_MAX_N is
+ *     RNG_ERANGE.
+ *   - tune: NULL or zero fields choose; layout, depth, block, grid, chains
+ *     and buffers mean what they mean for rng_generate_at; step, conv, skip
+ *     and unit must be 0 (the variant has one of each), else RNG_EINVAL. */
+rng_status rng40_generate_at(uint64_t start_index, uint64_t offset, uint64_t n, rng_dtype dt,
+                             void *out, void *cuda_stream, const rng_tune *tune);
+
+/* The launch rng40_generate_at would make for n elements of dt: layout,
+ * depth, block, grid, chains and buffers (other fields 0). */
+rng_status rng40_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune *tune, rng_tune *out);
+
 /* ----------------------------------------------------------------- serving */
 
-/* A continuous-batching request server (spec serving form; the paper
+/* A continuous-batching request server (a serving form; the paper
  * has none).  Requests are generation calls (offset .. offset+n-1 of the
  * sequence seeded with a start index, as rng_generate_at) whose outputs are
  * placed in one device pool the server owns.  A scheduler thread admits

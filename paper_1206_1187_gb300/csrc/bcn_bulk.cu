@@ -170,7 +170,7 @@ static const void* pick_kernel(int layout, int dt, int st, int cv, int ilp, uint
 }
 
 // Large dynamic shared memory must be enabled once per kernel and device.
-static rng_status enable_smem(const void* fn, int device, size_t bytes) {
+rng_status enable_smem(const void* fn, int device, size_t bytes) {
   static std::mutex mu;
   static std::set<std::pair<const void*, int>> done;
   std::lock_guard<std::mutex> lock(mu);

@@ -49,6 +49,10 @@ struct DeviceInfo {
 };
 rng_status device_info(DeviceInfo* out);
 
+// Allow a kernel the device's full opt-in dynamic shared memory (once per
+// kernel and device).
+rng_status enable_smem(const void* fn, int device, size_t bytes);
+
 // The tuning installed by rng_set_auto_tune for dtype dt (zeros if none).
 rng_tune auto_defaults(int dt);
 

@@ -93,6 +93,8 @@ def _load() -> ctypes.CDLL:
         "rng_set_state": ([vp, u64, u64], i32),
         "rng_sync": ([vp], i32),
         "rng_generate_at": ([u64, u64, u64, i32, vp, vp, tp], i32),
+        "rng40_generate_at": ([u64, u64, u64, i32, vp, vp, tp], i32),
+        "rng40_resolve_tune": ([u64, i32, tp, tp], i32),
         "rng_fill_constant": ([u64, i32, dbl, vp, vp, tp], i32),
         "rng_last_error": ([], ctypes.c_char_p),
         "rng_resolve_tune": ([u64, i32, tp, tp], i32),
@@ -253,6 +255,25 @@ def generate_at_ptr(start_index: int, offset: int, n: int, dtype: str, ptr: int,
     code, _ = _dtype(dtype)
     _check(lib.rng_generate_at(start_index, offset, n, code, ctypes.c_void_p(ptr),
                                ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
+
+
+def generate40_at(start_index: int, offset: int, n: int, dtype: str = "f64", out=None,
+                  tune=None, stream=None):
+    """Variates offset .. offset+n-1 of the 3^40-modulus generator seeded with
+    start_index (in [3^40+100, 2^64-1])."""
+    code, out = _out_tensor(n, dtype, out)
+    _check(lib.rng40_generate_at(start_index, offset, n, code, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
+    return out
+
+
+def resolve_tune40(n: int, dtype: str = "f64", tune=None) -> dict:
+    code, _ = _dtype(dtype)
+    res = Tune()
+    _check(lib.rng40_resolve_tune(n, code, _tune_ptr(tune), ctypes.byref(res)))
+    inv = lambda d, v: next((k for k, x in d.items() if x == v), v)
+    return {"layout": inv(LAYOUT, res.layout), "depth": res.depth, "block": res.block,
+            "grid": res.grid, "chains": res.chains, "buffers": res.buffers}
 
 
 def fill_constant(n: int, dtype: str = "f64", value: float = 0.5, out=None, tune=None,

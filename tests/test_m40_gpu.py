@@ -1,0 +1,126 @@
+"""GPU parity of the 3^40-modulus generator against its oracle.
+
+Every output must equal the oracle's bit for bit: states, truncated FP64
+variates and FP32 variates, for any tile depth, block, chain count, buffer
+count, layout and output alignment, at offsets across the period, and at the
+rare smallest states whose variates need a third quotient digit.
+"""
+import numpy as np
+import pytest
+
+from m40_math import M40, P40, index_of_state
+
+pytestmark = pytest.mark.gpu
+
+ESZ = {"f64": 8, "f32": 4, "u64": 8}
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1206_1187_gb300 import rng
+    return rng
+
+
+def _bits(a):
+    return a.view(np.int64 if a.itemsize == 8 else np.int32)
+
+
+def _dev_bits(t):
+    import torch
+    return t.view(torch.int64 if t.element_size() == 8 else torch.int32).cpu().numpy()
+
+
+def _check(R, oracle_mod, a, off, n, dtype, tune=None, shift=0):
+    """Generate into a canary-filled buffer at element offset `shift`."""
+    import torch
+    tdt = {"f64": torch.float64, "f32": torch.float32, "u64": torch.uint64}[dtype]
+    esz = ESZ[dtype]
+    raw = torch.full(((n + shift + 8) * esz,), 0x5A, dtype=torch.uint8, device="cuda")
+    out = raw[shift * esz: (shift + n) * esz].view(tdt)
+    R.generate40_at(a, off, n, dtype, out=out, tune=tune)
+    torch.cuda.synchronize()
+    want = oracle_mod.generate40(a, off, n, dtype)
+    got = _dev_bits(out)
+    bad = np.nonzero(got != _bits(want))[0]
+    assert bad.size == 0, (a, off, n, dtype, tune, shift, bad[:8])
+    host = raw.cpu().numpy()
+    assert np.all(host[: shift * esz] == 0x5A) and np.all(host[(shift + n) * esz:] == 0x5A)
+
+
+TUNES = [None,
+         dict(depth=15, block=64, chains=1),
+         dict(depth=31, block=128, chains=2),
+         dict(depth=7, block=32),
+         dict(depth=63, block=128, chains=2, buffers=2),
+         dict(depth=1, block=96),
+         dict(layout="direct", block=64),
+         dict(depth=31, block=512, chains=2, buffers=1, grid=7)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "u64"])
+def test_matches_the_oracle_for_every_tuning(R, oracle_mod, dtype):
+    for k, tune in enumerate(TUNES):
+        for a, off, n in [(M40 + 100, 0, 1), (2 ** 64 - 1, 12345, 31 * 32 * 5 + 17),
+                          (M40 + 987654321, 2 ** 40 + 7, 100003)]:
+            _check(R, oracle_mod, a, off, n, dtype, tune, shift=k % 3)
+
+
+def test_heads_tails_and_small_sizes(R, oracle_mod):
+    a = M40 + 4242
+    for n in (2, 3, 31, 32, 33, 992, 993, 31 * 32 * 3 - 1):
+        for shift in (0, 1, 2, 3):
+            _check(R, oracle_mod, a, 77, n, "f64", dict(depth=31, block=64), shift)
+            _check(R, oracle_mod, a, 77, n, "f32", dict(depth=15, block=64, chains=2), shift)
+
+
+def test_offsets_across_the_period(R, oracle_mod):
+    a = M40 + 100
+    for off in (P40 - 3000, P40 // 2 - 17, 2 ** 63 + 5, 2 ** 64 - 5000):
+        _check(R, oracle_mod, a, off, 20000, "f64", dict(depth=15, block=128))
+        _check(R, oracle_mod, a, off, 4000, "u64")
+
+
+def test_smallest_states(R, oracle_mod):
+    """States 1, 2, 4, ... below 3^40/2^53 give variates below 2^-53 (a zero
+    first quotient); each is placed inside tiles, at tile edges, in the head
+    and in the tail of a call."""
+    a = M40 + 100
+    for z in (1, 2, 4, 5, 1348, 1349, 1351, M40 - 1):
+        i = index_of_state(a, z)
+        for lead, n, tune in [(40, 81, None), (5, 3000, dict(depth=31, block=32)),
+                              (31 * 32 - 1, 31 * 32 * 4, dict(depth=31, block=32, chains=2)),
+                              (16, 1000, dict(depth=15, block=64, chains=1)),
+                              (0, 7, dict(layout="direct", block=1))]:
+            off = (i - lead) % P40
+            for dtype in ("f64", "f32", "u64"):
+                _check(R, oracle_mod, a, off, n, dtype, tune, shift=1)
+        v = R.generate40_at(a, i, 1, "f64").cpu().numpy()
+        assert v[0] == oracle_mod.to_f64_40(z) and v[0] > 0.0
+
+
+def test_bad_arguments(R):
+    with pytest.raises(R.RNGError) as e:
+        R.generate40_at(M40 + 99, 0, 10)
+    assert e.value.status == 2
+    for tune in (dict(step="barrett"), dict(depth=4), dict(block=33), dict(chains=3)):
+        with pytest.raises(R.RNGError) as e:
+            R.generate40_at(M40 + 100, 0, 10, tune=tune)
+        assert e.value.status == 1
+
+
+def test_full_size_sampled(R, oracle_mod):
+    """The 2^28-variate FP64 call in its default launch: first and last 4096
+    variates and 8192 random positions against the oracle."""
+    import torch
+    a, n = M40 + 12345, 1 << 28
+    out = R.generate40_at(a, 0, n, "f64")
+    torch.cuda.synchronize()
+    rnd = np.random.default_rng(40)
+    idx = np.unique(np.concatenate([np.arange(4096), np.arange(n - 4096, n),
+                                    rnd.integers(0, n, size=8192)])).astype(np.int64)
+    got = _dev_bits(out[torch.from_numpy(idx).cuda()])
+    want = _bits(oracle_mod.at40(a, idx.astype(np.uint64), "f64"))
+    assert np.array_equal(got, want)
+    del out

@@ -1,0 +1,178 @@
+"""The 3^40 variant's device arithmetic, restated in Python from its
+derivations and checked against the definitions (no GPU).
+
+Models: the quotient floor(2^53 z / 3^40) from the 118-bit reciprocal with
+the carry rule, the remainder in 64-bit wrap-around arithmetic, the
+Montgomery product with its 65-bit sum, the fixed-base skip-ahead table,
+and the variate bits joined from two consecutive quotients (and from the
+next two when the first is 0).  Each is compared with `//`, `%` and exact
+rational truncation on random, edge and adversarial states.
+"""
+import math
+import random
+import struct
+from fractions import Fraction
+
+from m40_math import H40, M40, P40, index_of_state
+
+U64 = 2 ** 64 - 1
+R = 2 ** 181 // M40
+RHI, RLO = R >> 64, R & U64
+NEG_MINV = (-pow(M40, -1, 2 ** 64)) % 2 ** 64
+
+
+def hi(a, b):
+    return (a * b) >> 64
+
+
+def quot_model(z):
+    """ahi + carry(alo + bhi): the high word of z*R / 2^128."""
+    alo = (z * RHI) & U64
+    ahi = hi(z, RHI)
+    bhi = hi(z, RLO)
+    return ahi + (1 if alo + bhi > U64 else 0)
+
+
+def rem_model(z, q):
+    return ((z << 53) - q * M40) & U64
+
+
+def mont_model(a, b):
+    tlo = (a * b) & U64
+    thi = hi(a, b)
+    u = (tlo * NEG_MINV) & U64
+    uhi = hi(u, M40)
+    s1 = thi + uhi
+    c1 = s1 > U64
+    s1 &= U64
+    s = s1 + (1 if tlo else 0)
+    c2 = s > U64
+    s &= U64
+    return (s - M40) & U64 if (c1 or c2 or s >= M40) else s
+
+
+def clz64(x):
+    return 64 - x.bit_length()
+
+
+def bits_model(q0, q1):
+    t = clz64(q0) - 11
+    mant = ((q0 << t) & U64) | (q1 >> (53 - t))
+    return (((1021 - t) << 52) + mant) & U64
+
+
+def bits_small_model(z1, q1):
+    q2 = quot_model(rem_model(z1, q1))
+    t = clz64(q1) - 11
+    mant = ((q1 << t) & U64) | (q2 >> (53 - t))
+    return (((1021 - 53 - t) << 52) + mant) & U64
+
+
+def f64_from_bits(b):
+    return struct.unpack("<d", struct.pack("<Q", b))[0]
+
+
+def trunc_quotient(z):
+    s = 53 + (M40.bit_length() - z.bit_length()) + 1
+    q = (z << s) // M40
+    drop = q.bit_length() - 53
+    return math.ldexp(q >> drop, drop - s)
+
+
+def states(count, seed):
+    rnd = random.Random(seed)
+    out = [1, 2, 4, 5, 7, M40 - 1, M40 - 2, H40, H40 + 1, 2 ** 63, 2 ** 63 + 1, U64 % M40]
+    out += [2 ** k for k in range(64) if 2 ** k < M40]
+    out += [rnd.randrange(1, M40) for _ in range(count)]
+    # states just above multiples of m / 2^53 (quotient boundaries)
+    for _ in range(count // 10):
+        j = rnd.randrange(1, 2 ** 53)
+        out.append(-(-j * M40 // 2 ** 53))
+    return [z for z in out if z % 3 and 0 < z < M40]
+
+
+def test_reciprocal_constants():
+    assert RHI == 2 ** 117 // M40 and RHI < 2 ** 54
+    assert (M40 * NEG_MINV + 1) % 2 ** 64 == 0
+    # the error bound of the quotient argument: z/2^128 < 2^-64 <= 1/m
+    assert Fraction(U64, 2 ** 128) < Fraction(1, M40) * 2
+
+
+def test_quotient_and_remainder_are_exact():
+    for z in states(40000, 1):
+        q = quot_model(z)
+        assert q == (z << 53) // M40, z
+        r = rem_model(z, q)
+        assert r == (z << 53) % M40 and 0 < r < M40
+
+
+def test_montgomery_product():
+    rnd = random.Random(2)
+    vals = [1, 2, M40 - 1, M40 - 2, 2 ** 63, H40] + [rnd.randrange(1, M40) for _ in range(20000)]
+    minv64 = pow(2 ** 64, -1, M40)
+    for k in range(len(vals) - 1):
+        a, b = vals[k], vals[k + 1]
+        assert mont_model(a, b) == a * b * minv64 % M40
+    # with one operand in Montgomery form the product is a plain product
+    for a, c in [(M40 - 1, M40 - 1), (12345, 2 ** 63 % M40), (H40, 3 ** 39 + 1)]:
+        assert mont_model(a, (c << 64) % M40) == a * c % M40
+
+
+def test_skip_ahead_table_model():
+    rnd = random.Random(3)
+    g, rows = 2, []
+    for k in range(8):
+        v = H40 if k == 0 else 1
+        row = []
+        for _ in range(256):
+            row.append(v if k == 0 else (v << 64) % M40)
+            v = v * g % M40
+        rows.append(row)
+        g = pow(g, 256, M40)
+    for e in [0, 1, 255, 256, P40 - 1, P40 // 2] + [rnd.randrange(P40) for _ in range(300)]:
+        z = rows[0][e & 255]
+        for k in range(1, 8):
+            z = mont_model(z, rows[k][(e >> (8 * k)) & 255])
+        assert z == pow(2, e, M40) * H40 % M40, e
+
+
+def test_variate_bits_from_two_quotients():
+    for z in states(20000, 4):
+        q0 = quot_model(z)
+        z1 = rem_model(z, q0)
+        q1 = quot_model(z1)
+        b = bits_model(q0, q1) if q0 else bits_small_model(z1, q1)
+        v = f64_from_bits(b)
+        assert v == trunc_quotient(z), z
+        assert Fraction(v) <= Fraction(z, M40) < Fraction(math.nextafter(v, 2.0))
+
+
+def test_smallest_variates_take_the_second_window():
+    """States below 3^40 / 2^53 (variates below 2^-53) have a zero first
+    quotient; their bits come from the next two quotients."""
+    small = [z for z in range(1, 1350) if z % 3] + [1349, 1348]
+    for z in small:
+        q0 = quot_model(z)
+        assert q0 == 0
+        z1 = rem_model(z, q0)
+        q1 = quot_model(z1)
+        assert q1 != 0
+        assert f64_from_bits(bits_small_model(z1, q1)) == trunc_quotient(z), z
+    assert quot_model(1349) == 0 and quot_model(1350) == 1  # 3^40/2^53 = 1349.77...
+    assert index_of_state(M40 + 100, 1) >= 0
+
+
+def test_two_chain_jump_distances():
+    """A chain that has emitted variates [s, s+len) holds the state of
+    variate s+len+1 (one quotient ahead); the jump to a run starting at s'
+    is 2^(53 (s' - s - len - 1)).  Tiles of 32c, a lane's run split into
+    h+1 and h variates (c = 2h+1)."""
+    for c in (3, 15, 31, 63):
+        h = c // 2
+        s = 1000
+        # chain a: variates [s, s+h+1), next run at s + 32c
+        assert (s + 32 * c) - (s + h + 1) - 1 == 32 * c - h - 2
+        # chain b: variates [s+h+1, s+c), next run at s+h+1 + 32c
+        assert (s + h + 1 + 32 * c) - (s + c) - 1 == 31 * c + h
+        # one chain: [s, s+c), next run at s + 32c
+        assert (s + 32 * c) - (s + c) - 1 == 31 * c - 1
