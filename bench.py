@@ -55,6 +55,7 @@ def parse_args():
     p.add_argument("--no-batch", action="store_true", help="skip the batched measurement")
     p.add_argument("--no-fused", action="store_true", help="skip the fused measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-m40", action="store_true", help="skip the 3^40-modulus measurement")
     p.add_argument("--paper-table", action="store_true",
                    help="print the paper's Table 1/2 protocol redone on this GPU and exit")
     p.add_argument("--no-autotune", action="store_true",
@@ -287,6 +288,40 @@ def measure_fused(rng, stream, steps: int):
     return out
 
 
+def measure_m40(rng, stream, peaks, steps: int):
+    """The larger-modulus variant (3^40, Sec. 1): 2^28 FP64 variates (2 GiB,
+    larger than L2) from a = 3^40+12345 into device memory, default tuning."""
+    import torch
+    n, a = 1 << 28, 3 ** 40 + 12345
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        rng.generate40_at(a, 0, n, "f64", out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rng.generate40_at(a, 0, n, "f64", out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    gbs = 8.0 * n / (ms / 1e3) / 1e9
+    out_d = {"workload": "modulus 3^40, 2^28 FP64 variates (2 GiB) from a = 3^40+12345, "
+                         "truncated variates, into device memory",
+             "launches": steps, "ms_per_launch": ms, "variates_per_s": n / (ms / 1e3),
+             "GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"],
+             "tune": rng.resolve_tune40(n, "f64")}
+    ipv = profiled_value("inst_per_variate", "m40_2e25", "m40")
+    if ipv is not None:
+        peak = 152 * 4 * 32 * 2.07e9
+        achieved = ipv * n / (ms / 1e3)
+        out_d["roofline_alu"] = {"achieved": achieved / 1e12, "peak": peak / 1e12,
+                                 "unit": "T thread-instructions/s", "frac": achieved / peak,
+                                 "inst_per_variate": ipv}
+    del out
+    return out_d
+
+
 def measure_serving(rng, n_requests: int = 20000):
     """The served form: Poisson arrivals at 20k req/s, sizes log-uniform 1 KiB..256
     MiB, random start indices and offsets, FP32/FP64 1:1, 40 GB device output pool
@@ -483,6 +518,9 @@ def run_ours(args):
     fused = None
     if not args.no_fused and rank == 0:
         fused = measure_fused(rng, stream, steps=3)
+    m40 = None
+    if not args.no_m40 and rank == 0:
+        m40 = measure_m40(rng, stream, load_peaks(), steps=max(min(args.steps // 20, 50), 5))
     serving = None
     if not args.no_serve and rank == 0:
         serving = measure_serving(rng)
@@ -552,6 +590,8 @@ def run_ours(args):
             line["batched"] = batched
         if fused is not None:
             line["fused"] = fused
+        if m40 is not None:
+            line["modulus_3_40"] = m40
         if serving is not None:
             line["serving"] = serving
         if tuned is not None:

@@ -106,6 +106,42 @@ __device__ __forceinline__ uint64_t quot40(uint64_t z) {
   return ahi + (alo + bhi < alo ? 1 : 0);
 }
 
+// The quotient's fast form.  T = z*Rhi + z1*r1, with z1 and r1 the high
+// 32-bit words of z and Rlo, falls short of z*R / 2^64 by less than 2^33 + 2
+// (the dropped partial products z0*Rlo and z1*(Rlo mod 2^32) contribute less
+// than 2^32 + 2^32 + 1 there), so floor(T / 2^64) is the quotient unless the
+// low word f of T lies within 2^34 of 2^64.  Five 32x32->64-bit products in
+// place of the twelve of the exact form.  Returns the quotient estimate and
+// the high word of f; the caller treats fhi >= 0xFFFFFFFC as "not decided"
+// and redoes the work with quot40.
+__device__ __forceinline__ uint64_t quot40_fast(uint64_t z, uint32_t& fhi) {
+  constexpr uint32_t h0 = (uint32_t)k40Rhi, h1 = (uint32_t)(k40Rhi >> 32);
+  constexpr uint32_t r1 = (uint32_t)(k40Rlo >> 32);
+  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
+  const uint64_t p00 = (uint64_t)z0 * h0;
+  const uint64_t p01 = (uint64_t)z0 * h1;
+  const uint64_t p10 = (uint64_t)z1 * h0;
+  const uint64_t p11 = (uint64_t)z1 * h1;
+  const uint64_t b = (uint64_t)z1 * r1;
+  const uint64_t lo = p00 + b;
+  const uint64_t c0 = lo < p00 ? 1 : 0;
+  const uint64_t mid = p01 + p10;                  // weight 2^32
+  const uint64_t cm = mid < p10 ? (1ull << 32) : 0;  // its carry, weight 2^96
+  const uint64_t f = lo + (mid << 32);
+  const uint64_t c1 = f < lo ? 1 : 0;
+  fhi = (uint32_t)(f >> 32);
+  return p11 + (mid >> 32) + cm + c0 + c1;
+}
+
+// The variate bits of bits40 when q0 >= 2^32 (a variate of at least 2^-21;
+// the caller routes smaller ones to the exact path): q0's leading one is in
+// its high word, and the digits taken from q1 come from q1's high word only.
+__device__ __forceinline__ uint64_t bits40_fast(uint64_t q0, uint64_t q1) {
+  const uint32_t t = (uint32_t)__clz((int)(uint32_t)(q0 >> 32)) - 11u;  // 0..20
+  const uint64_t mant = (q0 << t) | (uint64_t)((uint32_t)(q1 >> 32) >> (21u - t));
+  return ((uint64_t)(1021u - t) << 52) + mant;
+}
+
 // Eq. 3 with the quotient q of z: 2^53 z - q 3^40, which lies in [1, 3^40),
 // so arithmetic modulo 2^64 gives it exactly.
 __device__ __forceinline__ uint64_t rem40(uint64_t z, uint64_t q) {

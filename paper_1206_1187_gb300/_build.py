@@ -60,6 +60,7 @@ KERNEL_SOURCES = {
     "tiled": ["bcn_bulk.cu", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
     "batch": ["bcn_batch.cu", "bcn_batch.cuh", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
     "mc": ["bcn_mc.cu", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
+    "m40": ["bcn_m40.cu", "bcn_gen.cuh", "bcn_math.cuh", "bcn_math40.cuh", "bcn_internal.h"],
 }
 
 

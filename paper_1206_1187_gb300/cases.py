@@ -4,6 +4,7 @@
     python -m paper_1206_1187_gb300.cases bulk32 33554432 [reps]
     python -m paper_1206_1187_gb300.cases batch 256 [reps]
     python -m paper_1206_1187_gb300.cases mc 16384 [reps]
+    python -m paper_1206_1187_gb300.cases m40 33554432 [reps]
 
 Each case runs `reps` launches (default 3) of one of the library's kernels on
 synthetic inputs and exits 0; nothing is checked here (the test suite does
@@ -36,6 +37,10 @@ def main(argv):
         b = rng.Batch(starts, counts, dtypes, outs=outs)
         for _ in range(reps):
             b.launch()
+    elif case == "m40":
+        out = torch.empty(size, dtype=torch.float64, device="cuda")
+        for _ in range(reps):
+            rng.generate40_at(3 ** 40 + 12345, 0, size, "f64", out=out)
     elif case == "mc":
         for _ in range(reps):
             rng.consume_mc(3 ** 33 + 100, size, 1 << 16)

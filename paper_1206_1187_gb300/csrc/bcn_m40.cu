@@ -36,6 +36,21 @@ struct Chain40 {
       z = rem40(s, q);
     }
   }
+  // A variate by the fast quotient and conversion (F64/F32 only).  qmin
+  // tracks the smallest high word of the quotients used as a variate's
+  // leading window (0 means a variate below 2^-21); fmax the largest high
+  // word of the estimates' fractions (>= 0xFFFFFFFC means undecided).
+  __device__ __forceinline__ typename Word<DT>::type next_fast(uint32_t& qmin, uint32_t& fmax) {
+    uint32_t fhi;
+    const uint64_t q1 = quot40_fast(z, fhi);
+    fmax = max(fmax, fhi);
+    const uint64_t bits = bits40_fast(q, q1);
+    z = rem40(z, q1);
+    q = q1;
+    qmin = min(qmin, (uint32_t)(q1 >> 32));
+    if constexpr (DT == DT_F64) return bits;
+    else return f32_bits_from_f64_bits(bits);
+  }
   __device__ __forceinline__ typename Word<DT>::type next() {
     if constexpr (DT == DT_U64) {
       const uint64_t w = z;
@@ -108,16 +123,53 @@ __global__ void __launch_bounds__(1024) tiled40_kernel(const M40Params p) {
       W* const buf = buf0 + (issued % p.nbuf) * tile_elems;
       wait_buffer_free(issued, p.nbuf, lane);
       W* const mine = buf + lane * c;
-      if constexpr (ILP == 2) {
+      if constexpr (DT == DT_U64) {
+        if constexpr (ILP == 2) {
 #pragma unroll
-        for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : h); ++i) {
-          mine[i] = a.next();
-          mine[h + 1 + i] = b.next();
+          for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : h); ++i) {
+            mine[i] = a.next();
+            mine[h + 1 + i] = b.next();
+          }
+          mine[h] = a.next();
+        } else {
+#pragma unroll
+          for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH : c); ++i) mine[i] = a.next();
         }
-        mine[h] = a.next();
       } else {
+        // fast path for the whole run; a lane whose run met an undecided
+        // quotient or a variate below 2^-21 redoes it exactly
+        const Chain40<DT> a0 = a, b0 = b;
+        uint32_t qmin = (uint32_t)(a.q >> 32), fmax = 0;
+        if constexpr (ILP == 2) {
+          qmin = min(qmin, (uint32_t)(b.q >> 32));
 #pragma unroll
-        for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH : c); ++i) mine[i] = a.next();
+          for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : h); ++i) {
+            mine[i] = a.next_fast(qmin, fmax);
+            mine[h + 1 + i] = b.next_fast(qmin, fmax);
+          }
+          mine[h] = a.next_fast(qmin, fmax);
+        } else {
+#pragma unroll
+          for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH : c); ++i)
+            mine[i] = a.next_fast(qmin, fmax);
+        }
+        const bool rare = qmin == 0 || fmax >= 0xFFFFFFFCu;
+        if (__any_sync(0xffffffffu, rare)) {
+          if (rare) {
+            a = a0;
+            b = b0;
+            if constexpr (ILP == 2) {
+              for (uint32_t i = 0; i < h; ++i) {
+                mine[i] = a.next();
+                mine[h + 1 + i] = b.next();
+              }
+              mine[h] = a.next();
+            } else {
+              for (uint32_t i = 0; i < c; ++i) mine[i] = a.next();
+            }
+          }
+          __syncwarp();
+        }
       }
       fence_proxy_async_shared();
       __syncwarp();
@@ -181,7 +233,7 @@ static const void* pick40(int dt, int layout, uint32_t chains, uint32_t depth) {
 
 // Defaults for fields left zero (measured on GB300 with the 2^28-variate
 // FP64 workload).
-constexpr uint32_t k40DefDepth = 31, k40DefBlock = 256, k40DefChains = 2, k40DefBuffers = 1;
+constexpr uint32_t k40DefDepth = 31, k40DefBlock = 512, k40DefChains = 1, k40DefBuffers = 1;
 
 struct Launch40 {
   int dt, layout;

@@ -176,3 +176,73 @@ def test_two_chain_jump_distances():
         assert (s + h + 1 + 32 * c) - (s + c) - 1 == 31 * c + h
         # one chain: [s, s+c), next run at s + 32c
         assert (s + 32 * c) - (s + c) - 1 == 31 * c - 1
+
+
+H0, H1 = RHI & 0xFFFFFFFF, RHI >> 32
+RL1 = RLO >> 32
+
+
+def quot_fast_model(z):
+    """T = z*Rhi + z1*r1 from five 32x32-bit products; returns (floor(T/2^64),
+    high word of T mod 2^64)."""
+    z0, z1 = z & 0xFFFFFFFF, z >> 32
+    p00, p01, p10, p11, b = z0 * H0, z0 * H1, z1 * H0, z1 * H1, z1 * RL1
+    lo = p00 + b
+    c0 = lo >> 64
+    lo &= U64
+    mid = p01 + p10
+    cm = (mid >> 64) << 32
+    mid &= U64
+    f = lo + ((mid << 32) & U64)
+    c1 = f >> 64
+    f &= U64
+    return p11 + (mid >> 32) + cm + c0 + c1, f >> 32
+
+
+def bits_fast_model(q0, q1):
+    t = (32 - (q0 >> 32).bit_length()) - 11
+    mant = ((q0 << t) & U64) | ((q1 >> 32) >> (21 - t))
+    return (((1021 - t) << 52) + mant) & U64
+
+
+def undecided_states(count):
+    """States whose next remainder is within a few units of 3^40, so that
+    frac(2^53 z / 3^40) is within 2^-60 of 1: the fast quotient's fraction
+    is then in the undecided band."""
+    inv = pow(2 ** 53, -1, M40)
+    out = []
+    for k in range(1, count):
+        if k % 3:
+            out.append((M40 - k) * inv % M40)
+    return out
+
+
+def test_fast_quotient_is_exact_when_decided():
+    zs = states(30000, 5) + undecided_states(300)
+    flagged = 0
+    for z in zs:
+        q_fast, fhi = quot_fast_model(z)
+        exact = (z << 53) // M40
+        # T = z*Rhi + z1*r1 exactly, and it falls short of z*R/2^64 by less than 2^33+2
+        full = z * R >> 64
+        tt = z * RHI + (z >> 32) * RL1
+        assert tt >> 64 == q_fast and 0 <= full - tt < 2 ** 33 + 2
+        if fhi >= 0xFFFFFFFC:
+            flagged += 1
+            assert q_fast in (exact, exact - 1)
+        else:
+            assert q_fast == exact, z
+    assert flagged >= 200
+    for z in undecided_states(300):
+        assert quot_fast_model(z)[1] >= 0xFFFFFFFC
+
+
+def test_fast_conversion_matches_the_exact_one():
+    for z in states(20000, 6):
+        q0 = (z << 53) // M40
+        if q0 < 2 ** 32:
+            continue  # routed to the exact path
+        z1 = (z << 53) % M40
+        q1 = (z1 << 53) // M40
+        assert bits_fast_model(q0, q1) == bits_model(q0, q1), z
+        assert f64_from_bits(bits_fast_model(q0, q1)) == trunc_quotient(z)
