@@ -48,8 +48,24 @@ __device__ __forceinline__ void shl128(uint64_t x, uint32_t k, uint64_t& lo, uin
 //   goes to (s0, s1).
 struct Terms {
   uint64_t v0, v1, q0, q1, s0, s1;
+  double sq;  // RN(v*v) (FP64-pipe form only)
   bool fast;
 };
+
+// The grid images of RN(v*v) = M2 * 2^(e2 - 1075), M2 with its leading one:
+// on the 2^-157 grid it is M2 << k, k = e2 - 918 >= 0 (every square is at
+// least 2^-105).  Shared by both forms of the square.
+__device__ __forceinline__ void square_terms(uint64_t m2, uint32_t k, Terms& t) {
+  t.s0 = t.s1 = 0;
+  t.fast = k >= 64u;
+  if (__builtin_expect(t.fast, 1)) {
+    shl128(m2, k - 64u, t.q0, t.q1);
+  } else {
+    shl128(m2, k, t.s0, t.s1);            // exact, below 2^117
+    t.q0 = t.s1 + (t.s0 != 0 ? 1ull : 0ull);  // ceiling on the 2^-93 grid
+    t.q1 = 0;
+  }
+}
 
 __device__ __forceinline__ Terms variate_terms(uint64_t bits) {
   Terms t;
@@ -63,16 +79,22 @@ __device__ __forceinline__ Terms variate_terms(uint64_t bits) {
   const uint64_t rest = plo & ((1ull << sh) - 1ull);
   const uint64_t half = 1ull << (sh - 1u);
   m2 += (rest > half) | ((rest == half) & (m2 & 1ull));
-  const uint32_t k = 2u * e + sh - 1993u;
-  t.s0 = t.s1 = 0;
-  t.fast = k >= 64u;
-  if (__builtin_expect(t.fast, 1)) {
-    shl128(m2, k - 64u, t.q0, t.q1);
-  } else {
-    shl128(m2, k, t.s0, t.s1);            // exact, below 2^117
-    t.q0 = t.s1 + (t.s0 != 0 ? 1ull : 0ull);  // ceiling on the 2^-93 grid
-    t.q1 = 0;
-  }
+  square_terms(m2, 2u * e + sh - 1993u, t);
+  return t;
+}
+
+// The same terms with the square taken on the FP64 pipe: one round-to-nearest
+// multiply is RN(v*v) by definition, and its bits give M2 and e2 directly, so
+// the integer pipes only place the result on the grids.
+__device__ __forceinline__ Terms variate_terms_fp64(uint64_t bits) {
+  Terms t;
+  const uint32_t e = (uint32_t)(bits >> 52);
+  const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  shl128(mant, e - 970u, t.v0, t.v1);
+  const double v = __longlong_as_double((long long)bits);
+  t.sq = __dmul_rn(v, v);
+  const uint64_t sb = (uint64_t)__double_as_longlong(t.sq);
+  square_terms((sb & ((1ull << 52) - 1)) | (1ull << 52), (uint32_t)(sb >> 52) - 918u, t);
   return t;
 }
 
@@ -104,6 +126,9 @@ __device__ double round_words(uint64_t w0, uint64_t w1, uint64_t w2, int scale) 
   return ldexp((double)mant, low - scale);
 }
 
+// Where the squares run when tune.conv is 0 (measured on GB300).
+constexpr uint32_t kMcDefaultConv = CV_FP64;
+
 struct McParams {
   uint64_t ebase;       // (a - 3^33) mod P
   uint64_t block0;      // global number of the first block
@@ -116,6 +141,10 @@ struct McParams {
   uint32_t skip;
 };
 
+// FP64SQ: squares and the hit test on the FP64 pipe (RN(v*v) by one multiply,
+// the test as RN(RN(x*x) + RN(y*y)) <= 1 by one add), else all on the
+// integer pipes.  The two forms give identical bits.
+template <bool FP64SQ>
 __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t wpb = blockDim.x >> 5;
@@ -139,13 +168,16 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
     auto pair = [&](bool exact, uint32_t& qmin) {
       const uint64_t bx = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
       const uint64_t by = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
-      const Terms x = variate_terms(bx);
-      const Terms y = variate_terms(by);
+      const Terms x = FP64SQ ? variate_terms_fp64(bx) : variate_terms(bx);
+      const Terms y = FP64SQ ? variate_terms_fp64(by) : variate_terms(by);
       add128(a0, a1, x.v0, x.v1);
       add128(a0, a1, y.v0, y.v1);
       uint64_t r0 = x.q0, r1 = x.q1;
       add128(r0, r1, y.q0, y.q1);
-      hits += ((r1 < lim1) | ((r1 == lim1) & (r0 <= lim0))) ? 1u : 0u;
+      if constexpr (FP64SQ)
+        hits += __dadd_rn(x.sq, y.sq) <= 1.0 ? 1u : 0u;
+      else
+        hits += ((r1 < lim1) | ((r1 == lim1) & (r0 <= lim0))) ? 1u : 0u;
       if (__builtin_expect(x.fast & y.fast, 1)) {
         add128(h0, h1, r0, r1);
       } else {
@@ -225,6 +257,10 @@ rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblock
     return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 256", block);
   const uint32_t skip = t.skip ? t.skip : SK_TABLE;
   if (skip != SK_TABLE && skip != SK_SQMUL) return set_error(RNG_EINVAL, "bad tune.skip");
+  // tune.conv chooses where the squares and the hit test run: RNG_CONV_FP64
+  // on the FP64 pipe, RNG_CONV_INT on the integer pipes (0: the default)
+  const uint32_t conv = t.conv ? t.conv : kMcDefaultConv;
+  if (conv != CV_INT && conv != CV_FP64) return set_error(RNG_EINVAL, "bad tune.conv");
   cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
   McParams p;
   p.ebase = host_exponent_base(start_index, 0);
@@ -242,7 +278,8 @@ rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblock
   const uint64_t grid = (nblocks + wpb - 1) / wpb;
   if (grid > 0x7fffffffull) return set_error(RNG_ERANGE, "too many blocks for one launch");
   void* args[] = {&p};
-  e = cudaLaunchKernel((const void*)mc_kernel, dim3((unsigned)grid), dim3(block), args, 0, cs);
+  const void* fn = conv == CV_FP64 ? (const void*)mc_kernel<true> : (const void*)mc_kernel<false>;
+  e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, 0, cs);
   if (e != cudaSuccess) return cuda_error(e, "mc kernel launch");
   return RNG_OK;
 }

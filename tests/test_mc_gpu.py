@@ -28,11 +28,12 @@ def _run(R, a, nblocks, length, block0=0, tune=None):
             s1.cpu().numpy(), s2.cpu().numpy())
 
 
+@pytest.mark.parametrize("conv", ["int", "fp64"])
 @pytest.mark.parametrize("length", [2, 4, 62, 64, 66, 1000, 4096])
-def test_small_blocks_match_the_oracle(R, oracle_mod, length):
+def test_small_blocks_match_the_oracle(R, oracle_mod, length, conv):
     a = M + 100
     nblocks = 37
-    total, hits, s1, s2 = _run(R, a, nblocks, length)
+    total, hits, s1, s2 = _run(R, a, nblocks, length, tune=R.make_tune(conv=conv))
     oh, o1, o2 = oracle_mod.mc(a, length, np.arange(nblocks))
     assert np.array_equal(hits, oh.astype(np.int64))
     assert np.array_equal(s1.view(np.int64), o1.view(np.int64))
@@ -44,8 +45,8 @@ def test_block_offset_and_launch_shape(R, oracle_mod):
     a, length = 2 ** 53, 2048
     block0 = 10 ** 9 + 7
     ref = _run(R, a, 64, length, block0=block0)
-    for block in (32, 64, 256):
-        got = _run(R, a, 64, length, block0=block0, tune=R.make_tune(block=block))
+    for block, conv in ((32, "int"), (64, "fp64"), (256, "int"), (256, "fp64"), (96, "fp64")):
+        got = _run(R, a, 64, length, block0=block0, tune=R.make_tune(block=block, conv=conv))
         assert got[0] == ref[0]
         for x, y in zip(got[1:], ref[1:]):
             assert np.array_equal(np.asarray(x).view(np.int64), np.asarray(y).view(np.int64))
@@ -64,11 +65,12 @@ def test_blocks_holding_tiny_variates(R, oracle_mod):
     blocks = sorted({int(i) // length for i in tiny})
     assert len(blocks) >= 3
     for b in blocks[:5]:
-        total, hits, s1, s2 = _run(R, a, 3, length, block0=b - 1)
         oh, o1, o2 = oracle_mod.mc(a, length, np.arange(b - 1, b + 2))
-        assert np.array_equal(hits, oh.astype(np.int64)), b
-        assert np.array_equal(s1.view(np.int64), o1.view(np.int64)), b
-        assert np.array_equal(s2.view(np.int64), o2.view(np.int64)), b
+        for conv in ("int", "fp64"):
+            total, hits, s1, s2 = _run(R, a, 3, length, block0=b - 1, tune=R.make_tune(conv=conv))
+            assert np.array_equal(hits, oh.astype(np.int64)), (b, conv)
+            assert np.array_equal(s1.view(np.int64), o1.view(np.int64)), (b, conv)
+            assert np.array_equal(s2.view(np.int64), o2.view(np.int64)), (b, conv)
 
 
 def test_bad_arguments(R):
@@ -76,6 +78,8 @@ def test_bad_arguments(R):
         R.consume_mc(M + 100, 4, 7)      # odd length
     with pytest.raises(R.RNGError):
         R.consume_mc(M + 99, 4, 8)       # seed below 3^33+100
+    with pytest.raises(R.RNGError):
+        R.consume_mc(M + 100, 4, 8, tune=R.make_tune(conv=7))
 
 
 @pytest.mark.slow
@@ -85,6 +89,11 @@ def test_2_36_variates_subsample(R, oracle_mod):
     oracle, and the total against the per-block counts."""
     a, nblocks, length = M + 100, 1 << 20, 1 << 16
     total, hits, s1, s2 = _run(R, a, nblocks, length)
+    for conv in ("int", "fp64"):  # both forms of the squares on a sixteenth of the blocks
+        t2, h2, u1, u2 = _run(R, a, nblocks // 16, length, tune=R.make_tune(conv=conv))
+        assert np.array_equal(h2, hits[: nblocks // 16]), conv
+        assert np.array_equal(u1.view(np.int64), s1[: nblocks // 16].view(np.int64)), conv
+        assert np.array_equal(u2.view(np.int64), s2[: nblocks // 16].view(np.int64)), conv
     assert total == int(hits.sum())
     sub = np.arange(0, nblocks, 4096)
     oh, o1, o2 = oracle_mod.mc(a, length, sub)

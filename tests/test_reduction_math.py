@@ -201,6 +201,21 @@ def _sq_grid(v: float):
     return m2 << k, k
 
 
+def test_fp64_pipe_square_lands_on_the_same_grid():
+    """The FP64-pipe form takes RN(v*v) from one multiply and places its
+    significand M2 at k = e2 - 918 on the 2^-157 grid; that is the integer
+    form's M2 << k for every variate (down to the smallest, near 2^-53)."""
+    for z in states(20000, seed=9) + [1, 2, 3, 4, M - 1]:
+        v = float(Fraction(z) * Fraction(R3I))
+        sq = v * v  # one round-to-nearest multiply
+        b = f64_bits(sq)
+        e2, m2 = b >> 52, (b & (2 ** 52 - 1)) | 2 ** 52
+        k = e2 - 918
+        assert k >= 0
+        zi, ki = _sq_grid(v)
+        assert (m2 << k, k) == (zi, ki), z
+
+
 def test_fused_square_grid_and_split_hit_rule():
     """RN(v*v) is an integer on the 2^-157 grid for every variate; the hit
     test RN(RN(x^2)+RN(y^2)) <= 1 equals: exact high parts (k >= 64) plus
