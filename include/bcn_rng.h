@@ -370,8 +370,8 @@ rng_status rng_pool_destroy(bcn_pool *p);
  * they do not depend on the launch shape.  Asynchronous on `cuda_stream`.
  * tune: only `block` (multiple of 32, <= 256), `skip` and `conv` are read;
  * conv = RNG_CONV_FP64 (or 0, the default) takes each RN(v*v) with one FP64
- * multiply and the hit test with one FP64 add, RNG_CONV_INT forms them on
- * the integer pipes; the results are identical. */
+ * multiply, RNG_CONV_INT forms it on the integer pipes; the results are
+ * identical. */
 rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblocks, uint64_t len,
                           uint64_t *hits_total, uint64_t *hits, double *sum, double *sumsq,
                           void *cuda_stream, const rng_tune *tune);

@@ -48,7 +48,6 @@ __device__ __forceinline__ void shl128(uint64_t x, uint32_t k, uint64_t& lo, uin
 //   goes to (s0, s1).
 struct Terms {
   uint64_t v0, v1, q0, q1, s0, s1;
-  double sq;  // RN(v*v) (FP64-pipe form only)
   bool fast;
 };
 
@@ -92,8 +91,7 @@ __device__ __forceinline__ Terms variate_terms_fp64(uint64_t bits) {
   const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
   shl128(mant, e - 970u, t.v0, t.v1);
   const double v = __longlong_as_double((long long)bits);
-  t.sq = __dmul_rn(v, v);
-  const uint64_t sb = (uint64_t)__double_as_longlong(t.sq);
+  const uint64_t sb = (uint64_t)__double_as_longlong(__dmul_rn(v, v));
   square_terms((sb & ((1ull << 52) - 1)) | (1ull << 52), (uint32_t)(sb >> 52) - 918u, t);
   return t;
 }
@@ -141,9 +139,10 @@ struct McParams {
   uint32_t skip;
 };
 
-// FP64SQ: squares and the hit test on the FP64 pipe (RN(v*v) by one multiply,
-// the test as RN(RN(x*x) + RN(y*y)) <= 1 by one add), else all on the
-// integer pipes.  The two forms give identical bits.
+// FP64SQ: each RN(v*v) by one multiply on the FP64 pipe, else formed on the
+// integer pipes; the hit test and the sums stay integer either way (taking
+// the test's add on the FP64 pipe as well measured slower: that pipe is the
+// scarcer one).  The two forms give identical bits.
 template <bool FP64SQ>
 __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
   const uint32_t lane = threadIdx.x & 31u;
@@ -174,10 +173,7 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
       add128(a0, a1, y.v0, y.v1);
       uint64_t r0 = x.q0, r1 = x.q1;
       add128(r0, r1, y.q0, y.q1);
-      if constexpr (FP64SQ)
-        hits += __dadd_rn(x.sq, y.sq) <= 1.0 ? 1u : 0u;
-      else
-        hits += ((r1 < lim1) | ((r1 == lim1) & (r0 <= lim0))) ? 1u : 0u;
+      hits += ((r1 < lim1) | ((r1 == lim1) & (r0 <= lim0))) ? 1u : 0u;
       if (__builtin_expect(x.fast & y.fast, 1)) {
         add128(h0, h1, r0, r1);
       } else {
@@ -257,8 +253,8 @@ rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblock
     return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 256", block);
   const uint32_t skip = t.skip ? t.skip : SK_TABLE;
   if (skip != SK_TABLE && skip != SK_SQMUL) return set_error(RNG_EINVAL, "bad tune.skip");
-  // tune.conv chooses where the squares and the hit test run: RNG_CONV_FP64
-  // on the FP64 pipe, RNG_CONV_INT on the integer pipes (0: the default)
+  // tune.conv chooses where each RN(v*v) is formed: RNG_CONV_FP64 on the FP64
+  // pipe, RNG_CONV_INT on the integer pipes (0: the default)
   const uint32_t conv = t.conv ? t.conv : kMcDefaultConv;
   if (conv != CV_INT && conv != CV_FP64) return set_error(RNG_EINVAL, "bad tune.conv");
   cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
