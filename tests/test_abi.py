@@ -90,3 +90,32 @@ def test_empty_and_bad_pointer_calls_fail_before_any_launch(lib):
     assert raw.rng_generate(s._h, (1 << 46) + 1, 0, ctypes.c_void_p(4096)) == 2
     assert s.state[1] == 0
     assert b"aligned" in raw.rng_last_error() or raw.rng_last_error()
+
+
+def test_host_output_call_checks_arguments_first(lib):
+    raw = lib.lib
+    s = lib.Stream(3 ** 33 + 100)
+    assert raw.rng_generate_to_host(s._h, 0, 0, None, 0, 0) == 0      # n = 0: no-op
+    assert raw.rng_generate_to_host(s._h, 10, 0, None, 0, 0) == 1     # NULL output
+    assert raw.rng_generate_to_host(s._h, 10, 0, ctypes.c_void_p(4), 0, 0) == 1  # misaligned
+    buf = ctypes.create_string_buffer(128)
+    addr = (ctypes.addressof(buf) + 15) // 16 * 16
+    assert raw.rng_generate_to_host(s._h, 10, 0, ctypes.c_void_p(addr), 0, 9) == 1  # nbuf > 8
+    assert raw.rng_generate_to_host(s._h, 10, 0, ctypes.c_void_p(addr), 2 ** 41, 2) == 1
+    assert raw.rng_generate_to_host(s._h, 10, 7, ctypes.c_void_p(addr), 0, 2) == 1  # dtype
+    assert s.state[1] == 0
+
+
+def test_modulus_40_checks_arguments_first(lib):
+    raw = lib.lib
+    m40 = 3 ** 40
+    vp = ctypes.c_void_p(4096)
+    assert raw.rng40_generate_at(m40 + 99, 0, 10, 0, vp, None, None) == 2   # seed range
+    assert raw.rng40_generate_at(m40 + 100, 0, 0, 0, None, None, None) == 0  # n = 0
+    assert raw.rng40_generate_at(m40 + 100, 0, 10, 0, None, None, None) == 1
+    assert raw.rng40_generate_at(m40 + 100, 0, 10, 0, ctypes.c_void_p(4), None, None) == 1
+    assert raw.rng40_generate_at(m40 + 100, 0, 10, 5, vp, None, None) == 1  # dtype
+    assert raw.rng40_generate_at(m40 + 100, 0, (1 << 46) + 1, 0, vp, None, None) == 2
+    t = lib.make_tune(step="barrett")
+    assert raw.rng40_generate_at(m40 + 100, 0, 10, 0, vp, None, ctypes.byref(t)) == 1
+    assert b"3^40" in raw.rng_last_error()
