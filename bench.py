@@ -461,7 +461,7 @@ def run_ours(args):
     tuned = None
     if not args.no_autotune:  # measured choice of step, conversion and tile shape
         from paper_1206_1187_gb300 import autotune
-        tuned = autotune.tune_bulk("f64", n=1 << 26)  # cached per GPU model
+        tuned = autotune.tune_bulk("f64", n=n)  # on the workload itself; cached per GPU model
     out = torch.empty(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     ptr = out.data_ptr()

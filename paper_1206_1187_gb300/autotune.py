@@ -38,6 +38,13 @@ def bulk_candidates(dtype: str) -> list[dict]:
                             cands.append(dict(step=step, conv=conv, layout="tiled",
                                               depth=depth, block=block, chains=chains,
                                               buffers=buffers))
+    # wide blocks: with one tile buffer per warp, up to 28 warps of depth-31 tiles
+    # share an SM's shared memory
+    if dtype != "u64":
+        for depth, blocks in ((15, (768, 1024)), (31, (640, 768, 896))):
+            for block in blocks:
+                cands.append(dict(step="shared", conv="int", layout="tiled", depth=depth,
+                                  block=block, chains=2, buffers=1))
     return cands
 
 
