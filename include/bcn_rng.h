@@ -109,9 +109,10 @@ typedef struct {
   uint32_t unit;    /* BATCH: tiles per work unit (0 = choose); else ignored */
   uint32_t chains;  /* TILED, forward steps: independent chains per lane, 1
                        or 2 (0 = choose); 2 splits each lane's run in halves */
-  uint32_t buffers; /* TILED: shared-memory tile buffers per warp, 1 or 2 (0 =
-                       choose); 1 halves the shared memory, so more warps fit,
-                       at the cost of waiting for each tile's copy to be read */
+  uint32_t buffers; /* TILED and BATCH: shared-memory tile buffers per warp,
+                       1 or 2 (0 = choose); 1 halves the shared memory, so
+                       more warps fit, at the cost of waiting for each tile's
+                       copy to be read */
 } rng_tune;
 
 /* Largest n accepted by one generation call. */

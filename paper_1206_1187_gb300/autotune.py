@@ -99,8 +99,13 @@ BATCH_UNITS = (4, 16, 64)
 
 
 def batch_candidates() -> list[dict]:
-    return [dict(step="shared", conv="int", depth=d, block=b, chains=c, unit=u)
-            for d in BATCH_DEPTHS for b in BATCH_BLOCKS for c in (1, 2) for u in BATCH_UNITS]
+    cands = [dict(step="shared", conv="int", depth=d, block=b, chains=c, unit=u)
+             for d in BATCH_DEPTHS for b in BATCH_BLOCKS for c in (1, 2) for u in BATCH_UNITS]
+    # one tile buffer per warp, so that more warps fit per SM
+    cands += [dict(step="shared", conv="int", depth=d, block=b, chains=2, unit=u, buffers=1)
+              for d, blocks in ((15, (512, 768, 1024)), (31, (512, 640, 768, 896)))
+              for b in blocks for u in BATCH_UNITS]
+    return cands
 
 
 def tune_batch(nstreams: int = 512, reps: int = 3, use_cache: bool = True) -> dict:

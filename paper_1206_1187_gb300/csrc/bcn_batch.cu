@@ -63,11 +63,12 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const
       Gen<DT, STEP, CONV> b = lane_chain<DT, STEP, CONV>(d.ebase, first + c / 2 + 1, c, p.skip);
       warp_tiles2<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.jump_a, p.jump_aq, p.jump_b,
                                           p.jump_bq, a, b, reinterpret_cast<W*>(buf0_bytes),
-                                          issued, lane);
+                                          issued, lane, p.nbuf);
     } else {
       Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(d.ebase, first, c, p.skip);
       warp_tiles<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.jump, p.jump_q, g,
-                                         reinterpret_cast<W*>(buf0_bytes), issued, lane, 0);
+                                         reinterpret_cast<W*>(buf0_bytes), issued, lane, 0,
+                                         p.nbuf);
     }
   }
   const uint64_t r0 = s0 + ntiles * tile_elems, rl = s1 - r0;
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
-  // two tile buffers per warp, sized for 8-byte elements
-  unsigned char* const buf0 = smem + (size_t)warp * 2u * 32u * p.depth * 8u;
+  // p.nbuf tile buffers per warp, sized for 8-byte elements
+  unsigned char* const buf0 = smem + (size_t)warp * p.nbuf * 32u * p.depth * 8u;
   uint32_t issued = 0;
   for (;;) {
     unsigned long long u = 0;
@@ -160,9 +161,10 @@ static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
   p.depth = b->tune.depth;
   p.unit_tiles = b->tune.unit;
   p.skip = b->tune.skip;
+  p.nbuf = b->tune.buffers;
   cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), cs);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(batch counter)");
-  const size_t smem = (size_t)(b->tune.block / 32) * 2 * 32 * b->tune.depth * 8;
+  const size_t smem = batch_smem_bytes(b->tune.block, b->tune.depth, b->tune.buffers);
   void* args[] = {&p};
   e = cudaLaunchKernel(fn, dim3(b->tune.grid), dim3(b->tune.block), args, smem, cs);
   if (e != cudaSuccess) return cuda_error(e, "batch kernel launch");
@@ -191,6 +193,7 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   if (!t.depth) t.depth = 15;
   if (!t.block) t.block = 256;
   if (!t.unit) t.unit = 16;  // tiles per work unit
+  t.buffers = batch_buffers(t);
   t.layout = RNG_LAYOUT_TILED;
   t.chains = batch_chains(t);
   if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
@@ -204,10 +207,11 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   if (t.block % 32 != 0 || t.block == 0 || t.block > 1024)
     return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024", t.block);
   if (t.unit > 4096) return set_error(RNG_EINVAL, "tune.unit (tiles per work unit) > 4096");
+  if (t.buffers > 2) return set_error(RNG_EINVAL, "tune.buffers %u must be 0, 1 or 2", t.buffers);
   DeviceInfo di;
   rng_status st = device_info(&di);
   if (st != RNG_OK) return st;
-  const size_t smem = (size_t)(t.block / 32) * 2 * 32 * t.depth * 8;
+  const size_t smem = batch_smem_bytes(t.block, t.depth, t.buffers);
   if (smem > di.smem_optin)
     return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
                      smem, di.smem_optin);
@@ -409,6 +413,7 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   if (!t.depth) t.depth = 15;
   if (!t.block) t.block = 256;
   if (!t.unit) t.unit = 16;
+  t.buffers = batch_buffers(t);
   t.chains = batch_chains(t);
   if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
     return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
@@ -421,12 +426,13 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   if (t.block % 32 != 0 || t.block == 0 || t.block > 1024)
     return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024", t.block);
   if (t.unit > 4096) return set_error(RNG_EINVAL, "tune.unit (tiles per work unit) > 4096");
+  if (t.buffers > 2) return set_error(RNG_EINVAL, "tune.buffers %u must be 0, 1 or 2", t.buffers);
   DeviceInfo di;
   rng_status st = device_info(&di);
   if (st != RNG_OK) return st;
   if (di.device < 0 || di.device >= kNoallocMaxDevices)
     return set_error(RNG_EINVAL, "device %d beyond the no-allocation device table", di.device);
-  const size_t smem = (size_t)(t.block / 32) * 2 * 32 * t.depth * 8;
+  const size_t smem = batch_smem_bytes(t.block, t.depth, t.buffers);
   if (smem > di.smem_optin)
     return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
                      smem, di.smem_optin);
@@ -503,6 +509,7 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   p.depth = t.depth;
   p.unit_tiles = t.unit;
   p.skip = t.skip;
+  p.nbuf = t.buffers;
   void* args[] = {&p};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(t.block), args, smem, cs);
   if (e != cudaSuccess) return cuda_error(e, "batch kernel launch (no-allocation)");

@@ -26,6 +26,7 @@ struct BatchParams {
   uint32_t depth;
   uint32_t unit_tiles;
   uint32_t skip;
+  uint32_t nbuf;         // tile buffers per warp (1 or 2)
 };
 
 // The batched kernel for a step variant, conversion, chains per lane and tile
@@ -42,8 +43,10 @@ inline uint32_t batch_chains(const rng_tune& t) {
 
 // Fill the tile-jump multipliers (and their precomputed quotients) of p.
 void batch_fill_jumps(BatchParams& p, int step, uint32_t depth);
-inline size_t batch_smem_bytes(uint32_t block, uint32_t depth) {
-  return (size_t)(block / 32) * 2 * 32 * depth * 8;
+// Tile buffers per warp for this tuning: tune.buffers, 0 meaning 2.
+inline uint32_t batch_buffers(const rng_tune& t) { return t.buffers ? t.buffers : 2u; }
+inline size_t batch_smem_bytes(uint32_t block, uint32_t depth, uint32_t nbuf) {
+  return (size_t)(block / 32) * nbuf * 32 * depth * 8;
 }
 
 }  // namespace bcn

@@ -233,7 +233,7 @@ static const void* pick40(int dt, int layout, uint32_t chains, uint32_t depth) {
 
 // Defaults for fields left zero (measured on GB300 with the 2^28-variate
 // FP64 workload).
-constexpr uint32_t k40DefDepth = 31, k40DefBlock = 512, k40DefChains = 1, k40DefBuffers = 1;
+constexpr uint32_t k40DefDepth = 31, k40DefBlock = 896, k40DefChains = 1, k40DefBuffers = 1;
 
 struct Launch40 {
   int dt, layout;

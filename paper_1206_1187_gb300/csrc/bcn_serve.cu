@@ -229,6 +229,7 @@ static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units)
   p.depth = s->tune.depth;
   p.unit_tiles = s->tune.unit;
   p.skip = s->tune.skip;
+  p.nbuf = s->tune.buffers;
   const uint64_t wpb = s->tune.block / 32;
   const uint64_t grid = std::max<uint64_t>(1, std::min(s->grid_full, (units + wpb - 1) / wpb));
   void* args[] = {&p};
@@ -306,15 +307,17 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
   if (!t.depth) t.depth = 15;
   if (!t.block) t.block = 256;
   if (!t.unit) t.unit = 4;
+  t.buffers = batch_buffers(t);
   t.chains = batch_chains(t);
-  if (t.depth % 2 == 0 || t.depth > kMaxDepth || t.block % 32 || !t.block || t.block > 1024)
+  if (t.depth % 2 == 0 || t.depth > kMaxDepth || t.block % 32 || !t.block || t.block > 1024 ||
+      t.buffers > 2)
     return set_error(RNG_EINVAL, "bad server tuning");
   const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, t.depth);
   if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
   DeviceInfo di;
   rng_status stt = device_info(&di);
   if (stt != RNG_OK) return stt;
-  const size_t smem = batch_smem_bytes(t.block, t.depth);
+  const size_t smem = batch_smem_bytes(t.block, t.depth, t.buffers);
   if (smem > di.smem_optin) return set_error(RNG_EINVAL, "tile buffers exceed shared memory");
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)di.smem_optin);

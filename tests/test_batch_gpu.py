@@ -85,7 +85,10 @@ def test_tuning_and_graph_never_change_the_bytes(R):
                  dict(depth=15, block=256, unit=16, conv="fp64"),
                  dict(depth=15, block=128, unit=8, chains=1),
                  dict(depth=31, block=128, unit=4, chains=2),
-                 dict(depth=21, block=64, unit=3, chains=2, step="barrett")]:
+                 dict(depth=21, block=64, unit=3, chains=2, step="barrett"),
+                 dict(depth=31, block=896, unit=4, chains=2, buffers=1),
+                 dict(depth=15, block=64, unit=5, chains=1, buffers=1),
+                 dict(depth=9, block=96, unit=2, chains=2, buffers=1, step="barrett")]:
         pool, offs, outs = _pool_outputs(counts, dtypes, np.random.default_rng(6))
         b = R.Batch(starts, counts, dtypes, outs=outs, offsets=offsets, tune=tune)
         b.launch()
@@ -108,6 +111,9 @@ def test_batch_rejects_bad_streams(R):
     assert e.value.status == 2
     with pytest.raises(R.RNGError) as e:
         R.Batch([M + 100], [10], ["f64"], outs=[out], tune=dict(depth=4))
+    assert e.value.status == 1
+    with pytest.raises(R.RNGError) as e:
+        R.Batch([M + 100], [10], ["f64"], outs=[out], tune=dict(buffers=3))
     assert e.value.status == 1
 
 
