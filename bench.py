@@ -48,7 +48,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -213,10 +213,11 @@ def measure_batched(rng, stream, achieved_gbs: float, steps: int):
     import torch
     from paper_1206_1187_gb300 import inputs
     from paper_1206_1187_gb300 import autotune
-    tuned = autotune.tune_batch()  # measured batch-plan tuning, cached per GPU model
     starts, counts, dtypes = inputs.batch_streams()
     tdt = {"f64": torch.float64, "f32": torch.float32}
     outs = [torch.empty(int(c), dtype=tdt[d], device="cuda") for c, d in zip(counts, dtypes)]
+    # batch-plan tuning measured on this workload itself, cached per GPU model
+    tuned = autotune.tune_batch(workload=(starts, counts, dtypes, outs), tag="batched-4096-seed7")
     b = rng.Batch(starts, counts, dtypes, outs=outs, tune=tuned["best"])
     info = b.info()
     for _ in range(3):

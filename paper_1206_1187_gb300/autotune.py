@@ -108,20 +108,28 @@ def batch_candidates() -> list[dict]:
     return cands
 
 
-def tune_batch(nstreams: int = 512, reps: int = 3, use_cache: bool = True) -> dict:
-    """Time batch-plan tunings on a representative batch (the batched workload's
-    generator, lengths log-uniform 10^3..10^6) and return
-    {"best": tuning, "table": [[candidate, ms], ...]}; cached per GPU model."""
+def tune_batch(nstreams: int = 512, reps: int = 3, use_cache: bool = True,
+               workload=None, tag: str = "") -> dict:
+    """Time batch-plan tunings and return {"best": tuning, "table": [[candidate,
+    ms], ...]}; cached per GPU model.  By default on a representative batch (the
+    batched workload's generator, nstreams streams of lengths log-uniform
+    10^3..10^6); `workload` = (starts, counts, dtypes, outs) tunes on that batch
+    itself, cached under `tag`."""
     from . import inputs
-    key = f"{torch.cuda.get_device_name(torch.cuda.current_device())}|batch|{nstreams}" \
+    name = tag if workload is not None else str(nstreams)
+    key = f"{torch.cuda.get_device_name(torch.cuda.current_device())}|batch|{name}" \
           f"|v{rng.version()}"
     with _lock:
         cache = _load_cache() if use_cache else {}
         if key in cache:
             return cache[key]
-        starts, counts, dtypes = inputs.batch_streams(nstreams=nstreams, len_hi=1e6)
-        tdt = {"f64": torch.float64, "f32": torch.float32}
-        outs = [torch.empty(int(c), dtype=tdt[d], device="cuda") for c, d in zip(counts, dtypes)]
+        if workload is not None:
+            starts, counts, dtypes, outs = workload
+        else:
+            starts, counts, dtypes = inputs.batch_streams(nstreams=nstreams, len_hi=1e6)
+            tdt = {"f64": torch.float64, "f32": torch.float32}
+            outs = [torch.empty(int(c), dtype=tdt[d], device="cuda")
+                    for c, d in zip(counts, dtypes)]
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         table = []
