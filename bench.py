@@ -350,7 +350,8 @@ def measure_serving(rng, n_requests: int = 20000):
                       "p99_ms": float(np.percentile(lat, 99) * 1e3),
                       "p999_ms": float(np.percentile(lat, 99.9) * 1e3),
                       "max_ms": float(lat.max() * 1e3),
-                      "iterations": st["iterations"], "mean_items_per_iteration":
+                      "iterations": st["iterations"],
+                      "heavy_iterations": st["heavy_iterations"], "mean_items_per_iteration":
                           st["items"] / max(st["iterations"], 1),
                       "peak_pool_gb": st["peak_pool_bytes"] / 1e9,
                       "peak_active": st["peak_active"]}

@@ -294,12 +294,17 @@ typedef struct {
   uint32_t pad;
   double release_after_s;  /* >= 0: free a result's pool range this long after
                               it completes; < 0: the caller releases it        */
-  rng_tune tune;           /* batched-kernel tuning (zero fields = choose)     */
+  rng_tune tune;           /* batched-kernel tuning; all zero = the server
+                              picks per iteration: short tiles in small blocks
+                              for light iterations, deep tiles in wide blocks
+                              (one buffer per warp) once an iteration holds two
+                              such tiles for every warp of the GPU            */
 } rng_server_config;
 
 typedef struct {
   uint64_t submitted, completed, iterations, items, max_items_seen;
   uint64_t peak_active, peak_pool_bytes, bytes_done, pool_in_use, pool_bytes;
+  uint64_t heavy_iterations;  /* iterations launched with the throughput shape */
 } rng_server_stats;
 
 /* Request states reported by rng_server_status. */
@@ -335,7 +340,9 @@ rng_status rng_server_stats_get(bcn_server *s, rng_server_stats *out);
  * arrival_s[i] seconds after the call starts (open loop), then every request
  * is awaited (RNG_ETIMEOUT after timeout_s).  latency_s[i] receives the time
  * from request i's scheduled arrival to its completion; *wall_s (nullable) the
- * time from the start to the last completion. */
+ * time from the start to the last completion.  With release_after_s < 0 the
+ * results are never freed, so a trace whose outputs exceed the pool is
+ * RNG_EINVAL before anything is submitted. */
 rng_status rng_server_run_trace(bcn_server *s, uint32_t n, const double *arrival_s,
                                 const uint64_t *starts, const uint64_t *offsets,
                                 const uint64_t *counts, const uint8_t *dtypes, double timeout_s,

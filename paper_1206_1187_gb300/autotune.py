@@ -113,7 +113,8 @@ def tune_batch(nstreams: int = 512, reps: int = 3, use_cache: bool = True,
     """Time batch-plan tunings and return {"best": tuning, "table": [[candidate,
     ms], ...]}; cached per GPU model.  By default on a representative batch (the
     batched workload's generator, nstreams streams of lengths log-uniform
-    10^3..10^6); `workload` = (starts, counts, dtypes, outs) tunes on that batch
+    10^3..10^6); `workload` = (starts, counts, dtypes, outs), or a callable
+    returning it (called only when the cache has no entry), tunes on that batch
     itself, cached under `tag`."""
     from . import inputs
     name = tag if workload is not None else str(nstreams)
@@ -124,7 +125,7 @@ def tune_batch(nstreams: int = 512, reps: int = 3, use_cache: bool = True,
         if key in cache:
             return cache[key]
         if workload is not None:
-            starts, counts, dtypes, outs = workload
+            starts, counts, dtypes, outs = workload() if callable(workload) else workload
         else:
             starts, counts, dtypes = inputs.batch_streams(nstreams=nstreams, len_hi=1e6)
             tdt = {"f64": torch.float64, "f32": torch.float32}

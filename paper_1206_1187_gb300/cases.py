@@ -31,13 +31,14 @@ def main(argv):
         for _ in range(reps):
             rng.generate_at(seed, 0, size, dtype, out=out)
     elif case == "batch":
-        # the benchmark's tuning, measured on the batched workload itself
-        starts, counts, dtypes = inputs.batch_streams()
         tdt = {"f64": torch.float64, "f32": torch.float32}
-        outs = [torch.empty(int(c), dtype=tdt[d], device="cuda") for c, d in zip(counts, dtypes)]
-        tune = autotune.tune_batch(workload=(starts, counts, dtypes, outs),
-                                   tag="batched-4096-seed7")["best"]
-        del outs
+
+        def workload():  # built only if the tuning is not cached yet
+            st, co, dt = inputs.batch_streams()
+            return st, co, dt, [torch.empty(int(c), dtype=tdt[d], device="cuda")
+                                for c, d in zip(co, dt)]
+        # the benchmark's tuning, measured on the batched workload itself
+        tune = autotune.tune_batch(workload=workload, tag="batched-4096-seed7")["best"]
         torch.cuda.empty_cache()
         starts, counts, dtypes = inputs.batch_streams(nstreams=size, len_hi=1e6)
         outs = [torch.empty(int(c), dtype=tdt[d], device="cuda") for c, d in zip(counts, dtypes)]

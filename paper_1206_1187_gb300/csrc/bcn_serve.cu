@@ -16,7 +16,14 @@
 //      launch the batched kernel on that slot's CUDA stream.
 // With several slots, requests admitted while earlier iterations run are
 // launched on another stream and overlap them on the device; chunking keeps a
-// 256 MiB request from holding back the small ones.  Every chunk is a block of
+// 256 MiB request from holding back the small ones.
+//
+// Two kernel shapes, chosen per iteration by its size when the tuning is left
+// to the server: a light iteration runs short tiles in small blocks (the
+// lowest latency for small requests), a heavy one -- enough work for two
+// wide tiles per warp of the whole GPU -- deep tiles in 896-thread blocks with
+// one buffer per warp (the highest throughput).  The bytes never depend on the
+// shape.  Every chunk is a block of
 // its request's sequence reached by skip-ahead (the paper's parallel split,
 // Sec. 1), so a request's bytes never depend on what it was batched with.
 #include <algorithm>
@@ -24,6 +31,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -51,6 +59,14 @@ struct Request {
   double t_arrive = 0, t_admit = 0, t_done = 0;
 };
 
+// One launch shape of the batched kernel.
+struct ServeShape {
+  rng_tune tune;
+  const void* fn = nullptr;
+  size_t smem = 0;
+  uint64_t grid_full = 0;
+};
+
 struct Slot {
   cudaStream_t cs = nullptr;
   cudaEvent_t ev = nullptr;
@@ -65,10 +81,9 @@ struct Slot {
 
 struct bcn_server {
   rng_server_config cfg;
-  rng_tune tune;
-  const void* fn = nullptr;
-  size_t smem = 0;
-  uint64_t grid_full = 0;
+  bcn::ServeShape shape[2];   // [0] light iterations, [1] heavy ones
+  uint32_t nshapes = 1;
+  uint64_t heavy_elems = 0;   // an iteration of at least this many elements is heavy
   int device = 0;
   unsigned char* pool_dev = nullptr;
   bcn::Pool pool;
@@ -168,12 +183,22 @@ static bool admit(bcn_server* s, double t) {
 }
 
 // Pack the next chunk of every active request into slot `sl` (mu held).
-// Returns the number of work items.
-static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out) {
-  const uint64_t unit_elems = 32ull * s->tune.depth * s->tune.unit;
+// Returns the number of work items; *shape_out the kernel shape to launch.
+static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out, uint32_t* shape_out) {
+  const size_t na = s->active.size();
+  uint32_t shape = 0;
+  if (s->nshapes > 1) {  // the iteration's size decides the shape
+    uint64_t total = 0;
+    for (size_t k = 0; k < na && k < s->cfg.max_items; ++k) {
+      const Request& r = s->reqs[s->active[(s->rr + k) % na]];
+      total += std::min<uint64_t>(r.n - r.scheduled, s->cfg.chunk_elems);
+    }
+    if (total >= s->heavy_elems) shape = 1;
+  }
+  const rng_tune& tn = s->shape[shape].tune;
+  const uint64_t unit_elems = 32ull * tn.depth * tn.unit;
   uint32_t items = 0;
   uint64_t units = 0;
-  const size_t na = s->active.size();
   std::vector<uint64_t> still;
   still.reserve(na);
   for (size_t k = 0; k < na; ++k) {
@@ -204,10 +229,13 @@ static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out) {
   s->active.swap(still);
   s->rr = s->active.empty() ? 0 : (s->rr + 1) % s->active.size();
   *units_out = units;
+  *shape_out = shape;
   return items;
 }
 
-static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units) {
+static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units,
+                        uint32_t shape) {
+  const ServeShape& sh = s->shape[shape];
   const size_t desc_bytes = sizeof(BatchDesc) * s->cfg.max_items;
   const size_t prefix_bytes = sizeof(uint64_t) * (s->cfg.max_items + 1);
   cudaError_t e = cudaMemcpyAsync(sl.d_table, sl.h_desc, sizeof(BatchDesc) * items,
@@ -224,16 +252,16 @@ static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units)
   p.prefix = reinterpret_cast<const uint64_t*>(sl.d_table + desc_bytes);
   p.counter = counter;
   p.total_units = units;
-  batch_fill_jumps(p, (int)s->tune.step, s->tune.depth);
+  batch_fill_jumps(p, (int)sh.tune.step, sh.tune.depth);
   p.nstreams = items;
-  p.depth = s->tune.depth;
-  p.unit_tiles = s->tune.unit;
-  p.skip = s->tune.skip;
-  p.nbuf = s->tune.buffers;
-  const uint64_t wpb = s->tune.block / 32;
-  const uint64_t grid = std::max<uint64_t>(1, std::min(s->grid_full, (units + wpb - 1) / wpb));
+  p.depth = sh.tune.depth;
+  p.unit_tiles = sh.tune.unit;
+  p.skip = sh.tune.skip;
+  p.nbuf = sh.tune.buffers;
+  const uint64_t wpb = sh.tune.block / 32;
+  const uint64_t grid = std::max<uint64_t>(1, std::min(sh.grid_full, (units + wpb - 1) / wpb));
   void* args[] = {&p};
-  e = cudaLaunchKernel(s->fn, dim3((unsigned)grid), dim3(s->tune.block), args, s->smem, sl.cs);
+  e = cudaLaunchKernel(sh.fn, dim3((unsigned)grid), dim3(sh.tune.block), args, sh.smem, sl.cs);
   if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.cs);
   if (e != cudaSuccess) return server_fail(s, e, "launching an iteration");
   sl.busy = true;
@@ -249,7 +277,7 @@ static void worker_main(bcn_server* s) {
         free_slot = &sl;
         break;
       }
-    uint32_t items = 0;
+    uint32_t items = 0, shape = 0;
     uint64_t units = 0;
     {
       std::unique_lock<std::mutex> lock(s->mu);
@@ -257,8 +285,9 @@ static void worker_main(bcn_server* s) {
       release_due(s, t);
       did |= admit(s, t);
       if (free_slot && !s->active.empty() && s->err == RNG_OK) {
-        items = pack(s, *free_slot, &units);
+        items = pack(s, *free_slot, &units, &shape);
         s->st.iterations += 1;
+        s->st.heavy_iterations += shape;
         s->st.items += items;
         if (items > s->st.max_items_seen) s->st.max_items_seen = items;
       }
@@ -275,7 +304,7 @@ static void worker_main(bcn_server* s) {
       }
     }
     if (items > 0) {
-      launch_slot(s, *free_slot, items, units);
+      launch_slot(s, *free_slot, items, units, shape);
       did = true;
     }
     if (!did) std::this_thread::yield();  // polling completion events
@@ -299,40 +328,61 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
   if (!cfg.max_items) cfg.max_items = 1024;
   if (!cfg.inflight) cfg.inflight = 2;
   if (cfg.inflight > 8) return set_error(RNG_EINVAL, "inflight must be 1..8");
-  rng_tune t = cfg.tune;
-  const rng_tune d = auto_defaults(RNG_F64);
-  if (!t.step) t.step = d.step ? d.step : ST_SHARED;
-  if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
-  if (!t.skip) t.skip = SK_TABLE;
-  if (!t.depth) t.depth = 15;
-  if (!t.block) t.block = 256;
-  if (!t.unit) t.unit = 4;
-  t.buffers = batch_buffers(t);
-  t.chains = batch_chains(t);
-  if (t.depth % 2 == 0 || t.depth > kMaxDepth || t.block % 32 || !t.block || t.block > 1024 ||
-      t.buffers > 2)
-    return set_error(RNG_EINVAL, "bad server tuning");
-  const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, t.depth);
-  if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
   DeviceInfo di;
   rng_status stt = device_info(&di);
   if (stt != RNG_OK) return stt;
-  const size_t smem = batch_smem_bytes(t.block, t.depth, t.buffers);
-  if (smem > di.smem_optin) return set_error(RNG_EINVAL, "tile buffers exceed shared memory");
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)di.smem_optin);
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(server)");
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)t.block, smem);
-  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  // the caller's tuning gives one shape; a tuning left to the server gives two
+  const rng_tune zero = {};
+  const bool adaptive = memcmp(&cfg.tune, &zero, sizeof zero) == 0;
+  ServeShape shapes[2];
+  const uint32_t nshapes = adaptive ? 2 : 1;
+  for (uint32_t k = 0; k < nshapes; ++k) {
+    rng_tune t = cfg.tune;
+    if (adaptive && k == 1) {  // the throughput shape
+      t.depth = 31;
+      t.block = 896;
+      t.unit = 16;
+      t.buffers = 1;
+      t.chains = 2;
+    }
+    const rng_tune d = auto_defaults(RNG_F64);
+    if (!t.step) t.step = d.step ? d.step : ST_SHARED;
+    if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
+    if (!t.skip) t.skip = SK_TABLE;
+    if (!t.depth) t.depth = 15;
+    if (!t.block) t.block = 256;
+    if (!t.unit) t.unit = 4;
+    t.buffers = batch_buffers(t);
+    t.chains = batch_chains(t);
+    if (t.depth % 2 == 0 || t.depth > kMaxDepth || t.block % 32 || !t.block || t.block > 1024 ||
+        t.buffers > 2)
+      return set_error(RNG_EINVAL, "bad server tuning");
+    const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, t.depth);
+    if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
+    const size_t smem = batch_smem_bytes(t.block, t.depth, t.buffers);
+    if (smem > di.smem_optin) return set_error(RNG_EINVAL, "tile buffers exceed shared memory");
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)di.smem_optin);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(server)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)t.block, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    shapes[k].tune = t;
+    shapes[k].fn = fn;
+    shapes[k].smem = smem;
+    shapes[k].grid_full = (uint64_t)std::max(per_sm, 1) * (uint64_t)di.sms;
+  }
+  cudaError_t e = cudaSuccess;
 
   bcn_server* s = new (std::nothrow) bcn_server(cfg.pool_bytes);
   if (!s) return set_error(RNG_ENOMEM, "out of host memory");
   s->cfg = cfg;
-  s->tune = t;
-  s->fn = fn;
-  s->smem = smem;
-  s->grid_full = (uint64_t)std::max(per_sm, 1) * (uint64_t)di.sms;
+  s->nshapes = nshapes;
+  for (uint32_t k = 0; k < nshapes; ++k) s->shape[k] = shapes[k];
+  if (nshapes > 1) {  // two wide tiles for every warp of the GPU
+    const rng_tune& w = shapes[1].tune;
+    s->heavy_elems = shapes[1].grid_full * (w.block / 32) * 2ull * 32ull * w.depth;
+  }
   s->device = di.device;
   auto cleanup = [s]() {
     for (Slot& sl : s->slots) {
@@ -494,6 +544,18 @@ rng_status rng_server_run_trace(bcn_server* s, uint32_t n, const double* arrival
                                 double* latency_s, double* wall_s) {
   if (!s || !arrival_s || !starts || !counts || !dtypes || !latency_s)
     return set_error(RNG_EINVAL, "NULL argument");
+  if (s->cfg.release_after_s < 0) {  // results stay in the pool: the trace must fit it
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      const uint64_t b = (counts[i] * dtype_size(dtypes[i]) + 255) / 256 * 256;
+      total = total > UINT64_MAX - b ? UINT64_MAX : total + b;
+    }
+    if (total > s->cfg.pool_bytes)
+      return set_error(RNG_EINVAL,
+                       "the trace needs %llu pool bytes and release_after_s < 0 never frees "
+                       "them: the pool holds %llu",
+                       (unsigned long long)total, (unsigned long long)s->cfg.pool_bytes);
+  }
   std::vector<uint64_t> ids(n, 0);
   const double t0 = now_s();
   for (uint32_t i = 0; i < n; ++i) {

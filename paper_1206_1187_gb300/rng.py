@@ -68,7 +68,8 @@ class ServerConfig(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in
                 ("submitted", "completed", "iterations", "items", "max_items_seen",
-                 "peak_active", "peak_pool_bytes", "bytes_done", "pool_in_use", "pool_bytes")]
+                 "peak_active", "peak_pool_bytes", "bytes_done", "pool_in_use", "pool_bytes",
+                 "heavy_iterations")]
 
 
 def _load() -> ctypes.CDLL:

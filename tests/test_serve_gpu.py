@@ -120,3 +120,46 @@ def test_trace_replay_latencies(R):
     assert st["completed"] == 3000
     assert np.percentile(lat, 99) < 0.5
     srv.close()
+
+
+def test_trace_that_cannot_fit_a_never_releasing_pool_is_rejected(R):
+    """With results held until the caller frees them, a trace whose outputs
+    exceed the pool could never finish: it is refused before any submission."""
+    from paper_1206_1187_gb300 import inputs
+    arrivals, counts, dtypes, seeds, offsets = inputs.request_trace(
+        200, rate_hz=20000.0, seed=3, min_bytes=1 << 20, max_bytes=4 << 20)
+    srv = R.Server(pool_bytes=64 << 20)  # release_after_s < 0: never freed by the server
+    with pytest.raises(R.RNGError) as e:
+        srv.run_trace(arrivals, seeds, counts, dtypes, offsets=offsets, timeout_s=10.0)
+    assert e.value.status == 1 and "never frees" in str(e.value)
+    assert srv.stats()["submitted"] == 0
+    srv.close()
+
+
+def test_heavy_iterations_give_the_same_bytes(R, oracle_mod):
+    """Iterations large enough for the throughput shape (deep tiles, wide
+    blocks) give each request the bytes it gets alone (light shape)."""
+    rnd = np.random.default_rng(21)
+    reqs = [(int(rnd.integers(M + 100, 2 ** 53 - 10 ** 8)), int(rnd.integers(0, 2 ** 40)),
+             int(rnd.integers(3 << 20, 5 << 20)), ("f64", "f32")[k % 2]) for k in range(12)]
+    srv = R.Server(pool_bytes=1 << 30)
+    ids = [srv.submit(a, off, n, dt) for a, off, n, dt in reqs]
+    for rid in ids:
+        srv.wait(rid, 60.0)
+    st = srv.stats()
+    assert st["heavy_iterations"] > 0
+    mixed = [_bits(srv.read(rid, n, dt)) for rid, (a, off, n, dt) in zip(ids, reqs)]
+    srv.close()
+    srv = R.Server(pool_bytes=1 << 30, chunk_elems=1 << 20)
+    for (a, off, n, dt), got in zip(reqs, mixed):
+        rid = srv.submit(a, off, n, dt)
+        srv.wait(rid, 60.0)
+        assert np.array_equal(_bits(srv.read(rid, n, dt)), got)
+        srv.release(rid)
+    assert srv.stats()["heavy_iterations"] == 0
+    srv.close()
+    for (a, off, n, dt), got in list(zip(reqs, mixed))[:3]:
+        idx = np.unique(np.concatenate([np.arange(1000), np.arange(n - 1000, n),
+                                        rnd.integers(0, n, 1000)]))
+        want = oracle_mod.at(a, (off + idx).astype(np.uint64), dt)
+        assert np.array_equal(got[idx], _obits(want))
