@@ -131,13 +131,18 @@ def test_undecided_quotients(R, oracle_mod):
     remainder within a few units of 3^40) force the exact redo of their run;
     placed inside tiles and in both chains of a lane."""
     a = M40 + 271828
-    inv = pow(2 ** 53, -1, M40)
-    for k in (1, 2, 4, 5, 1000, 2 ** 20 + 1):
-        z = (M40 - k) * inv % M40
+    zs = []
+    for shift in (53, 106):  # one step (single estimate) or two steps (pair estimate) ahead
+        inv = pow(2 ** shift, -1, M40)
+        zs += [(M40 - k) * inv % M40 for k in (1, 2, 4, 5, 1000, 2 ** 20 + 1)]
+    for z in zs:
         i = index_of_state(a, z)
         for lead, n, tune in [(100, 5000, None), (3, 992 * 3, dict(depth=31, block=32, chains=2)),
                               (20, 992 * 3, dict(depth=31, block=32, chains=2)),
-                              (7, 480 * 2, dict(depth=15, block=32, chains=1))]:
+                              (7, 480 * 2, dict(depth=15, block=32, chains=1)),
+                              (8, 480 * 2, dict(depth=15, block=32, chains=1)),
+                              (30, 992 * 2, dict(depth=31, block=32, chains=1)),
+                              (31, 992 * 2, dict(depth=31, block=32, chains=1))]:
             off = (i - lead) % P40
             for dtype in ("f64", "f32"):
                 _check(R, oracle_mod, a, off, n, dtype, tune)
