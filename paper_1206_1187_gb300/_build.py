@@ -10,6 +10,7 @@ import concurrent.futures
 import glob
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -69,13 +70,22 @@ def _source_path(name: str) -> str:
     return p if os.path.exists(p) else os.path.join(INCLUDE, name)
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and with whitespace runs collapsed, so a
+    digest changes with the code, not with its commentary."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_digest(kernel: str) -> str:
-    """16 hex digits identifying the sources and flags one kernel is built from."""
+    """16 hex digits identifying the code (comments aside) and flags one kernel
+    is built from."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
-        with open(_source_path(name), "rb") as fh:
+        with open(_source_path(name), encoding="utf-8") as fh:
             h.update(name.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     h.update(" ".join(f for f in NVCC_FLAGS if not os.path.isabs(f)).encode())  # no paths
     return h.hexdigest()[:16]
 

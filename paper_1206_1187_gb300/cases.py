@@ -2,7 +2,7 @@
 
     python -m paper_1206_1187_gb300.cases bulk 33554432 [reps]
     python -m paper_1206_1187_gb300.cases bulk32 33554432 [reps]
-    python -m paper_1206_1187_gb300.cases batch 256 [reps]
+    python -m paper_1206_1187_gb300.cases batch 2048 [reps]
     python -m paper_1206_1187_gb300.cases mc 16384 [reps]
     python -m paper_1206_1187_gb300.cases m40 33554432 [reps]
 

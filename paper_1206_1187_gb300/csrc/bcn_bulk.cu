@@ -9,9 +9,12 @@
 // stores bank-conflict free), and one lane hands the whole tile to the bulk
 // async-copy engine (cp.async.bulk shared::cta -> global), so global memory
 // sees one contiguous, 16-byte aligned write per tile with no per-thread
-// store instructions.  Two tile buffers per warp let the copy of one tile
-// overlap the generation of the next.  Moving from a tile to the warp's next
-// tile is one modular product by a precomputed power of 2^53.
+// store instructions.  A warp keeps one or two tile buffers: with two, the
+// copy of one tile overlaps the generation of the next; with one (the
+// measured choice at depth 31), the warp waits for its last copy to finish
+// reading before refilling, and twice as many warps fit per SM to cover the
+// wait.  Moving from a tile to the warp's next tile is one modular product by
+// a precomputed power of 2^53.
 //
 // DIRECT layout (the paper's per-thread split, Sec. 1): thread t of T owns
 // [t*n/T, (t+1)*n/T) and stores each variate itself.  It serves odd thread

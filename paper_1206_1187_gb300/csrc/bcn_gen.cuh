@@ -143,15 +143,7 @@ __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-// `ntiles` consecutive tiles of 32*c elements, the first at element `first`
-// of `out` (16-byte aligned).  Lane l produces elements [l*c, (l+1)*c) of each
-// tile with c steps of chain g, writes them to one of the warp's two tile
-// buffers in shared memory, and lane 0 hands the tile to the bulk-copy engine.
-// `issued` counts the warp's committed bulk groups: before a buffer is reused,
-// lane 0 waits until the copy that last read it is done.  Between tiles the
-// chain jumps with one product by `jump` (2^(53*31c) forward, 2^(53*33c) for
-// the backward Montgomery chain, whose state is the last element of a run);
-// `jump_q` is its precomputed quotient for mulmod_pre.
+
 // The shared-quotient step's fast path for a whole run of c variates: no
 // per-variate branch; a lane whose run met the rare case (a variate below
 // 2^-21, probability about 2^-21 each) redoes its run exactly after a
@@ -190,6 +182,15 @@ __device__ __forceinline__ void shared_run_fast(typename Word<DT>::type* mine, u
   }
 }
 
+// `ntiles` consecutive tiles of 32*c elements, the first at element `first`
+// of `out` (16-byte aligned).  Lane l produces elements [l*c, (l+1)*c) of each
+// tile with c steps of chain g, writes them to one of the warp's `nbuf` tile
+// buffers in shared memory, and lane 0 hands the tile to the bulk-copy engine.
+// `issued` counts the warp's committed bulk groups: before a buffer is reused,
+// lane 0 waits until the copy that last read it is done.  Between tiles the
+// chain jumps with one product by `jump` (2^(53*31c) forward, 2^(53*33c) for
+// the backward Montgomery chain, whose state is the last element of a run);
+// `jump_q` is its precomputed quotient for mulmod_pre.
 template <int DT, int STEP, int CONV, int CDEPTH = 0>
 __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__ out,
                                            uint64_t first, uint64_t ntiles, uint32_t c_rt,
@@ -234,9 +235,7 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
 // the other chain's work.  Stores to mine[i] and mine[h+1+i] keep lane
 // stride c (odd), so they stay bank-conflict free.  Between tiles chain a
 // jumps by 32c-h-1 steps and chain b by 31c+h+1.  Forward steps only.
-// Two interleaved chains of the branch-free shared-quotient step over a run
-// of c = 2h+1 elements (chain a: the first h+1, chain b: the last h); a lane
-// that left the fast path redoes its run with one exact chain.
+
 // Every third step of chain a (compile-time depths) converts on the FP64 pipe
 // (int->double and one round-to-nearest multiply, the definition itself)
 // instead of the integer rounding: the FP64 pipe is otherwise idle here, and
@@ -248,6 +247,9 @@ __device__ __forceinline__ uint64_t fp64_conv_step(uint64_t& z) {
   z = shared_advance(z);
   return bits;
 }
+
+// The two interleaved chains of the branch-free shared-quotient step over one
+// run; a lane that left the fast path redoes its run with one exact chain.
 template <int DT, int CDEPTH>
 __device__ __forceinline__ void shared_run_fast2(typename Word<DT>::type* mine, uint32_t c,
                                                  uint64_t& za, uint64_t& zb) {
