@@ -134,6 +134,25 @@ def test_4096_stream_batch_in_a_graph(R, oracle_mod):
     assert info["bytes"] == total and info["elems"] == int(sum(int(c) for c in counts))
     b.graph_launch()
     torch.cuda.synchronize()
+    _check_workload(starts, counts, dtypes, outs, oracle_mod)
+    # the benchmark's launch: the plan tuning measured on this workload, and the
+    # shape it has picked on GB300
+    from paper_1206_1187_gb300 import autotune
+    best = autotune.tune_batch(workload=(starts, counts, dtypes, outs),
+                               tag="batched-4096-seed7")["best"]
+    for tune in (best, dict(step="shared", conv="int", depth=31, block=896, unit=64, chains=2,
+                            buffers=1)):
+        for o in outs:
+            o.zero_()
+        b2 = R.Batch(starts, counts, dtypes, outs=outs, tune=tune)
+        b2.graph_launch()
+        torch.cuda.synchronize()
+        _check_workload(starts, counts, dtypes, outs, oracle_mod)
+        b2.close()
+
+
+def _check_workload(starts, counts, dtypes, outs, oracle_mod):
+    import torch
     rnd = np.random.default_rng(8)
     for s in range(len(starts)):
         n, d, a = int(counts[s]), dtypes[s], int(starts[s])

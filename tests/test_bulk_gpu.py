@@ -257,3 +257,12 @@ def test_two_gib_single_stream_is_thread_count_invariant(R, oracle_mod):
                                                              chains=chains))
         assert torch.equal(out.view(torch.int64), tb), (step, conv, chains)
         del out
+    # the benchmark's launch: the autotuner's pick on this size, and the shape it
+    # has picked on GB300 (depth 31, 896-thread blocks, one buffer per warp)
+    from paper_1206_1187_gb300 import autotune
+    best = autotune.tune_bulk("f64", n=n)["best"]
+    for tune in (best, dict(step="shared", conv="int", layout="tiled", depth=31, block=896,
+                            chains=2, buffers=1)):
+        out = R.generate_at(a, 0, n, "f64", tune=tune)
+        assert torch.equal(out.view(torch.int64), tb), tune
+        del out
