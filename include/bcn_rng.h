@@ -28,10 +28,16 @@
  *     library never frees them.  A pointer must be aligned to its element
  *     size, else RNG_EINVAL.
  *   - `cuda_stream` arguments are cudaStream_t handles passed as void*
- *     (NULL = the legacy default stream).  Generation calls are asynchronous
+ *     (NULL = the legacy default stream).  The calls that write device
+ *     memory (rng_generate, rng_generate_tuned, rng_generate_at,
+ *     rng40_generate_at, rng_fill_constant, rng_consume_mc) are asynchronous
  *     on that stream: they return after the launch, and the caller orders
- *     later use of the output on the same stream.  They allocate nothing
- *     and synchronise nothing, so they may be captured in a CUDA graph.
+ *     later use of the output on the same stream.  They allocate no device
+ *     memory and wait for nothing; once a kernel has been launched on the
+ *     device (so its shared-memory limit is set), later launches of it can
+ *     be captured into a CUDA graph (checked for rng_generate_at and
+ *     rng40_generate_at).  rng_generate_to_host is the synchronous
+ *     exception.
  *   - A launch failure reported by the CUDA runtime is RNG_ECUDA.
  *   - bcn_stream objects are not thread-safe; use one per host thread.
  */

@@ -266,3 +266,30 @@ def test_two_gib_single_stream_is_thread_count_invariant(R, oracle_mod):
         out = R.generate_at(a, 0, n, "f64", tune=tune)
         assert torch.equal(out.view(torch.int64), tb), tune
         del out
+
+
+def test_generation_calls_replay_in_a_cuda_graph(R, oracle_mod):
+    """rng_generate_at and rng40_generate_at captured into a CUDA graph (after
+    one eager call) and replayed write the oracle's variates."""
+    import torch
+    from m40_math import M40
+    n = 300007
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    out40 = torch.empty(n, dtype=torch.float32, device="cuda")
+    R.generate_at(M + 777, 5, n, "f64", out=out)
+    R.generate40_at(M40 + 777, 5, n, "f32", out=out40)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            R.generate_at(M + 777, 5, n, "f64", out=out, stream=s)
+            R.generate40_at(M40 + 777, 5, n, "f32", out=out40, stream=s)
+    out.zero_()
+    out40.zero_()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert_same(out, oracle_mod.generate(M + 777, 5, n, "f64"), "graph f64")
+    assert np.array_equal(out40.view(torch.int32).cpu().numpy(),
+                          oracle_mod.generate40(M40 + 777, 5, n, "f32").view(np.int32))
