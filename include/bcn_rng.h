@@ -197,7 +197,8 @@ rng_status rng_fill_constant(uint64_t n, rng_dtype dt, double value, void *out,
  * output must be aligned to its element size (else RNG_EINVAL).  The host
  * arrays are copied; the output arrays stay caller-owned and must outlive the
  * plan's launches.  tune (NULL = choose) sets step, conversion, tile depth,
- * block, grid and `unit` (tiles per work unit).  Creation allocates a small
+ * block, grid, chains, buffers and `unit` (tiles per work unit).  Creation
+ * allocates a small
  * device table (about 48 bytes per stream) and synchronises the device, so it
  * is not capturable; launches are. */
 typedef struct bcn_batch bcn_batch;
