@@ -236,12 +236,15 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
 // stride c (odd), so they stay bank-conflict free.  Between tiles chain a
 // jumps by 32c-h-1 steps and chain b by 31c+h+1.  Forward steps only.
 
-// Every third step of chain a (compile-time depths) converts on the FP64 pipe
-// (int->double and one round-to-nearest multiply, the definition itself)
-// instead of the integer rounding: the FP64 pipe is otherwise idle here, and
-// taking about a sixth of the conversions off the integer pipes measured 2%
-// faster (a third or a half of chain a's: no better).  Same bits either way.
-constexpr uint32_t kFp64ConvEvery = 3;
+// Every second iteration of the two-chain loop (compile-time depths) takes
+// one conversion on the FP64 pipe, alternating between chain a (iterations
+// 0, 4, 8, ...) and chain b (2, 6, 10, ...): int->double and one
+// round-to-nearest multiply, the definition itself, instead of the integer
+// rounding.  The FP64 pipe is otherwise idle here; a quarter of the
+// conversions spread evenly this way measured 3% faster than none (a sixth,
+// or uneven spacings such as every third step of each chain: 1-2%).  Same
+// bits either way.
+constexpr uint32_t kFp64ConvEvery = 4;
 __device__ __forceinline__ uint64_t fp64_conv_step(uint64_t& z) {
   const uint64_t bits = f64_bits_fp64(z);
   z = shared_advance(z);
@@ -261,7 +264,8 @@ __device__ __forceinline__ void shared_run_fast2(typename Word<DT>::type* mine, 
   for (uint32_t i = 0; i < h; ++i) {
     const uint64_t x = (CDEPTH > 0 && i % kFp64ConvEvery == 0) ? fp64_conv_step(za)
                                                                 : shared_step_f64_ptx(za, qmin);
-    const uint64_t y = shared_step_f64_ptx(zb, qmin);
+    const uint64_t y = (CDEPTH > 0 && i % kFp64ConvEvery == kFp64ConvEvery / 2)
+                           ? fp64_conv_step(zb) : shared_step_f64_ptx(zb, qmin);
     if constexpr (DT == DT_F64) {
       mine[i] = (W)x;
       mine[h + 1 + i] = (W)y;
