@@ -505,17 +505,24 @@ def run_ours(args):
     ms = shard.max_over_ranks(ms, device=dev)
     value = n * world / (ms / 1e3)
 
-    # the paper's Constant kernel: same tiled store path, no generation
+    # the paper's Constant kernel: same tiled store path, no generation; the
+    # ceiling is its best over a few tile shapes
     fills = max(min(args.steps, 200), 3)
-    for _ in range(3):
-        rng.fill_constant(n, "f64", 0.5, out=out, stream=stream)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(fills):
-        rng.fill_constant(n, "f64", 0.5, out=out, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_fill = e0.elapsed_time(e1) / fills
+    ms_fill, fill_shape = None, None
+    for shape in (dict(depth=31, block=896, buffers=1), dict(depth=15, block=256, buffers=2),
+                  dict(depth=31, block=512, buffers=1), dict(depth=15, block=512, buffers=2)):
+        ftune = rng.make_tune(layout="tiled", **shape)
+        for _ in range(3):
+            rng.fill_constant(n, "f64", 0.5, out=out, tune=ftune, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(fills):
+            rng.fill_constant(n, "f64", 0.5, out=out, tune=ftune, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_fill = e0.elapsed_time(e1) / fills
+        if ms_fill is None or t_fill < ms_fill:
+            ms_fill, fill_shape = t_fill, shape
 
     # end to end through the public API into pinned host memory: the library
     # generates chunks into device staging buffers and copies each to the host
@@ -582,7 +589,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "n": n, "seed": SEED, "tune": tune,
                        "l2": "each step writes 2 GiB (> 126 MB L2); no flush needed"},
             "roofline": roofline,
-            "write_ceiling": {"kernel": "constant fill, same tiled store path (Sec. 3.2)",
+            "write_ceiling": {"kernel": "constant fill, same tiled store path (Sec. 3.2), "
+                                        "best of four tile shapes",
+                              "shape": fill_shape,
                               "gbs": fill_gbs, "frac_of_peak": fill_gbs / peaks["hbm_gbs"],
                               "generation_frac_of_ceiling": achieved / fill_gbs},
             "e2e": e2e,

@@ -102,8 +102,11 @@ typedef enum {
   RNG_SKIP_SQMUL = 2   /* binary square-and-multiply                   */
 } rng_skip_method;
 
-/* Launch tuning.  Zero in any field means "choose".  Results never depend on
- * these fields; only speed does. */
+/* Launch tuning.  Zero in any field means "choose": the tuning installed by
+ * rng_set_auto_tune for the output type if any, else the shape measured best
+ * on GB300 (tiles 31 deep, 896-thread blocks, two chains per lane, one tile
+ * buffer per warp; batch plans also 64-tile work units).  Results never
+ * depend on these fields; only speed does. */
 typedef struct {
   uint32_t step;    /* rng_step                                              */
   uint32_t conv;    /* rng_conv                                              */

@@ -190,9 +190,12 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   if (!t.step) t.step = d.step ? d.step : ST_SHARED;
   if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
   if (!t.skip) t.skip = SK_TABLE;
-  if (!t.depth) t.depth = 15;
-  if (!t.block) t.block = 256;
-  if (!t.unit) t.unit = 16;  // tiles per work unit
+  // zero fields: the plan shape the autotuner picks on GB300 for the batched
+  // workload (4096 streams of 10^3..10^7 variates)
+  if (!t.depth) t.depth = 31;
+  if (!t.block) t.block = 896;
+  if (!t.unit) t.unit = 64;  // tiles per work unit
+  if (!t.buffers) t.buffers = 1;
   t.buffers = batch_buffers(t);
   t.layout = RNG_LAYOUT_TILED;
   t.chains = batch_chains(t);

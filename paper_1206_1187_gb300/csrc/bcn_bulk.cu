@@ -193,6 +193,12 @@ static uint64_t tile_count(uint64_t n, uint64_t head, uint32_t depth) {
   return n > head ? (n - head) / (32ull * depth) : 0;
 }
 
+// The launch shape for fields left zero when no tuning is installed: the
+// shape the autotuner picks on GB300 for 2^28 variates of every output type
+// (FP64 752, FP32 719, raw states 820 G/s there, against 573, 628 and 704
+// with 15-deep tiles in 256-thread blocks).
+constexpr uint32_t kDefDepth = 31, kDefBlock = 896, kDefChains = 2, kDefBuffers = 1;
+
 rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* out,
                         bool constant) {
   rng_tune t = {};
@@ -235,15 +241,16 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   if (st != RNG_OK) return st;
   if (t.chains > 2) return set_error(RNG_EINVAL, "tune.chains %u must be 0, 1 or 2", t.chains);
   L.chains = 1;
+  const uint32_t want_chains = t.chains ? t.chains : kDefChains;
   if (L.layout == RNG_LAYOUT_TILED && (L.step == ST_SHARED || L.step == ST_BARRETT) &&
-      t.chains == 2 && (t.depth ? t.depth : 15) >= 3)
+      want_chains == 2 && (t.depth ? t.depth : kDefDepth) >= 3)
     L.chains = 2;
-  const uint32_t depth0 = L.layout == RNG_LAYOUT_TILED ? (t.depth ? t.depth : 15) : 0;
+  const uint32_t depth0 = L.layout == RNG_LAYOUT_TILED ? (t.depth ? t.depth : kDefDepth) : 0;
   const void* fn = pick_kernel(L.layout, dt, L.step, L.conv, (int)L.chains, depth0);
   if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   if (L.layout == RNG_LAYOUT_TILED) {
-    L.depth = t.depth ? t.depth : 15;
-    L.block = t.block ? t.block : 256;
+    L.depth = t.depth ? t.depth : kDefDepth;
+    L.block = t.block ? t.block : kDefBlock;
     if (L.depth % 2 == 0 || L.depth > kMaxDepth)
       return set_error(RNG_EINVAL, "tune.depth %u must be odd and at most %u", L.depth,
                        kMaxDepth);
@@ -251,11 +258,14 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
       return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024",
                        L.block);
     if (t.buffers > 2) return set_error(RNG_EINVAL, "tune.buffers %u must be 0, 1 or 2", t.buffers);
-    L.buffers = t.buffers ? t.buffers : 2;
-    L.smem_bytes = (size_t)(L.block / 32) * L.buffers * 32 * L.depth * dtype_size(dt);
-    while (!t.block && L.smem_bytes > di.smem_optin && L.block > 32) {  // chosen block: shrink
-      L.block /= 2;
-      L.smem_bytes /= 2;
+    L.buffers = t.buffers ? t.buffers : kDefBuffers;
+    const size_t warp_bytes = (size_t)L.buffers * 32 * L.depth * dtype_size(dt);
+    L.smem_bytes = (size_t)(L.block / 32) * warp_bytes;
+    // a chosen block that does not fit shrinks, four warps at a time while it
+    // can (whole warps for each of the SM's four schedulers), then by halves
+    while (!t.block && L.smem_bytes > di.smem_optin && L.block > 32) {
+      L.block = L.block > 128 ? L.block - 128 : L.block / 2;
+      L.smem_bytes = (size_t)(L.block / 32) * warp_bytes;
     }
     if (L.smem_bytes > di.smem_optin)
       return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
