@@ -201,10 +201,17 @@ def cpu_baseline(seconds: float, dtype: str = "f64"):
     t = time.perf_counter()
     oracle.generate_mt(SEED, 0, sample, dtype, threads=cores)
     dt = time.perf_counter() - t
+    # one core as well (the paper's serial baseline is a single thread)
+    one = 1 << 22
+    t = time.perf_counter()
+    oracle.generate(SEED, 0, one, dtype)
+    dt1 = time.perf_counter() - t
     return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {sample} FP64 variates of the workload's stream "
                       f"(a = 3^33+12345), split over {cores} threads by skip-ahead; "
-                      f"{dt:.2f} s wall"}
+                      f"{dt:.2f} s wall",
+            "single_thread": {"value": one / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"first {one} variates, one thread"}}
 
 
 def measure_batched(rng, stream, achieved_gbs: float, steps: int):
