@@ -293,3 +293,23 @@ def test_generation_calls_replay_in_a_cuda_graph(R, oracle_mod):
     assert_same(out, oracle_mod.generate(M + 777, 5, n, "f64"), "graph f64")
     assert np.array_equal(out40.view(torch.int32).cpu().numpy(),
                           oracle_mod.generate40(M40 + 777, 5, n, "f32").view(np.int32))
+
+
+@pytest.mark.slow
+def test_full_size_fp32_and_states_sampled(R, oracle_mod):
+    """2^28 FP32 variates and 2^28 raw states of the bench's stream in the
+    default launch: first and last 4096 and 8192 random positions each."""
+    import torch
+    a, n = M + 12345, 1 << 28
+    rnd = np.random.default_rng(28)
+    idx = np.unique(np.concatenate([np.arange(4096), np.arange(n - 4096, n),
+                                    rnd.integers(0, n, size=8192)])).astype(np.int64)
+    for dtype in ("f32", "u64"):
+        out = R.generate_at(a, 0, n, dtype)
+        torch.cuda.synchronize()
+        got = out[torch.from_numpy(idx).cuda()]
+        want = oracle_mod.at(a, idx.astype(np.uint64), dtype)
+        iv = torch.int32 if dtype == "f32" else torch.int64
+        assert np.array_equal(got.view(iv).cpu().numpy(),
+                              want.view(np.int32 if dtype == "f32" else np.int64)), dtype
+        del out, got

@@ -124,6 +124,12 @@ def test_full_size_sampled(R, oracle_mod):
     want = _bits(oracle_mod.at40(a, idx.astype(np.uint64), "f64"))
     assert np.array_equal(got, want)
     del out
+    for dtype in ("f32", "u64"):
+        out = R.generate40_at(a, 0, n, dtype)
+        torch.cuda.synchronize()
+        got = _dev_bits(out[torch.from_numpy(idx).cuda()])
+        assert np.array_equal(got, _bits(oracle_mod.at40(a, idx.astype(np.uint64), dtype))), dtype
+        del out
 
 
 def test_undecided_quotients(R, oracle_mod):
