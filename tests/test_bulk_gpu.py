@@ -307,9 +307,9 @@ def test_full_size_fp32_and_states_sampled(R, oracle_mod):
     for dtype in ("f32", "u64"):
         out = R.generate_at(a, 0, n, dtype)
         torch.cuda.synchronize()
-        got = out[torch.from_numpy(idx).cuda()]
-        want = oracle_mod.at(a, idx.astype(np.uint64), dtype)
         iv = torch.int32 if dtype == "f32" else torch.int64
-        assert np.array_equal(got.view(iv).cpu().numpy(),
+        got = out.view(iv)[torch.from_numpy(idx).cuda()]  # index the integer view
+        want = oracle_mod.at(a, idx.astype(np.uint64), dtype)
+        assert np.array_equal(got.cpu().numpy(),
                               want.view(np.int32 if dtype == "f32" else np.int64)), dtype
         del out, got

@@ -127,7 +127,8 @@ def test_full_size_sampled(R, oracle_mod):
     for dtype in ("f32", "u64"):
         out = R.generate40_at(a, 0, n, dtype)
         torch.cuda.synchronize()
-        got = _dev_bits(out[torch.from_numpy(idx).cuda()])
+        iv = torch.int32 if dtype == "f32" else torch.int64
+        got = out.view(iv)[torch.from_numpy(idx).cuda()].cpu().numpy()  # integer view
         assert np.array_equal(got, _bits(oracle_mod.at40(a, idx.astype(np.uint64), dtype))), dtype
         del out
 
