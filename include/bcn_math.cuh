@@ -382,7 +382,67 @@ __device__ __forceinline__ uint64_t shared_step_f64_ptx(uint64_t& z, uint32_t& q
   qmin = qm_out;
   return ((uint64_t)b1 << 32) | b0;
 }
+// The same step producing the FP32 variate directly: the FP32 variate is
+// the FP64 one rounded toward zero, i.e. the top 24 bits of its rounded
+// significand, and ((G + 1) >> 1) >> 29 = (G + 1) >> 30, so the rounding add
+// is the FP64 path's and the final shift is by 30 with the FP32 exponent
+// (biased 126 - lz, that is 137 - c with c the leading-zero count of q's top
+// word) pre-shifted into the high word.  Same state advance.
+__device__ __forceinline__ uint32_t shared_step_f32_ptx(uint64_t& z, uint32_t& qmin) {
+  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
+  uint32_t r0, r1, b0, qm_out;
+  asm("{\n\t"
+      ".reg .u32 a0, a1, k0, k1, m0, m1, qi, zr;\n\t"
+      ".reg .u32 h0, w1, w2, w3, t1h, q0, q1, ml, mh, zh, c, s, lh, gh, gl, ew, x0, x1;\n\t"
+      ".reg .u64 t1, t2, qm, h0w, t1hw;\n\t"
+      ".reg .pred neg;\n\t"
+      "mov.u32 a0, %4;\n\t"
+      "mov.u32 a1, %5;\n\t"
+      "mov.u32 k0, %6;\n\t"
+      "mov.u32 k1, %7;\n\t"
+      "mov.u32 m0, %8;\n\t"
+      "mov.u32 m1, %9;\n\t"
+      "mov.u32 qi, %10;\n\t"
+      "mov.u32 zr, 0;\n\t"
+      "mul.hi.u32 h0, a0, k0;\n\t"
+      "cvt.u64.u32 h0w, h0;\n\t"
+      "mad.wide.u32 t1, a0, k1, h0w;\n\t"
+      "mad.wide.u32 t1, a1, k0, t1;\n\t"
+      "mov.b64 {w1, t1h}, t1;\n\t"
+      "cvt.u64.u32 t1hw, t1h;\n\t"
+      "mad.wide.u32 t2, a1, k1, t1hw;\n\t"
+      "mov.b64 {w2, w3}, t2;\n\t"
+      "shf.r.clamp.b32 q0, w1, w2, 21;\n\t"
+      "shf.r.clamp.b32 q1, w2, w3, 21;\n\t"
+      "mul.wide.u32 qm, q0, m0;\n\t"
+      "mov.b64 {ml, mh}, qm;\n\t"
+      "mad.lo.u32 mh, q0, m1, mh;\n\t"
+      "mad.lo.u32 mh, q1, m0, mh;\n\t"
+      "shl.b32 zh, a0, 21;\n\t"
+      "sub.cc.u32 %0, zr, ml;\n\t"
+      "subc.u32 %1, zh, mh;\n\t"
+      "setp.lt.s32 neg, %1, 0;\n\t"
+      "@neg add.cc.u32 %0, %0, m0;\n\t"
+      "@neg addc.u32 %1, %1, m1;\n\t"
+      "min.u32 %3, qi, q1;\n\t"
+      "clz.b32 c, q1;\n\t"
+      "sub.u32 s, c, 10;\n\t"
+      "shl.b32 lh, w1, 11;\n\t"
+      "shf.l.clamp.b32 gh, q0, q1, s;\n\t"
+      "shf.l.clamp.b32 gl, lh, q0, s;\n\t"
+      "mad.lo.u32 ew, c, 0xFFE00000, 0x11000000;\n\t"
+      "add.cc.u32 x0, gl, 1;\n\t"
+      "addc.u32 x1, gh, ew;\n\t"
+      "shf.r.clamp.b32 %2, x0, x1, 30;\n\t"
+      "}"
+      : "=r"(r0), "=r"(r1), "=r"(b0), "=r"(qm_out)
+      : "r"(z0), "r"(z1), "r"(kK0), "r"(kK1), "r"(kM0), "r"(kM1), "r"(qmin));
+  z = ((uint64_t)r1 << 32) | r0;
+  qmin = qm_out;
+  return b0;
+}
 static_assert((1032u << 21) == 0x81000000u, "exponent constant of the PTX step");
+static_assert((136u << 21) == 0x11000000u, "exponent constant of the FP32 PTX step");
 
 // The state advance of shared_step_f64 alone (raw-state output).
 __device__ __forceinline__ uint64_t shared_advance(uint64_t z) {

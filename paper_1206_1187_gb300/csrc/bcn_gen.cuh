@@ -241,14 +241,30 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
 // 0, 4, 8, ...) and chain b (2, 6, 10, ...): int->double and one
 // round-to-nearest multiply, the definition itself, instead of the integer
 // rounding.  The FP64 pipe is otherwise idle here; a quarter of the
-// conversions spread evenly this way measured 3% faster than none (a sixth,
-// or uneven spacings such as every third step of each chain: 1-2%).  Same
-// bits either way.
-constexpr uint32_t kFp64ConvEvery = 4;
+// conversions spread evenly this way measured 3% faster than none for FP64
+// output (a sixth, or uneven spacings such as every third step of each chain:
+// 1-2%).  FP32 output, whose integer conversion is cheaper, does best with
+// one conversion in six (every third iteration).  Same bits either way.
+template <int DT>
+constexpr uint32_t kFp64ConvEvery = DT == DT_F32 ? 6 : 4;
 __device__ __forceinline__ uint64_t fp64_conv_step(uint64_t& z) {
   const uint64_t bits = f64_bits_fp64(z);
   z = shared_advance(z);
   return bits;
+}
+
+// One fast step's output word: FP64 bits, or the FP32 bits made directly by
+// the FP32 form of the step; `fp64` takes the conversion on the FP64 pipe.
+template <int DT>
+__device__ __forceinline__ typename Word<DT>::type fast_word(uint64_t& z, uint32_t& qmin,
+                                                             bool fp64) {
+  if (fp64) {
+    const uint64_t bits = fp64_conv_step(z);
+    if constexpr (DT == DT_F64) return bits;
+    else return f32_bits_from_f64_bits(bits);
+  }
+  if constexpr (DT == DT_F64) return shared_step_f64_ptx(z, qmin);
+  else return shared_step_f32_ptx(z, qmin);
 }
 
 // The two interleaved chains of the branch-free shared-quotient step over one
@@ -262,23 +278,11 @@ __device__ __forceinline__ void shared_run_fast2(typename Word<DT>::type* mine, 
   const uint32_t h = CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : c / 2;
 #pragma unroll
   for (uint32_t i = 0; i < h; ++i) {
-    const uint64_t x = (CDEPTH > 0 && i % kFp64ConvEvery == 0) ? fp64_conv_step(za)
-                                                                : shared_step_f64_ptx(za, qmin);
-    const uint64_t y = (CDEPTH > 0 && i % kFp64ConvEvery == kFp64ConvEvery / 2)
-                           ? fp64_conv_step(zb) : shared_step_f64_ptx(zb, qmin);
-    if constexpr (DT == DT_F64) {
-      mine[i] = (W)x;
-      mine[h + 1 + i] = (W)y;
-    } else {
-      mine[i] = (W)f32_bits_from_f64_bits(x);
-      mine[h + 1 + i] = (W)f32_bits_from_f64_bits(y);
-    }
+    constexpr uint32_t K = kFp64ConvEvery<DT>;
+    mine[i] = fast_word<DT>(za, qmin, CDEPTH > 0 && i % K == 0);
+    mine[h + 1 + i] = fast_word<DT>(zb, qmin, CDEPTH > 0 && i % K == K / 2);
   }
-  {
-    const uint64_t x = shared_step_f64_ptx(za, qmin);
-    if constexpr (DT == DT_F64) mine[h] = (W)x;
-    else mine[h] = (W)f32_bits_from_f64_bits(x);
-  }
+  mine[h] = fast_word<DT>(za, qmin, false);
   const bool rare = qmin == 0;
   if (__any_sync(0xffffffffu, rare)) {
     if (rare) {

@@ -8,6 +8,7 @@ random, edge and adversarial states, and the bounds its correctness argument
 uses are checked directly.  The GPU parity tests then check the kernels
 themselves against the oracle.
 """
+import math
 import random
 import struct
 from fractions import Fraction
@@ -301,3 +302,68 @@ def test_precomputed_quotient_mulmod():
             if r >= M:
                 r -= M
             assert r == (z * j) % M
+
+
+def f32_step_model(z):
+    """The FP32-output step: the FP64 path's rounding add with the FP32
+    exponent (136 - c) pre-shifted into the high word, then >> 30."""
+    z0, z1 = z & MASK32, z >> 32
+    t0 = z0 * K0
+    t1 = z0 * K1 + (t0 >> 32)
+    t1 = z1 * K0 + t1
+    t2 = z1 * K1 + (t1 >> 32)
+    w1, w2, w3 = t1 & MASK32, t2 & MASK32, t2 >> 32
+    q0, q1 = funnel_r(w1, w2, 21), funnel_r(w2, w3, 21)
+    if q1 == 0:
+        return None
+    c = clz32(q1)
+    s = c - 10
+    lh = (w1 << 11) & MASK32
+    g_hi, g_lo = funnel_l(q0, q1, s), funnel_l(lh, q0, s)
+    ew = (0x11000000 - c * 0x200000) & MASK32
+    x0 = g_lo + 1
+    x1 = (g_hi + ew + (x0 >> 32)) & MASK32
+    x0 &= MASK32
+    return (((x1 << 32) | x0) >> 30) & MASK32
+
+
+def rz_f32_bits(z: int) -> int:
+    """Bits of the FP32 variate: RN(z * r3i) as a double, then toward zero."""
+    import numpy as np
+    v = float(Fraction(z) * Fraction(R3I))
+    f = np.float32(v)
+    if float(f) > v:
+        f = np.nextafter(f, np.float32(0.0))
+    return int(np.array([f], dtype=np.float32).view(np.uint32)[0])
+
+
+def test_f32_step_model_is_the_truncated_double():
+    n_fast = 0
+    for z in states(60000, seed=12):
+        bits = f32_step_model(z)
+        if bits is None:
+            continue
+        n_fast += 1
+        b64 = rn_bits(z)
+        assert bits == ((b64 >> 29) - (896 << 23)) & MASK32, z  # the FP64 path's truncation
+        assert bits == rz_f32_bits(z), z
+    assert n_fast > 50000
+    # states whose double lands on a float value (low 29 significand bits zero),
+    # among them those rounded up across the float boundary: the rounding
+    # carry must reach the float bits.  For random floats f, the states next to
+    # f / r3i give products within a few ulps of f.
+    rnd = random.Random(13)
+    hits = 0
+    for _ in range(20000):
+        f = struct.unpack("<f", struct.pack("<f", rnd.uniform(2.0 ** -20, 1.0)))[0]
+        zc = int(f / R3I)
+        for z in range(zc - 3, zc + 4):
+            if not 0 < z < M:
+                continue
+            b64 = f64_bits(float(z) * R3I)  # one round-to-nearest multiply
+            if (b64 & (2 ** 29 - 1)) == 0:
+                bits = f32_step_model(z)
+                if bits is not None:
+                    hits += 1
+                    assert bits == ((b64 >> 29) - (896 << 23)) & MASK32, z
+    assert hits > 1000
