@@ -313,3 +313,38 @@ def test_full_size_fp32_and_states_sampled(R, oracle_mod):
         assert np.array_equal(got.cpu().numpy(),
                               want.view(np.int32 if dtype == "f32" else np.int64)), dtype
         del out, got
+
+
+def test_host_threads_generate_concurrently(R, oracle_mod):
+    """Four host threads, each with its own stream object and CUDA stream,
+    generate at once (the library's shared state -- installed tunings, device
+    properties, kernel attributes -- is locked); every result is exact."""
+    import threading
+    import torch
+    results, errors = {}, []
+
+    def work(k):
+        try:
+            cs = torch.cuda.Stream()
+            s = R.Stream(M + 1000 * (k + 1))
+            s.skip(7 * k)
+            outs = []
+            for j in range(5):
+                outs.append(s.generate(200003 + j, ("f64", "f32", "u64")[j % 3], stream=cs))
+            cs.synchronize()
+            results[k] = outs
+        except Exception as ex:  # reported below
+            errors.append(repr(ex))
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for k in range(4):
+        a, pos = M + 1000 * (k + 1), 7 * k
+        for j, out in enumerate(results[k]):
+            n, dt = 200003 + j, ("f64", "f32", "u64")[j % 3]
+            assert_same(out, oracle_mod.generate(a, pos, n, dt), f"thread {k} call {j}")
+            pos += n
