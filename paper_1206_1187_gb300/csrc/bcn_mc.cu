@@ -96,6 +96,32 @@ __device__ __forceinline__ Terms variate_terms_fp64(uint64_t bits) {
   return t;
 }
 
+// (a1:a0) += v * 2^105 for a variate v >= 2^-21 (the branch-free path, where
+// every variate of a kept chunk is at least 2^-21): its biased exponent e is
+// in [1002, 1022], so v * 2^105 = mant << (32 + j) with j = e - 1002 in
+// [0, 20], and the image's low 32-bit word is zero.  Three shifts make the
+// three upper words and one carry chain adds them.
+__device__ __forceinline__ void add_variate_fast(uint64_t& a0, uint64_t& a1, uint64_t bits) {
+  const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
+  const uint32_t j = (hi >> 20) - 1002u;
+  const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+  asm("{\n\t"
+      ".reg .u32 A0, A1, A2, A3, w1, w2, w3;\n\t"
+      "mov.b64 {A0, A1}, %0;\n\t"
+      "mov.b64 {A2, A3}, %1;\n\t"
+      "shl.b32 w1, %2, %4;\n\t"
+      "shf.l.clamp.b32 w2, %2, %3, %4;\n\t"
+      "shf.l.clamp.b32 w3, %3, 0, %4;\n\t"
+      "add.cc.u32 A1, A1, w1;\n\t"
+      "addc.cc.u32 A2, A2, w2;\n\t"
+      "addc.u32 A3, A3, w3;\n\t"
+      "mov.b64 %0, {A0, A1};\n\t"
+      "mov.b64 %1, {A2, A3};\n\t"
+      "}"
+      : "+l"(a0), "+l"(a1)
+      : "r"(lo), "r"(mh), "r"(j));
+}
+
 // Round (w2:w1:w0) * 2^-scale to the nearest double, ties to even.
 __device__ double round_words(uint64_t w0, uint64_t w1, uint64_t w2, int scale) {
   int top;
@@ -169,8 +195,13 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
       const uint64_t by = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
       const Terms x = FP64SQ ? variate_terms_fp64(bx) : variate_terms(bx);
       const Terms y = FP64SQ ? variate_terms_fp64(by) : variate_terms(by);
-      add128(a0, a1, x.v0, x.v1);
-      add128(a0, a1, y.v0, y.v1);
+      if (exact) {
+        add128(a0, a1, x.v0, x.v1);
+        add128(a0, a1, y.v0, y.v1);
+      } else {  // every variate of a kept chunk is at least 2^-21
+        add_variate_fast(a0, a1, bx);
+        add_variate_fast(a0, a1, by);
+      }
       uint64_t r0 = x.q0, r1 = x.q1;
       add128(r0, r1, y.q0, y.q1);
       hits += ((r1 < lim1) | ((r1 == lim1) & (r0 <= lim0))) ? 1u : 0u;

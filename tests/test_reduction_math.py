@@ -367,3 +367,25 @@ def test_f32_step_model_is_the_truncated_double():
                     hits += 1
                     assert bits == ((b64 >> 29) - (896 << 23)) & MASK32, z
     assert hits > 1000
+
+
+def test_fused_fast_variate_image():
+    """The fused kernel's fast accumulation of v * 2^105 for v >= 2^-21: the
+    three upper 32-bit words of mant << (32 + j), j = e - 1002, from three
+    shifts (funnel shifts clamp a zero shift to the high operand)."""
+    rnd = random.Random(14)
+    vals = [float(Fraction(z) * Fraction(R3I)) for z in states(20000, seed=15)]
+    vals += [2.0 ** -21, math.nextafter(1.0, 0.0), 0.5, math.nextafter(0.5, 0.0)]
+    for v in vals:
+        if v < 2.0 ** -21:
+            continue
+        b = f64_bits(v)
+        hi, lo = b >> 32, b & MASK32
+        j = (hi >> 20) - 1002
+        assert 0 <= j <= 20
+        mh = (hi & 0xFFFFF) | 0x100000
+        w1 = (lo << j) & MASK32
+        w2 = funnel_l(lo, mh, j)
+        w3 = funnel_l(mh, 0, j)
+        image = (w3 << 96) | (w2 << 64) | (w1 << 32)
+        assert Fraction(image, 2 ** 105) == Fraction(v), v
