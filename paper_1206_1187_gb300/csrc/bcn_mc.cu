@@ -96,6 +96,22 @@ __device__ __forceinline__ Terms variate_terms_fp64(uint64_t bits) {
   return t;
 }
 
+// hits += [ (r1:r0) <= (lim1:lim0) ]: the borrow of (r1:r0) - (lim1:lim0) - 1
+// (one subtract-with-borrow chain instead of three 64-bit compares).
+__device__ __forceinline__ void count_hit(uint32_t& hits, uint64_t r0, uint64_t r1,
+                                          uint64_t lim0p1, uint64_t lim1) {
+  asm("{\n\t"
+      ".reg .u64 t0, t1;\n\t"
+      ".reg .u32 b;\n\t"
+      "sub.cc.u64 t0, %1, %2;\n\t"
+      "subc.cc.u64 t1, %3, %4;\n\t"
+      "subc.u32 b, 0, 0;\n\t"
+      "sub.u32 %0, %0, b;\n\t"
+      "}"
+      : "+r"(hits)
+      : "l"(r0), "l"(lim0p1), "l"(r1), "l"(lim1));
+}
+
 // (a1:a0) += v * 2^105 for a variate v >= 2^-21 (the branch-free path, where
 // every variate of a kept chunk is at least 2^-21): its biased exponent e is
 // in [1002, 1022], so v * 2^105 = mant << (32 + j) with j = e - 1002 in
@@ -204,7 +220,7 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
       }
       uint64_t r0 = x.q0, r1 = x.q1;
       add128(r0, r1, y.q0, y.q1);
-      hits += ((r1 < lim1) | ((r1 == lim1) & (r0 <= lim0))) ? 1u : 0u;
+      count_hit(hits, r0, r1, lim0 + 1, lim1);
       if (__builtin_expect(x.fast & y.fast, 1)) {
         add128(h0, h1, r0, r1);
       } else {
@@ -279,7 +295,7 @@ rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblock
   if (len / 2 > 0xFFFFFFFFull) return set_error(RNG_ERANGE, "len too large for 32-bit hit counts");
   rng_tune t = {};
   if (tune) t = *tune;
-  const uint32_t block = t.block ? t.block : 256;
+  const uint32_t block = t.block ? t.block : 128;  // measured: 128 and 256 within 0.5%
   if (block % 32 != 0 || block > 256)
     return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 256", block);
   const uint32_t skip = t.skip ? t.skip : SK_TABLE;
