@@ -296,6 +296,33 @@ def measure_fused(rng, stream, steps: int):
     return out
 
 
+def measure_other_outputs(rng, stream, peaks, steps: int):
+    """The same stream and size as the headline with FP32 variates and with raw
+    states, default launch: variates/s and bytes written per second."""
+    import torch
+    n = N_DEFAULT
+    res = {}
+    for dtype, tdt in (("f32", torch.float32), ("u64", torch.uint64)):
+        out = torch.empty(n, dtype=tdt, device="cuda")
+        for _ in range(3):
+            rng.generate_at(SEED, 0, n, dtype, out=out, stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            rng.generate_at(SEED, 0, n, dtype, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        gbs = out.element_size() * n / (ms / 1e3) / 1e9
+        res[dtype] = {"variates_per_s": n / (ms / 1e3), "GBps": gbs,
+                      "frac_of_hbm": gbs / peaks["hbm_gbs"], "ms_per_launch": ms,
+                      "launches": steps}
+        del out
+    return res
+
+
 def measure_m40(rng, stream, peaks, steps: int):
     """The larger-modulus variant (3^40, Sec. 1): 2^28 FP64 variates (2 GiB,
     larger than L2) from a = 3^40+12345 into device memory, default tuning."""
@@ -565,6 +592,10 @@ def run_ours(args):
     fused = None
     if not args.no_fused and rank == 0:
         fused = measure_fused(rng, stream, steps=3)
+    others = None
+    if rank == 0:
+        others = measure_other_outputs(rng, stream, load_peaks(),
+                                       steps=max(min(args.steps // 20, 50), 5))
     m40 = None
     if not args.no_m40 and rank == 0:
         m40 = measure_m40(rng, stream, load_peaks(), steps=max(min(args.steps // 20, 50), 5))
@@ -611,6 +642,8 @@ def run_ours(args):
             line["fused"] = fused
         if m40 is not None:
             line["modulus_3_40"] = m40
+        if others is not None:
+            line["other_outputs"] = others
         if serving is not None:
             line["serving"] = serving
         if tuned is not None:
