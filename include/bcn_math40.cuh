@@ -193,7 +193,7 @@ __device__ __forceinline__ uint64_t bits40(uint64_t q0, uint64_t q1) {
 // one is in the next window (the variate is at least 3^-40 > 2^-64), so the
 // digits come from q1 and q2, 53 places further down.  z1 is the state whose
 // quotient is q1.
-__device__ __noinline__ uint64_t bits40_small(uint64_t z1, uint64_t q1) {
+static __device__ __noinline__ uint64_t bits40_small(uint64_t z1, uint64_t q1) {
   const uint64_t q2 = quot40(rem40(z1, q1));
   const uint32_t t = (uint32_t)__clzll((long long)q1) - 11u;
   const uint64_t mant = (q1 << t) | (q2 >> (53u - t));

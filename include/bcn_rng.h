@@ -236,9 +236,12 @@ rng_status rng_batch_destroy(bcn_batch *b);
  * instead of a cudaMalloc'd plan, and it allocates no device or host memory.
  *   - At most 1024 streams per call; more is RNG_ERANGE.  The array (about
  *     49 KB) is held by every device that loads the library until exit.
+ *   - Zero tuning fields take a batch plan's shape (31-deep tiles,
+ *     896-thread blocks, one buffer per warp, 64-tile work units).
  *   - The first call on a device, with that device current, looks up the
- *     array's device address and sets the kernel's shared-memory limit; make
- *     that first call before any stream capture on the device.
+ *     array's device address, and the first call with each kernel shape
+ *     (step, conversion, chains, depth) sets that kernel's shared-memory
+ *     limit; make those calls before any stream capture on the device.
  *   - Every call rewrites the one shared table and clears its work counter:
  *     calls whose work overlaps on the GPU (on different streams, or from
  *     different host threads' streams) race and must be serialised by the
@@ -333,6 +336,12 @@ rng_status rng_server_submit(bcn_server *s, uint64_t start_index, uint64_t offse
                              rng_dtype dt, uint64_t *id);
 /* Withdraw a request that is still queued (RNG_EBUSY once admitted). */
 rng_status rng_server_cancel(bcn_server *s, uint64_t id);
+/* Request ids stay known while the request is queued, active or done; after
+ * its pool range is released (or a cancelled request leaves the queue) the
+ * server keeps its final state and times for the 65536 most recent such
+ * requests only, so its bookkeeping stays bounded.  An id no longer known is
+ * RNG_EINVAL in the calls below; reading or releasing a released request is
+ * RNG_EBUSY. */
 /* State and, once done, latency (submission or scheduled arrival to the
  * host seeing its last iteration complete, seconds; -1 before). */
 rng_status rng_server_status(bcn_server *s, uint64_t id, int *state, double *latency_s);
@@ -351,8 +360,11 @@ rng_status rng_server_stats_get(bcn_server *s, rng_server_stats *out);
 /* Replay a request trace in real time: request i is submitted at
  * arrival_s[i] seconds after the call starts (open loop), then every request
  * is awaited (RNG_ETIMEOUT after timeout_s).  latency_s[i] receives the time
- * from request i's scheduled arrival to its completion; *wall_s (nullable) the
- * time from the start to the last completion.  With release_after_s < 0 the
+ * from request i's scheduled arrival to its completion, written by the
+ * scheduler as the request completes (any trace length); *wall_s (nullable)
+ * the time from the start to the last completion.  On an error return the
+ * trace's requests already submitted keep running, and entries of latency_s
+ * for those not yet complete are left as they were.  With release_after_s < 0 the
  * results are never freed, so a trace whose outputs exceed the pool is
  * RNG_EINVAL before anything is submitted. */
 rng_status rng_server_run_trace(bcn_server *s, uint32_t n, const double *arrival_s,

@@ -161,8 +161,7 @@ rng_status rng_generate_to_host(bcn_stream* s, uint64_t n, rng_dtype dt, void* h
   if (!nbuf) nbuf = 4;
   if (nbuf > 8) return set_error(RNG_EINVAL, "at most 8 staging buffers");
   const size_t esz = dtype_size((int)dt);
-  chunk_bytes = (chunk_bytes + 255) / 256 * 256;
-  if (chunk_bytes < esz * 32) chunk_bytes = 256;
+  chunk_bytes = (chunk_bytes + 255) / 256 * 256;  // whole 256-byte blocks, >= 32 elements
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -190,6 +189,12 @@ rng_status rng_generate_to_host(bcn_stream* s, uint64_t n, rng_dtype dt, void* h
   if (start) cudaEventDestroy(start);
   if (e != cudaSuccess) return cuda_error(e, "ordering host transfer");
   const uint64_t per = chunk_bytes / esz;
+  // on an error part way, the copies already queued still write into the
+  // caller's buffer: wait for them before returning
+  auto drain = [s, nbuf](rng_status r) {
+    for (uint32_t i = 0; i < nbuf; ++i) cudaStreamSynchronize(s->stage_cs[i]);
+    return r;
+  };
   BulkLaunch L;
   bool resolved = false;
   uint64_t done = 0;
@@ -198,14 +203,14 @@ rng_status rng_generate_to_host(bcn_stream* s, uint64_t n, rng_dtype dt, void* h
     const uint32_t b = (uint32_t)(k % nbuf);
     if (!resolved || cnt != per) {
       st = resolve_bulk(cnt, (int)dt, nullptr, &L, false);
-      if (st != RNG_OK) return st;
+      if (st != RNG_OK) return drain(st);
       resolved = cnt == per;
     }
     st = launch_bulk(L, s->seed, s->count + done, cnt, s->stage[b], 0, s->stage_cs[b]);
-    if (st != RNG_OK) return st;
+    if (st != RNG_OK) return drain(st);
     e = cudaMemcpyAsync(static_cast<unsigned char*>(host_out) + done * esz, s->stage[b],
                         cnt * esz, cudaMemcpyDeviceToHost, s->stage_cs[b]);
-    if (e != cudaSuccess) return cuda_error(e, "device-to-host copy");
+    if (e != cudaSuccess) return drain(cuda_error(e, "device-to-host copy"));
     done += cnt;
   }
   for (uint32_t i = 0; i < nbuf; ++i) {

@@ -187,8 +187,8 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   rng_tune t = {};
   if (tune) t = *tune;
   const rng_tune d = auto_defaults(RNG_F64);
-  if (!t.step) t.step = d.step ? d.step : ST_SHARED;
-  if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
+  if (!t.step) t.step = d.step ? d.step : (uint32_t)ST_SHARED;
+  if (!t.conv) t.conv = d.conv ? d.conv : (uint32_t)CV_INT;
   if (!t.skip) t.skip = SK_TABLE;
   // zero fields: the plan shape the autotuner picks on GB300 for the batched
   // workload (4096 streams of 10^3..10^7 variates)
@@ -389,8 +389,12 @@ static_assert(kNoallocDescBytes % 16 == 0 && kNoallocPrefixBytes % 8 == 0, "layo
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 constexpr int kNoallocMaxDevices = 64;
+constexpr int kNoallocMaxKernels = 32;  // more than the batched kernel's instantiations
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_dev[kNoallocMaxDevices];  // device address of the array, per device
+// per device, the kernels whose shared-memory limit has been raised (a fixed
+// table: recording them allocates nothing either)
+static const void* g_noalloc_ready[kNoallocMaxDevices][kNoallocMaxKernels];
 // host staging for the table (static: building it allocates nothing either)
 static BatchDesc g_noalloc_desc[kNoallocMaxStreams];
 static uint64_t g_noalloc_prefix[kNoallocMaxStreams + 1];
@@ -410,12 +414,14 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   rng_tune t = {};
   if (tune) t = *tune;
   const rng_tune d = auto_defaults(RNG_F64);
-  if (!t.step) t.step = d.step ? d.step : ST_SHARED;
-  if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
+  if (!t.step) t.step = d.step ? d.step : (uint32_t)ST_SHARED;
+  if (!t.conv) t.conv = d.conv ? d.conv : (uint32_t)CV_INT;
   if (!t.skip) t.skip = SK_TABLE;
-  if (!t.depth) t.depth = 15;
-  if (!t.block) t.block = 256;
-  if (!t.unit) t.unit = 16;
+  // zero fields: the same shape as a batch plan's
+  if (!t.depth) t.depth = 31;
+  if (!t.block) t.block = 896;
+  if (!t.unit) t.unit = 64;
+  if (!t.buffers) t.buffers = 1;
   t.buffers = batch_buffers(t);
   t.chains = batch_chains(t);
   if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
@@ -451,9 +457,19 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation table)");
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin);
-    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(batch)");
     g_noalloc_dev[di.device] = ptr;
+  }
+  // once per device and kernel: the kernel's full shared-memory allowance
+  {
+    const void** ready = g_noalloc_ready[di.device];
+    int k = 0;
+    while (k < kNoallocMaxKernels && ready[k] && ready[k] != fn) ++k;
+    if (k == kNoallocMaxKernels || ready[k] != fn) {
+      cudaError_t e =
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin);
+      if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(batch)");
+      if (k < kNoallocMaxKernels) ready[k] = fn;
+    }
   }
   unsigned char* base = static_cast<unsigned char*>(g_noalloc_dev[di.device]);
 

@@ -28,7 +28,9 @@ struct Pool {
 
   bool alloc(uint64_t bytes, uint64_t* off) {
     if (bytes == 0) bytes = 1;
-    const uint64_t need = (bytes + align - 1) / align * align;
+    if (bytes > capacity) return false;  // also keeps the rounding below from wrapping
+    const uint64_t need = bytes + (align - bytes % align) % align;
+    if (need < bytes) return false;
     for (auto it = free_by_off.begin(); it != free_by_off.end(); ++it) {
       if (it->second >= need) {
         const uint64_t o = it->first, sz = it->second;

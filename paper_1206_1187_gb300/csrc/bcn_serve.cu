@@ -53,12 +53,32 @@ static double now_s() {
 
 enum { RQ_QUEUED = 0, RQ_ACTIVE = 1, RQ_DONE = 2, RQ_RELEASED = 3, RQ_CANCELLED = 4 };
 
+// Where rng_server_run_trace collects its requests' latencies: the worker
+// fills it in as requests complete (under the server's lock).
+struct TraceSink {
+  double* latency;    // one entry per request of the trace
+  uint64_t pending;   // requests of the trace not yet complete
+  double last_done;   // completion time of the latest one
+};
+
 struct Request {
   uint64_t seed = 0, offset = 0, n = 0, bytes = 0, pool_off = 0, scheduled = 0;
   uint32_t dt = 0;
   int state = RQ_QUEUED;
   double t_arrive = 0, t_admit = 0, t_done = 0;
+  TraceSink* sink = nullptr;  // set while a running trace waits for this request
+  uint32_t sink_idx = 0;
 };
+
+// What is kept of a request once its pool range is released (or once it is
+// dropped from the queue after a cancel): its final state and times.  Only
+// the most recent kPastRequests of them are kept, so a long-running server's
+// bookkeeping stays bounded.
+struct PastRequest {
+  int state;
+  double t_arrive, t_done;
+};
+constexpr size_t kPastRequests = 1u << 16;
 
 // One launch shape of the batched kernel.
 struct ServeShape {
@@ -91,7 +111,9 @@ struct bcn_server {
   std::mutex mu;
   std::condition_variable cv_work;   // wakes the scheduler
   std::condition_variable cv_done;   // wakes waiters
-  std::unordered_map<uint64_t, bcn::Request> reqs;
+  std::unordered_map<uint64_t, bcn::Request> reqs;        // queued, active or done
+  std::unordered_map<uint64_t, bcn::PastRequest> past;   // released or dropped
+  std::deque<uint64_t> past_order;                       // ids in `past`, oldest first
   std::deque<uint64_t> queue;
   std::vector<uint64_t> active;
   std::deque<std::pair<double, uint64_t>> to_release;  // (time, id)
@@ -116,6 +138,37 @@ static void server_fail(bcn_server* s, cudaError_t e, const char* what) {
   s->cv_done.notify_all();
 }
 
+// Move a released or cancelled request from the live table to the bounded
+// history (mu held).
+static void forget(bcn_server* s, std::unordered_map<uint64_t, Request>::iterator it) {
+  const uint64_t id = it->first;
+  s->past.emplace(id, PastRequest{it->second.state, it->second.t_arrive, it->second.t_done});
+  s->reqs.erase(it);
+  s->past_order.push_back(id);
+  while (s->past_order.size() > kPastRequests) {
+    s->past.erase(s->past_order.front());
+    s->past_order.pop_front();
+  }
+}
+
+// A request's state and times, live or past (mu held); false if unknown.
+static bool lookup(const bcn_server* s, uint64_t id, int* state, double* t_arrive,
+                   double* t_done) {
+  auto it = s->reqs.find(id);
+  if (it != s->reqs.end()) {
+    *state = it->second.state;
+    *t_arrive = it->second.t_arrive;
+    *t_done = it->second.t_done;
+    return true;
+  }
+  auto p = s->past.find(id);
+  if (p == s->past.end()) return false;
+  *state = p->second.state;
+  *t_arrive = p->second.t_arrive;
+  *t_done = p->second.t_done;
+  return true;
+}
+
 // Retire finished iterations; returns true if any finished.
 static bool retire(bcn_server* s) {
   bool any = false;
@@ -131,11 +184,17 @@ static bool retire(bcn_server* s) {
     const double t = now_s();
     std::lock_guard<std::mutex> lock(s->mu);
     for (uint64_t id : sl.finishing) {
-      Request& r = s->reqs[id];
+      Request& r = s->reqs.at(id);  // an active request is never forgotten
       r.state = RQ_DONE;
       r.t_done = t;
       s->st.completed += 1;
       s->st.bytes_done += r.bytes;
+      if (r.sink) {
+        r.sink->latency[r.sink_idx] = t - r.t_arrive;
+        r.sink->last_done = std::max(r.sink->last_done, t);
+        r.sink->pending -= 1;
+        r.sink = nullptr;
+      }
       if (s->cfg.release_after_s >= 0) s->to_release.emplace_back(t + s->cfg.release_after_s, id);
     }
     sl.finishing.clear();
@@ -155,6 +214,7 @@ static void release_due(bcn_server* s, double t) {
     if (it != s->reqs.end() && it->second.state == RQ_DONE) {
       s->pool.release(it->second.pool_off);
       it->second.state = RQ_RELEASED;
+      forget(s, it);
     }
   }
 }
@@ -164,9 +224,11 @@ static bool admit(bcn_server* s, double t) {
   bool any = false;
   while (!s->queue.empty() && s->active.size() < s->cfg.max_active) {
     const uint64_t id = s->queue.front();
-    Request& r = s->reqs[id];
+    auto it = s->reqs.find(id);
+    Request& r = it->second;
     if (r.state == RQ_CANCELLED) {
       s->queue.pop_front();
+      forget(s, it);
       continue;
     }
     uint64_t off = 0;
@@ -200,7 +262,7 @@ static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out, uint32_t* sha
   if (s->nshapes > 1) {  // the iteration's size decides the shape
     uint64_t total = 0;
     for (size_t k = 0; k < na && k < s->cfg.max_items; ++k) {
-      const Request& r = s->reqs[s->active[(s->rr + k) % na]];
+      const Request& r = s->reqs.at(s->active[(s->rr + k) % na]);
       total += std::min<uint64_t>(r.n - r.scheduled, piece);
     }
     if (total >= s->heavy_elems) shape = 1;
@@ -213,7 +275,7 @@ static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out, uint32_t* sha
   still.reserve(na);
   for (size_t k = 0; k < na; ++k) {
     const uint64_t id = s->active[(s->rr + k) % na];
-    Request& r = s->reqs[id];
+    Request& r = s->reqs.at(id);
     if (items >= s->cfg.max_items) {
       still.push_back(id);
       continue;
@@ -356,8 +418,8 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
       t.chains = 2;
     }
     const rng_tune d = auto_defaults(RNG_F64);
-    if (!t.step) t.step = d.step ? d.step : ST_SHARED;
-    if (!t.conv) t.conv = d.conv ? d.conv : CV_INT;
+    if (!t.step) t.step = d.step ? d.step : (uint32_t)ST_SHARED;
+    if (!t.conv) t.conv = d.conv ? d.conv : (uint32_t)CV_INT;
     if (!t.skip) t.skip = SK_TABLE;
     if (!t.depth) t.depth = 15;
     if (!t.block) t.block = 256;
@@ -429,8 +491,14 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
   return RNG_OK;
 }
 
-rng_status rng_server_submit(bcn_server* s, uint64_t start_index, uint64_t offset, uint64_t n,
-                             rng_dtype dt, uint64_t* id) {
+}  // extern "C"
+
+namespace bcn {
+
+// Queue a request arriving at t_arrive; `sink` (nullable) collects its latency.
+static rng_status submit_at(bcn_server* s, uint64_t start_index, uint64_t offset, uint64_t n,
+                            rng_dtype dt, uint64_t* id, double t_arrive, TraceSink* sink,
+                            uint32_t sink_idx) {
   if (!s || !id) return set_error(RNG_EINVAL, "NULL argument");
   if (start_index < kSeedMin || start_index > kSeedMax)
     return set_error(RNG_ERANGE, "start index outside [3^33+100, 2^53]");
@@ -449,7 +517,9 @@ rng_status rng_server_submit(bcn_server* s, uint64_t start_index, uint64_t offse
   r.n = n;
   r.bytes = bytes;
   r.dt = (uint32_t)dt;
-  r.t_arrive = now_s();
+  r.t_arrive = t_arrive;
+  r.sink = sink;
+  r.sink_idx = sink_idx;
   const uint64_t rid = s->next_id++;
   s->reqs.emplace(rid, r);
   s->queue.push_back(rid);
@@ -459,11 +529,23 @@ rng_status rng_server_submit(bcn_server* s, uint64_t start_index, uint64_t offse
   return RNG_OK;
 }
 
+}  // namespace bcn
+
+extern "C" {
+
+rng_status rng_server_submit(bcn_server* s, uint64_t start_index, uint64_t offset, uint64_t n,
+                             rng_dtype dt, uint64_t* id) {
+  return submit_at(s, start_index, offset, n, dt, id, now_s(), nullptr, 0);
+}
+
 rng_status rng_server_cancel(bcn_server* s, uint64_t id) {
   if (!s) return set_error(RNG_EINVAL, "NULL server");
   std::lock_guard<std::mutex> lock(s->mu);
   auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
+  if (it == s->reqs.end()) {
+    if (s->past.count(id)) return set_error(RNG_EBUSY, "request already finished");
+    return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
+  }
   if (it->second.state != RQ_QUEUED) return set_error(RNG_EBUSY, "request already admitted");
   it->second.state = RQ_CANCELLED;
   return RNG_OK;
@@ -472,31 +554,33 @@ rng_status rng_server_cancel(bcn_server* s, uint64_t id) {
 rng_status rng_server_status(bcn_server* s, uint64_t id, int* state, double* latency_s) {
   if (!s) return set_error(RNG_EINVAL, "NULL server");
   std::lock_guard<std::mutex> lock(s->mu);
-  auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
-  if (state) *state = it->second.state;
-  if (latency_s)
-    *latency_s = it->second.state >= RQ_DONE && it->second.state != RQ_CANCELLED
-                     ? it->second.t_done - it->second.t_arrive
-                     : -1.0;
+  int st = 0;
+  double ta = 0, td = 0;
+  if (!lookup(s, id, &st, &ta, &td))
+    return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
+  if (state) *state = st;
+  if (latency_s) *latency_s = st >= RQ_DONE && st != RQ_CANCELLED ? td - ta : -1.0;
   return RNG_OK;
 }
 
 rng_status rng_server_wait(bcn_server* s, uint64_t id, double timeout_s) {
   if (!s) return set_error(RNG_EINVAL, "NULL server");
   std::unique_lock<std::mutex> lock(s->mu);
-  auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
+  int st = 0;
+  double ta = 0, td = 0;
+  if (!lookup(s, id, &st, &ta, &td))
+    return set_error(RNG_EINVAL, "unknown request %llu", (unsigned long long)id);
   const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
                                            std::chrono::duration<double>(timeout_s));
-  while (s->reqs[id].state < RQ_DONE && s->err == RNG_OK) {
-    if (s->cv_done.wait_until(lock, deadline) == std::cv_status::timeout &&
-        s->reqs[id].state < RQ_DONE)
+  while (st < RQ_DONE && s->err == RNG_OK) {
+    const bool timed_out = s->cv_done.wait_until(lock, deadline) == std::cv_status::timeout;
+    lookup(s, id, &st, &ta, &td);  // a queued or active request is never forgotten
+    if (timed_out && st < RQ_DONE)
       return set_error(RNG_ETIMEOUT, "request %llu not done after %.3f s", (unsigned long long)id,
                        timeout_s);
   }
   if (s->err != RNG_OK) return set_error(s->err, "server failed: %s", s->errmsg);
-  if (s->reqs[id].state == RQ_CANCELLED) return set_error(RNG_EINVAL, "request was cancelled");
+  if (st == RQ_CANCELLED) return set_error(RNG_EINVAL, "request was cancelled");
   return RNG_OK;
 }
 
@@ -506,8 +590,11 @@ rng_status rng_server_read(bcn_server* s, uint64_t id, void* dst, uint64_t dst_b
   {
     std::lock_guard<std::mutex> lock(s->mu);
     auto it = s->reqs.find(id);
-    if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request");
-    if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done or released");
+    if (it == s->reqs.end()) {
+      if (s->past.count(id)) return set_error(RNG_EBUSY, "request released");
+      return set_error(RNG_EINVAL, "unknown request");
+    }
+    if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done");
     off = it->second.pool_off;
     bytes = it->second.bytes;
   }
@@ -521,8 +608,11 @@ rng_status rng_server_result_ptr(bcn_server* s, uint64_t id, void** dev_ptr) {
   if (!s || !dev_ptr) return set_error(RNG_EINVAL, "NULL argument");
   std::lock_guard<std::mutex> lock(s->mu);
   auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request");
-  if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done or released");
+  if (it == s->reqs.end()) {
+    if (s->past.count(id)) return set_error(RNG_EBUSY, "request released");
+    return set_error(RNG_EINVAL, "unknown request");
+  }
+  if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done");
   *dev_ptr = s->pool_dev + it->second.pool_off;
   return RNG_OK;
 }
@@ -531,10 +621,14 @@ rng_status rng_server_release(bcn_server* s, uint64_t id) {
   if (!s) return set_error(RNG_EINVAL, "NULL server");
   std::lock_guard<std::mutex> lock(s->mu);
   auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return set_error(RNG_EINVAL, "unknown request");
-  if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done or already released");
+  if (it == s->reqs.end()) {
+    if (s->past.count(id)) return set_error(RNG_EBUSY, "request already released");
+    return set_error(RNG_EINVAL, "unknown request");
+  }
+  if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done");
   s->pool.release(it->second.pool_off);
   it->second.state = RQ_RELEASED;
+  forget(s, it);
   s->cv_work.notify_one();
   return RNG_OK;
 }
@@ -557,7 +651,9 @@ rng_status rng_server_run_trace(bcn_server* s, uint32_t n, const double* arrival
   if (s->cfg.release_after_s < 0) {  // results stay in the pool: the trace must fit it
     uint64_t total = 0;
     for (uint32_t i = 0; i < n; ++i) {
-      const uint64_t b = (counts[i] * dtype_size(dtypes[i]) + 255) / 256 * 256;
+      const uint64_t b = counts[i] > RNG_MAX_N
+                             ? UINT64_MAX
+                             : (counts[i] * dtype_size(dtypes[i]) + 255) / 256 * 256;
       total = total > UINT64_MAX - b ? UINT64_MAX : total + b;
     }
     if (total > s->cfg.pool_bytes)
@@ -566,33 +662,54 @@ rng_status rng_server_run_trace(bcn_server* s, uint32_t n, const double* arrival
                        "them: the pool holds %llu",
                        (unsigned long long)total, (unsigned long long)s->cfg.pool_bytes);
   }
-  std::vector<uint64_t> ids(n, 0);
+  // the worker writes each latency into the sink as its request completes;
+  // on every early return the trace's requests that are still pending are
+  // detached from it (they keep running; only their latency goes unrecorded)
+  TraceSink sink = {latency_s, 0, 0.0};
+  std::vector<uint64_t> ids;
+  ids.reserve(n);
+  auto detach = [&]() {  // mu held
+    for (uint64_t id : ids) {
+      auto it = s->reqs.find(id);
+      if (it != s->reqs.end() && it->second.sink == &sink) it->second.sink = nullptr;
+    }
+  };
   const double t0 = now_s();
   for (uint32_t i = 0; i < n; ++i) {
     const double due = t0 + arrival_s[i];
     while (now_s() < due) {
     }  // open-loop arrivals: spin until the request's arrival time
-    rng_status st = rng_server_submit(s, starts[i], offsets ? offsets[i] : 0, counts[i],
-                                      (rng_dtype)dtypes[i], &ids[i]);
-    if (st != RNG_OK) return st;
+    uint64_t id = 0;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      sink.pending += 1;  // counted before the worker can complete it
+    }
+    // latency counts from the scheduled arrival
+    rng_status st = submit_at(s, starts[i], offsets ? offsets[i] : 0, counts[i],
+                              (rng_dtype)dtypes[i], &id, due, &sink, i);
     std::lock_guard<std::mutex> lock(s->mu);
-    s->reqs[ids[i]].t_arrive = due;  // latency counts from the scheduled arrival
+    if (st != RNG_OK) {
+      sink.pending -= 1;
+      detach();
+      return st;
+    }
+    ids.push_back(id);
   }
-  const double deadline = now_s() + timeout_s;
-  for (uint32_t i = 0; i < n; ++i) {
-    const double left = deadline - now_s();
-    rng_status st = rng_server_wait(s, ids[i], left > 0 ? left : 0.0);
-    if (st != RNG_OK) return st;
-    std::lock_guard<std::mutex> lock(s->mu);
-    const Request& r = s->reqs[ids[i]];
-    latency_s[i] = r.t_done - r.t_arrive;
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                           std::chrono::duration<double>(timeout_s));
+  std::unique_lock<std::mutex> lock(s->mu);
+  while (sink.pending > 0 && s->err == RNG_OK) {
+    if (s->cv_done.wait_until(lock, deadline) == std::cv_status::timeout && sink.pending > 0) {
+      detach();
+      return set_error(RNG_ETIMEOUT, "%llu of %u trace requests not done after %.3f s",
+                       (unsigned long long)sink.pending, n, timeout_s);
+    }
   }
-  if (wall_s) {
-    double last = 0;
-    std::lock_guard<std::mutex> lock(s->mu);
-    for (uint32_t i = 0; i < n; ++i) last = std::max(last, s->reqs[ids[i]].t_done);
-    *wall_s = last - t0;
+  if (s->err != RNG_OK) {
+    detach();
+    return set_error(s->err, "server failed: %s", s->errmsg);
   }
+  if (wall_s) *wall_s = n ? sink.last_done - t0 : 0.0;
   return RNG_OK;
 }
 

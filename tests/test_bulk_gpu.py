@@ -226,6 +226,25 @@ def test_bad_tuning_is_rejected(R):
         assert e.value.status == 1
 
 
+def test_oversized_tiles_shrink_the_block_by_whole_warps(R, oracle_mod):
+    """Tiles too large for the default block's shared memory shrink the block
+    in whole warps until they fit, and the output is unchanged."""
+    import torch
+    optin = getattr(torch.cuda.get_device_properties(0), "shared_memory_per_block_optin",
+                    232448)
+    esz = {"f64": 8, "f32": 4, "u64": 8}
+    for dtype in ("f64", "f32", "u64"):
+        for depth in (255, 127, 63):
+            tune = dict(depth=depth, buffers=2)
+            r = R.resolve_tune(1 << 20, dtype, R.make_tune(**tune))
+            assert r["block"] >= 32 and r["block"] % 32 == 0, (tune, r)
+            assert r["block"] // 32 * r["buffers"] * 32 * r["depth"] * esz[dtype] <= optin
+            n = 32 * depth * 3 + 77
+            a = M + 2718281
+            out = R.generate_at(a, 5, n, dtype, tune=R.make_tune(**tune))
+            assert_same(out, oracle_mod.generate(a, 5, n, dtype), f"{dtype} {tune}")
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_fill_constant_writes_every_element(R, dtype):
     import torch

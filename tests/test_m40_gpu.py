@@ -100,6 +100,22 @@ def test_smallest_states(R, oracle_mod):
         assert v[0] == oracle_mod.to_f64_40(z) and v[0] > 0.0
 
 
+def test_oversized_tiles_shrink_the_block_by_whole_warps(R, oracle_mod):
+    """Tiles too large for the default block's shared memory shrink the block
+    in whole warps until they fit, and the output is unchanged."""
+    import torch
+    optin = getattr(torch.cuda.get_device_properties(0), "shared_memory_per_block_optin",
+                    232448)
+    for dtype in ("f64", "f32"):
+        for tune in (dict(depth=255, buffers=2), dict(depth=127, buffers=2),
+                     dict(depth=63, buffers=2)):
+            r = R.resolve_tune40(1 << 20, dtype, tune)
+            assert r["block"] >= 32 and r["block"] % 32 == 0, (tune, r)
+            smem = r["block"] // 32 * r["buffers"] * 32 * r["depth"] * ESZ[dtype]
+            assert smem <= optin, (tune, r)
+            _check(R, oracle_mod, M40 + 31337, 99, 32 * tune["depth"] * 3 + 77, dtype, tune)
+
+
 def test_bad_arguments(R):
     with pytest.raises(R.RNGError) as e:
         R.generate40_at(M40 + 99, 0, 10)

@@ -90,3 +90,17 @@ def test_pool_rejects_bad_frees(R):
     with pytest.raises(R.RNGError):
         pool.free(o)
     assert pool.alloc(5000) is None
+
+
+def test_pool_refuses_sizes_whose_alignment_would_wrap(R):
+    # a pool near 2^64 bytes: rounding such a request up to the alignment
+    # would pass 2^64 and must not come back as a tiny range
+    cap = (1 << 64) - 1
+    pool = R.Pool(cap, 256)
+    assert pool.alloc(cap) is None
+    assert pool.alloc((1 << 64) - 200) is None
+    st = pool.stats()
+    assert st["in_use"] == 0 and st["live"] == 0 and st["largest_free"] == cap
+    o = pool.alloc(1 << 63)
+    assert o == 0 and pool.stats()["in_use"] == 1 << 63
+    pool.free(o)

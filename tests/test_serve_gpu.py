@@ -122,6 +122,38 @@ def test_trace_replay_latencies(R):
     srv.close()
 
 
+def test_released_requests_are_forgotten_beyond_the_history(R):
+    """A long-running server keeps only a bounded history of released
+    requests; a trace longer than that history still records every latency."""
+    import time
+    n = 70000  # more than the 65536 released requests the server remembers
+    rnd = np.random.default_rng(17)
+    seeds = rnd.integers(M + 100, 2 ** 53, size=n, endpoint=True, dtype=np.uint64)
+    counts = rnd.integers(1, 65, size=n, dtype=np.uint64)
+    dtypes = ["f64" if k % 2 else "f32" for k in range(n)]
+    arrivals = np.zeros(n)
+    srv = R.Server(pool_bytes=64 << 20, release_after_s=0.0)
+    lat, wall = srv.run_trace(arrivals, seeds, counts, dtypes, timeout_s=120.0)
+    assert np.isfinite(lat).all() and np.all(lat > 0) and wall > 0
+    assert srv.stats()["completed"] == n
+    deadline = time.time() + 10.0
+    while srv.stats()["pool_in_use"] and time.time() < deadline:
+        time.sleep(0.01)
+    assert srv.stats()["pool_in_use"] == 0
+    with pytest.raises(R.RNGError) as e:  # the oldest ids are no longer known
+        srv.status(1)
+    assert e.value.status == 1
+    state, last_lat = srv.status(n)  # the newest are, with their latency
+    assert state == "released" and last_lat == pytest.approx(lat[-1])
+    with pytest.raises(R.RNGError) as e:
+        srv.release(n)
+    assert e.value.status == 6  # already released
+    with pytest.raises(R.RNGError) as e:
+        srv.read(n, int(counts[-1]), dtypes[-1])
+    assert e.value.status == 6
+    srv.close()
+
+
 def test_trace_that_cannot_fit_a_never_releasing_pool_is_rejected(R):
     """With results held until the caller frees them, a trace whose outputs
     exceed the pool could never finish: it is refused before any submission."""

@@ -57,6 +57,37 @@ def test_noalloc_batch_equals_the_allocating_batch_twice():
         b.close()
 
 
+def test_noalloc_batch_switches_kernel_shapes():
+    # each kernel shape gets its own shared-memory allowance: a shape needing
+    # more than the 48 KB default after another shape ran first still launches
+    import torch
+    from paper_1206_1187_gb300 import inputs, rng
+
+    fn = rng.lib.rng_batch_generate_noalloc
+    codes_of = {"f64": 0, "f32": 1, "u64": 2}
+    starts, offsets, counts, dtypes = inputs.small_batch(nstreams=200, seed=23, max_len=40000)
+    ref = _tensors(counts, dtypes, -1.0)
+    b = rng.Batch(starts, counts, dtypes, outs=ref, offsets=offsets)
+    b.launch()
+    codes = np.ascontiguousarray([codes_of[d] for d in dtypes], dtype=np.uint8)
+    shapes = [dict(), dict(depth=15, block=256, unit=16, buffers=2),
+              dict(depth=31, block=512, unit=8, buffers=1, chains=1),
+              dict(depth=9, block=128, unit=4, buffers=2), dict()]
+    for shape in shapes:
+        got = _tensors(counts, dtypes, -2.0)
+        ptrs = (ctypes.c_void_p * len(got))(*[t.data_ptr() for t in got])
+        t = rng.make_tune(**shape)
+        rc = fn(len(got), ctypes.c_void_p(starts.ctypes.data),
+                ctypes.c_void_p(offsets.ctypes.data), ctypes.c_void_p(counts.ctypes.data),
+                ctypes.c_void_p(codes.ctypes.data), ptrs, ctypes.byref(t),
+                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0, (shape, rng.lib.rng_last_error())
+        torch.cuda.synchronize()
+        for s in range(len(got)):
+            assert np.array_equal(_bits(got[s]), _bits(ref[s])), (shape, s, dtypes[s])
+    b.close()
+
+
 def test_noalloc_batch_rejects_more_streams_than_its_table_holds():
     import torch
     from paper_1206_1187_gb300 import rng
