@@ -357,6 +357,13 @@ rng_status rng_server_result_ptr(bcn_server *s, uint64_t id, void **dev_ptr);
 rng_status rng_server_release(bcn_server *s, uint64_t id);
 /* Counters since creation (returns the server's error status, if any). */
 rng_status rng_server_stats_get(bcn_server *s, rng_server_stats *out);
+/* Latencies of the requests completed since creation (as rng_server_status
+ * reports them) in quarter-octave bins: bin k counts latencies in
+ * [2^(k/4), 2^((k+1)/4)) microseconds, bin 0 also everything shorter and the
+ * last bin everything longer (2^(95/4) us is about 14 s).  `counts` receives
+ * RNG_SERVER_HIST_BINS words.  Returns the server's error status, if any. */
+#define RNG_SERVER_HIST_BINS 96
+rng_status rng_server_latency_histogram(bcn_server *s, uint64_t *counts);
 /* Replay a request trace in real time: request i is submitted at
  * arrival_s[i] seconds after the call starts (open loop), then every request
  * is awaited (RNG_ETIMEOUT after timeout_s).  latency_s[i] receives the time
@@ -434,8 +441,24 @@ rng_status rng_autotune_bulk(uint64_t n, rng_dtype dt, void *out, void *cuda_str
 
 /* Install `t` as the choice for the zero fields of later calls of dtype dt
  * (its grid is ignored: the grid follows n).  NULL restores the built-in
- * choice.  Process-wide; results never change, only speed. */
+ * choice.  Process-wide; results never change, only speed.
+ *
+ * The environment variable BCN_RNG_TUNE, when set, overrides every installed
+ * tuning for the 3^33 generator's calls: it is read once, on the first call
+ * that resolves a launch, in the form rng_parse_tune reads (for example
+ * "step=barrett,conv=fp64,depth=15,block=256"); its fields fill the zero
+ * fields of bulk calls, and its step and conversion those of batch plans and
+ * the server (grid is ignored).  If it does not parse, every such call fails
+ * with RNG_EINVAL naming the problem. */
 rng_status rng_set_auto_tune(rng_dtype dt, const rng_tune *t);
+
+/* Read a tuning from text: comma-separated key=value pairs with the keys
+ * step (barrett, montgomery, shared, lecuyer, barrett_classic), conv (int,
+ * fp64), layout (tiled, direct), skip (table, sqmul), depth, block, grid,
+ * unit, chains and buffers (decimal; enum fields also accept their numbers).
+ * Fields not named are 0; spaces around pairs are allowed.  RNG_EINVAL for an
+ * unknown key or a bad value.  Host-only; checks no ranges (a launch does). */
+rng_status rng_parse_tune(const char *text, rng_tune *out);
 
 /* ------------------------------------------------------------- utilities */
 
@@ -447,6 +470,15 @@ rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune *in, rng_tu
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int rng_version(void);
+
+/* Testing hook: after `skip` more device or pinned-host allocations by the
+ * library succeed, make the next `count` fail as if cudaMalloc (or
+ * cudaMallocHost) had run out of memory (cudaErrorMemoryAllocation, reported
+ * as RNG_ECUDA by the failing call, which frees what it had allocated).
+ * count = 0 turns injection off.  Process-wide.  The allocating calls are
+ * rng_batch_create, rng_server_create and the first rng_generate_to_host of a
+ * stream (or one with a new chunk size or buffer count). */
+rng_status rng_debug_fail_allocations(uint32_t skip, uint32_t count);
 
 #ifdef __cplusplus
 }

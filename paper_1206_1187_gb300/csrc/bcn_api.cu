@@ -65,6 +65,38 @@ rng_status device_info(DeviceInfo* out) {
   return RNG_OK;
 }
 
+// Allocation failures injected by rng_debug_fail_allocations: after
+// g_fail_skip more allocations succeed, the next g_fail_count fail.
+static std::mutex g_fail_mu;
+static uint64_t g_fail_skip = 0, g_fail_count = 0;
+
+static bool injected_failure() {
+  std::lock_guard<std::mutex> lock(g_fail_mu);
+  if (g_fail_count == 0) return false;
+  if (g_fail_skip > 0) {
+    --g_fail_skip;
+    return false;
+  }
+  --g_fail_count;
+  return true;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_malloc(void** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
+
 static bool seed_ok(uint64_t seed) { return seed >= kSeedMin && seed <= kSeedMax; }
 
 // Shared checks of a bulk call; returns RNG_OK when there is work to launch
@@ -168,7 +200,7 @@ rng_status rng_generate_to_host(bcn_stream* s, uint64_t n, rng_dtype dt, void* h
   if (s->nstage != nbuf || s->stage_bytes != chunk_bytes || s->staging_device != dev) {
     release_staging(s);
     for (uint32_t i = 0; i < nbuf; ++i) {
-      e = cudaMalloc(&s->stage[i], chunk_bytes);
+      e = dev_malloc(&s->stage[i], chunk_bytes);
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stage_cs[i], cudaStreamNonBlocking);
       if (e != cudaSuccess) {
         s->nstage = i + 1;
@@ -303,6 +335,13 @@ rng_status rng_fill_constant(uint64_t n, rng_dtype dt, double value, void* out,
 
 const char* rng_last_error(void) { return g_err; }
 
+rng_status rng_debug_fail_allocations(uint32_t skip, uint32_t count) {
+  std::lock_guard<std::mutex> lock(g_fail_mu);
+  g_fail_skip = skip;
+  g_fail_count = count;
+  return RNG_OK;
+}
+
 rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune* in, rng_tune* out) {
   if (!out) return set_error(RNG_EINVAL, "out is NULL");
   BulkLaunch L;
@@ -321,6 +360,6 @@ rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune* in, rng_tu
   return RNG_OK;
 }
 
-int rng_version(void) { return 102; }
+int rng_version(void) { return 103; }
 
 }  // extern "C"

@@ -186,6 +186,8 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
     return set_error(RNG_EINVAL, "nstreams > 0 and the starts/counts/dtypes/outs arrays are required");
   rng_tune t = {};
   if (tune) t = *tune;
+  const rng_status env = env_tune_check();
+  if (env != RNG_OK) return env;
   const rng_tune d = auto_defaults(RNG_F64);
   if (!t.step) t.step = d.step ? d.step : (uint32_t)ST_SHARED;
   if (!t.conv) t.conv = d.conv ? d.conv : (uint32_t)CV_INT;
@@ -263,7 +265,7 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   const size_t desc_bytes = sizeof(BatchDesc) * nstreams;
   const size_t prefix_bytes = sizeof(uint64_t) * (nstreams + 1);
   b->dev_bytes = desc_bytes + prefix_bytes + 16;
-  cudaError_t e = cudaMalloc(&b->dev, b->dev_bytes);
+  cudaError_t e = dev_malloc(&b->dev, b->dev_bytes);
   if (e != cudaSuccess) {
     delete b;
     return cuda_error(e, "cudaMalloc(batch plan)");
@@ -413,6 +415,8 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
     return set_error(RNG_EINVAL, "the starts/counts/dtypes/outs arrays are required");
   rng_tune t = {};
   if (tune) t = *tune;
+  const rng_status env = env_tune_check();
+  if (env != RNG_OK) return env;
   const rng_tune d = auto_defaults(RNG_F64);
   if (!t.step) t.step = d.step ? d.step : (uint32_t)ST_SHARED;
   if (!t.conv) t.conv = d.conv ? d.conv : (uint32_t)CV_INT;

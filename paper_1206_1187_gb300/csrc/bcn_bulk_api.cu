@@ -42,6 +42,8 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   rng_tune t = {};
   if (tune) t = *tune;
   if (!constant) {  // zero fields take the installed (measured) defaults
+    const rng_status env = env_tune_check();
+    if (env != RNG_OK) return env;
     const rng_tune d = auto_defaults(dt);
     const bool same_layout = !t.layout || !d.layout || t.layout == d.layout;
     if (!t.step) t.step = d.step;

@@ -124,6 +124,7 @@ struct bcn_server {
   char errmsg[256] = {0};
   uint64_t next_id = 1, rr = 0;
   rng_server_stats st = {};
+  uint64_t lat_hist[RNG_SERVER_HIST_BINS] = {};  // completion latencies, quarter octaves
   bcn_server(uint64_t cap) : pool(cap, 256) {}
 };
 
@@ -169,6 +170,15 @@ static bool lookup(const bcn_server* s, uint64_t id, int* state, double* t_arriv
   return true;
 }
 
+// The latency histogram's bin: k with 2^(k/4) <= latency in us < 2^((k+1)/4),
+// clamped to the first and last bins.
+static uint32_t latency_bin(double seconds) {
+  const double us = seconds * 1e6;
+  if (!(us > 1.0)) return 0;
+  const double k = std::floor(4.0 * std::log2(us));
+  return k >= RNG_SERVER_HIST_BINS - 1 ? RNG_SERVER_HIST_BINS - 1 : (uint32_t)k;
+}
+
 // Retire finished iterations; returns true if any finished.
 static bool retire(bcn_server* s) {
   bool any = false;
@@ -189,6 +199,7 @@ static bool retire(bcn_server* s) {
       r.t_done = t;
       s->st.completed += 1;
       s->st.bytes_done += r.bytes;
+      s->lat_hist[latency_bin(t - r.t_arrive)] += 1;
       if (r.sink) {
         r.sink->latency[r.sink_idx] = t - r.t_arrive;
         r.sink->last_done = std::max(r.sink->last_done, t);
@@ -403,6 +414,8 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
   DeviceInfo di;
   rng_status stt = device_info(&di);
   if (stt != RNG_OK) return stt;
+  stt = env_tune_check();
+  if (stt != RNG_OK) return stt;
   // the caller's tuning gives one shape; a tuning left to the server gives two
   const rng_tune zero = {};
   const bool adaptive = memcmp(&cfg.tune, &zero, sizeof zero) == 0;
@@ -467,7 +480,7 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
     if (s->pool_dev) cudaFree(s->pool_dev);
     delete s;
   };
-  e = cudaMalloc(&s->pool_dev, cfg.pool_bytes);
+  e = dev_malloc((void**)&s->pool_dev, cfg.pool_bytes);
   if (e != cudaSuccess) {
     s->pool_dev = nullptr;
     cleanup();
@@ -478,9 +491,10 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
   for (Slot& sl : s->slots) {
     e = cudaStreamCreateWithFlags(&sl.cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_desc, sizeof(BatchDesc) * cfg.max_items);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_prefix, sizeof(uint64_t) * (cfg.max_items + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_table, table);
+    if (e == cudaSuccess) e = pinned_malloc((void**)&sl.h_desc, sizeof(BatchDesc) * cfg.max_items);
+    if (e == cudaSuccess)
+      e = pinned_malloc((void**)&sl.h_prefix, sizeof(uint64_t) * (cfg.max_items + 1));
+    if (e == cudaSuccess) e = dev_malloc((void**)&sl.d_table, table);
     if (e != cudaSuccess) {
       cleanup();
       return cuda_error(e, "creating server slots");
@@ -639,6 +653,13 @@ rng_status rng_server_stats_get(bcn_server* s, rng_server_stats* out) {
   *out = s->st;
   out->pool_in_use = s->pool.in_use;
   out->pool_bytes = s->cfg.pool_bytes;
+  return s->err;
+}
+
+rng_status rng_server_latency_histogram(bcn_server* s, uint64_t* counts) {
+  if (!s || !counts) return set_error(RNG_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  memcpy(counts, s->lat_hist, sizeof s->lat_hist);
   return s->err;
 }
 

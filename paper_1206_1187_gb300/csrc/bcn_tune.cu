@@ -6,6 +6,9 @@
 // its threads per block by running every candidate 100 times and keeping the
 // best (Sec. 3.2); this is the same procedure over this kernel's parameters
 // (reduction, conversion, tile depth, block, grid).
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "bcn_internal.h"
@@ -16,10 +19,110 @@ namespace bcn {
 static std::mutex g_auto_mu;
 static rng_tune g_auto[3] = {};  // per rng_dtype; zero fields = built-in choice
 
+// "key=value,key=value" into *out (fields not named stay 0).  On failure
+// returns false with the reason in err.
+static bool parse_tune(const char* text, rng_tune* out, char* err, size_t errlen) {
+  static const char* const kSteps[] = {"", "barrett", "montgomery", "shared", "lecuyer",
+                                       "barrett_classic"};
+  static const char* const kConvs[] = {"", "int", "fp64"};
+  static const char* const kLayouts[] = {"", "tiled", "direct"};
+  static const char* const kSkips[] = {"", "table", "sqmul"};
+  struct Field {
+    const char* key;
+    uint32_t rng_tune::*member;
+    const char* const* names;
+    int nnames;
+  };
+  static const Field kFields[] = {
+      {"step", &rng_tune::step, kSteps, 6},       {"conv", &rng_tune::conv, kConvs, 3},
+      {"layout", &rng_tune::layout, kLayouts, 3}, {"skip", &rng_tune::skip, kSkips, 3},
+      {"depth", &rng_tune::depth, nullptr, 0},    {"block", &rng_tune::block, nullptr, 0},
+      {"grid", &rng_tune::grid, nullptr, 0},      {"unit", &rng_tune::unit, nullptr, 0},
+      {"chains", &rng_tune::chains, nullptr, 0},  {"buffers", &rng_tune::buffers, nullptr, 0},
+  };
+  rng_tune t = {};
+  const char* p = text;
+  while (*p) {
+    while (*p == ' ' || *p == '\t' || *p == ',') ++p;
+    if (!*p) break;
+    const char* k0 = p;
+    while (*p && *p != '=' && *p != ',' && *p != ' ' && *p != '\t') ++p;
+    const size_t klen = (size_t)(p - k0);
+    while (*p == ' ' || *p == '\t') ++p;
+    if (*p != '=') {
+      snprintf(err, errlen, "expected key=value at '%.*s'", (int)klen, k0);
+      return false;
+    }
+    ++p;
+    while (*p == ' ' || *p == '\t') ++p;
+    const char* v0 = p;
+    while (*p && *p != ',' && *p != ' ' && *p != '\t') ++p;
+    const size_t vlen = (size_t)(p - v0);
+    const Field* f = nullptr;
+    for (const Field& c : kFields)
+      if (strlen(c.key) == klen && strncmp(c.key, k0, klen) == 0) f = &c;
+    if (!f) {
+      snprintf(err, errlen, "unknown key '%.*s'", (int)klen, k0);
+      return false;
+    }
+    bool ok = false;
+    uint32_t value = 0;
+    for (int i = 1; i < f->nnames && !ok; ++i)
+      if (strlen(f->names[i]) == vlen && strncmp(f->names[i], v0, vlen) == 0) {
+        value = (uint32_t)i;
+        ok = true;
+      }
+    if (!ok && vlen > 0 && vlen <= 10) {  // a decimal number
+      uint64_t x = 0;
+      ok = true;
+      for (size_t i = 0; i < vlen; ++i) {
+        if (v0[i] < '0' || v0[i] > '9') {
+          ok = false;
+          break;
+        }
+        x = x * 10 + (uint64_t)(v0[i] - '0');
+      }
+      if (ok && x > 0xFFFFFFFFull) ok = false;
+      value = (uint32_t)x;
+    }
+    if (!ok) {
+      snprintf(err, errlen, "bad value '%.*s' for %s", (int)vlen, v0, f->key);
+      return false;
+    }
+    t.*(f->member) = value;
+  }
+  *out = t;
+  return true;
+}
+
+// BCN_RNG_TUNE, read once: a tuning forced on every call of the 3^33
+// generator (its grid ignored, as the grid follows n).
+static std::once_flag g_env_once;
+static bool g_env_set = false;
+static rng_tune g_env = {};
+static char g_env_err[160] = "";
+
+static void load_env_tune() {
+  const char* v = getenv("BCN_RNG_TUNE");
+  if (!v) return;
+  g_env_set = true;
+  if (!parse_tune(v, &g_env, g_env_err, sizeof g_env_err) && !g_env_err[0])
+    snprintf(g_env_err, sizeof g_env_err, "does not parse");
+  g_env.grid = 0;
+}
+
 rng_tune auto_defaults(int dt) {
+  std::call_once(g_env_once, load_env_tune);
+  if (g_env_set && !g_env_err[0]) return g_env;
   std::lock_guard<std::mutex> lock(g_auto_mu);
   if (dt < 0 || dt > 2) return rng_tune{};
   return g_auto[dt];
+}
+
+rng_status env_tune_check() {
+  std::call_once(g_env_once, load_env_tune);
+  if (g_env_set && g_env_err[0]) return set_error(RNG_EINVAL, "BCN_RNG_TUNE: %s", g_env_err);
+  return RNG_OK;
 }
 
 }  // namespace bcn
@@ -27,6 +130,13 @@ rng_tune auto_defaults(int dt) {
 using namespace bcn;
 
 extern "C" {
+
+rng_status rng_parse_tune(const char* text, rng_tune* out) {
+  if (!text || !out) return set_error(RNG_EINVAL, "NULL argument");
+  char err[160];
+  if (!parse_tune(text, out, err, sizeof err)) return set_error(RNG_EINVAL, "%s", err);
+  return RNG_OK;
+}
 
 rng_status rng_set_auto_tune(rng_dtype dt, const rng_tune* t) {
   if ((int)dt < 0 || (int)dt > 2) return set_error(RNG_EINVAL, "dtype %d", (int)dt);

@@ -100,6 +100,9 @@ def _load() -> ctypes.CDLL:
         "rng_last_error": ([], ctypes.c_char_p),
         "rng_resolve_tune": ([u64, i32, tp, tp], i32),
         "rng_version": ([], i32),
+        "rng_parse_tune": ([ctypes.c_char_p, tp], i32),
+        "rng_debug_fail_allocations": ([u32, u32], i32),
+        "rng_server_latency_histogram": ([vp, ctypes.POINTER(u64)], i32),
         "rng_autotune_bulk": ([u64, i32, vp, vp, tp, u32, u32, tp,
                                ctypes.POINTER(ctypes.c_float)], i32),
         "rng_set_auto_tune": ([i32, tp], i32),
@@ -461,6 +464,14 @@ class Server:
     def release(self, rid: int) -> None:
         _check(lib.rng_server_release(self._h, rid))
 
+    def latency_histogram(self):
+        """Completed-request latency counts in quarter-octave bins: bin k
+        covers [2^(k/4), 2^((k+1)/4)) microseconds (first and last bins open)."""
+        import numpy as np
+        counts = (ctypes.c_uint64 * HIST_BINS)()
+        _check(lib.rng_server_latency_histogram(self._h, counts))
+        return np.array(counts[:], dtype=np.uint64)
+
     def stats(self) -> dict:
         st = ServerStats()
         rc = lib.rng_server_stats_get(self._h, ctypes.byref(st))
@@ -537,6 +548,22 @@ class Pool:
 
 def version() -> int:
     return lib.rng_version()
+
+
+HIST_BINS = 96  # RNG_SERVER_HIST_BINS
+
+
+def parse_tune(text: str) -> dict:
+    """A tuning from "key=value,..." text (the form BCN_RNG_TUNE takes)."""
+    res = Tune()
+    _check(lib.rng_parse_tune(text.encode(), ctypes.byref(res)))
+    return {f: getattr(res, f) for f, _ in Tune._fields_}
+
+
+def debug_fail_allocations(skip: int, count: int) -> None:
+    """Testing hook: after `skip` more library allocations succeed, fail the
+    next `count` as if the device had run out of memory (0, 0 turns it off)."""
+    _check(lib.rng_debug_fail_allocations(skip, count))
 
 
 @dataclass

@@ -119,6 +119,13 @@ def test_trace_replay_latencies(R):
     st = srv.stats()
     assert st["completed"] == 3000
     assert np.percentile(lat, 99) < 0.5
+    # the server's own latency histogram holds the same latencies
+    hist = srv.latency_histogram()
+    assert hist.sum() == 3000
+    us = lat * 1e6
+    k = np.where(us > 1.0, np.floor(4.0 * np.log2(np.maximum(us, 1.0))), 0)
+    want = np.bincount(np.minimum(k, R.HIST_BINS - 1).astype(np.int64), minlength=R.HIST_BINS)
+    assert np.abs(hist.astype(np.int64) - want).sum() <= 4  # bin-edge rounding at most
     srv.close()
 
 
