@@ -90,9 +90,9 @@ def test_host_transfer_staging_failure_leaves_the_stream_usable(R, oracle_mod):
     with pytest.raises(R.RNGError) as e:
         s.generate_to_host(n, "f64", chunk_bytes=1 << 20, nbuf=4)
     assert e.value.status == 4
-    assert s.state() == (M + 4321, 1000)  # a failed call does not advance the stream
+    assert s.state == (M + 4321, 1000)  # a failed call does not advance the stream
     h = s.generate_to_host(n, "f64", chunk_bytes=1 << 20, nbuf=4)
-    assert s.state() == (M + 4321, 1000 + n)
+    assert s.state == (M + 4321, 1000 + n)
     want = oracle_mod.generate(M + 4321, 1000, n, "f64")
     assert np.array_equal(h.numpy().view(np.int64), _obits(want))
 
