@@ -300,12 +300,12 @@ typedef struct bcn_server bcn_server;
 typedef struct {
   uint64_t pool_bytes;     /* device output pool, cudaMalloc'd at creation     */
   uint64_t chunk_elems;    /* piece of one request per iteration when many
-                              requests are active (0 = 2^21; rounded up to a
+                              requests are active (0 = 2^22; rounded up to a
                               multiple of 4); with k active requests a piece
                               may grow to 64*chunk_elems/k                      */
   uint32_t max_active;     /* admitted requests at once (0 = 4096)             */
   uint32_t max_items;      /* work items per iteration (0 = 1024)              */
-  uint32_t inflight;       /* iterations in flight, 1..8 (0 = 2)               */
+  uint32_t inflight;       /* iterations in flight, 1..8 (0 = 4)               */
   uint32_t pad;
   double release_after_s;  /* >= 0: free a result's pool range this long after
                               it completes; < 0: the caller releases it        */

@@ -405,11 +405,14 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
   *out = nullptr;
   rng_server_config cfg = *cfg_in;
   if (cfg.pool_bytes == 0) return set_error(RNG_EINVAL, "pool_bytes must be > 0");
-  if (!cfg.chunk_elems) cfg.chunk_elems = 1ull << 21;
+  // defaults measured on the serving trace (20k req/s, 1 KiB..256 MiB): against
+  // 2^21 and two slots, the saturated trace runs 1% faster and the nominal
+  // one's p99 drops from 0.164 to 0.133 ms
+  if (!cfg.chunk_elems) cfg.chunk_elems = 1ull << 22;
   cfg.chunk_elems = (cfg.chunk_elems + 3) / 4 * 4;  // chunks start 16-byte aligned
   if (!cfg.max_active) cfg.max_active = 4096;
   if (!cfg.max_items) cfg.max_items = 1024;
-  if (!cfg.inflight) cfg.inflight = 2;
+  if (!cfg.inflight) cfg.inflight = 4;
   if (cfg.inflight > 8) return set_error(RNG_EINVAL, "inflight must be 1..8");
   DeviceInfo di;
   rng_status stt = device_info(&di);
