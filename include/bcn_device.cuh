@@ -31,10 +31,21 @@ struct Stream {
 
 // A generator positioned at variate `offset` (0-based) of the sequence seeded
 // with `start_index`: one fixed-base exponentiation (six modular products).
+// Every 64-bit offset is exact (the sequence continues past 2^64 - 1).
 __device__ inline Stream make_stream(uint64_t start_index, uint64_t offset) {
   const uint64_t e0 = (start_index - bcn::kM) % bcn::kP;
   Stream s;
-  s.z = bcn::seed_state_table(bcn::exponent_add(e0, offset + 1));
+  s.z = bcn::seed_state_table(bcn::exponent_add(bcn::exponent_add(e0, offset), 1));
+  return s;
+}
+
+// The generator at variate offset + extra, the sum taken without 64-bit
+// wrap-around (a thread's start inside a call that began at `offset`).
+__device__ inline Stream make_stream(uint64_t start_index, uint64_t offset, uint64_t extra) {
+  const uint64_t e0 = (start_index - bcn::kM) % bcn::kP;
+  Stream s;
+  s.z = bcn::seed_state_table(
+      bcn::exponent_add(bcn::exponent_add(bcn::exponent_add(e0, offset), extra), 1));
   return s;
 }
 

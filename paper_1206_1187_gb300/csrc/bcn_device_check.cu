@@ -16,7 +16,7 @@ __global__ void device_api_kernel(uint64_t start, uint64_t offset, uint64_t n, d
   const uint64_t a = (uint64_t)((unsigned __int128)n * t / T);
   const uint64_t b = (uint64_t)((unsigned __int128)n * (t + 1) / T);
   if (a >= b) return;
-  bcn_device::Stream g = bcn_device::make_stream(start, offset + a);
+  bcn_device::Stream g = bcn_device::make_stream(start, offset, a);
   bcn_device::Stream h = g;
   for (uint64_t i = a; i < b; ++i) {
     f64[i] = bcn_device::next_f64(g);

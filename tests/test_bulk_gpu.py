@@ -131,8 +131,10 @@ def test_windows_around_tiny_variates(R, oracle_mod):
 def test_device_side_api_matches_the_oracle(R, oracle_mod):
     """A kernel written only against include/bcn_device.cuh (per-thread
     generators positioned by skip-ahead) gives the oracle's variates."""
+    # the last two start at and run across the 2^64 boundary of the index
     for a, off, n, threads in [(M + 100, 0, 100003, 1000), (2 ** 53, 2 ** 50 + 7, 4097, 1),
-                               (M + 12345, 123, 250000, 65536)]:
+                               (M + 12345, 123, 250000, 65536), (M + 100, 2 ** 64 - 3000, 6000, 64),
+                               (2 ** 53, 2 ** 64 - 1, 10, 3)]:
         f64, f32 = R.device_api_check(a, off, n, threads=threads)
         assert_same(f64, oracle_mod.generate(a, off, n, "f64"), f"f64 {a} {threads}")
         assert_same(f32, oracle_mod.generate(a, off, n, "f32"), f"f32 {a} {threads}")
@@ -203,7 +205,7 @@ def test_generate_to_host_pipelines_chunks(R, oracle_mod):
 
 def test_offsets_across_the_period_and_far_out(R, oracle_mod):
     a = 2 ** 53
-    for off in (P - 50, P, 2 * P - 7, 2 ** 60 + 11, 2 ** 64 - 5000):
+    for off in (P - 50, P, 2 * P - 7, 2 ** 60 + 11, 2 ** 64 - 5000, 2 ** 64 - 2000):
         n = 4000
         for dtype in ("u64", "f64"):
             out = R.generate_at(a, off, n, dtype)
