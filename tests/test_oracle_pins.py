@@ -213,6 +213,10 @@ def test_f32_is_truncated_f64(oracle_mod):
         got = oracle_mod.to_f32(z)
         assert got.view(np.uint32) == want.view(np.uint32), z
         assert 0.0 < got < 1.0
+        # rounding toward zero as exact rationals: got <= v < the next float up
+        v = Fraction(float(oracle_mod.to_f64(z)))
+        up = np.nextafter(np.float32(got), np.float32(1.0))
+        assert Fraction(float(got)) <= v < Fraction(float(up)), z
 
 
 def test_vector_paths_match_scalar_paths(oracle_mod):
