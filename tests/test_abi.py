@@ -119,3 +119,63 @@ def test_modulus_40_checks_arguments_first(lib):
     t = lib.make_tune(step="barrett")
     assert raw.rng40_generate_at(m40 + 100, 0, 10, 0, vp, None, ctypes.byref(t)) == 1
     assert b"3^40" in raw.rng_last_error()
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "bcn_rng.h"
+
+#define CHECK(x) do { rng_status st_ = (x); if (st_ != RNG_OK) { \
+    printf("FAIL %s: %d %s\n", #x, (int)st_, rng_last_error()); return 1; } } while (0)
+
+int main(void) {
+  bcn_stream *s = NULL;
+  uint64_t a = 0, c = 0, off = 0, in_use = 0, live = 0;
+  rng_tune t;
+  bcn_pool *p = NULL;
+  if (rng_create(5559060566555523ULL + 99, &s) != RNG_ERANGE) return 2;
+  CHECK(rng_create(5559060566555523ULL + 100, &s));
+  CHECK(rng_skip(s, 1000));
+  CHECK(rng_get_state(s, &a, &c));
+  if (a != 5559060566555523ULL + 100 || c != 1000) return 3;
+  CHECK(rng_set_state(s, 1ULL << 53, 7));
+  CHECK(rng_get_state(s, &a, &c));
+  if (a != (1ULL << 53) || c != 7) return 4;
+  CHECK(rng_destroy(s));
+  CHECK(rng_parse_tune("step=barrett,depth=15", &t));
+  if (t.step != RNG_STEP_BARRETT || t.depth != 15 || t.block != 0) return 5;
+  if (rng_parse_tune("depth=x", &t) != RNG_EINVAL || strstr(rng_last_error(), "depth") == NULL)
+    return 6;
+  CHECK(rng_pool_create(1 << 20, 256, &p));
+  CHECK(rng_pool_alloc(p, 1000, &off));
+  CHECK(rng_pool_stats(p, &in_use, NULL, &live, NULL, NULL));
+  if (off != 0 || in_use != 1024 || live != 1) return 7;
+  CHECK(rng_pool_free(p, off));
+  CHECK(rng_pool_destroy(p));
+  printf("ok %d\n", rng_version());
+  return 0;
+}
+"""
+
+
+def test_the_boundary_is_usable_from_plain_c(lib, tmp_path):
+    """The header compiles as C99 with warnings as errors, and a C program
+    linked against the library drives its host-side entry points."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib.library_info.path)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        "-L", libdir, "-lbcn_rng", f"-Wl,-rpath,{libdir}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() == f"ok {lib.version()}"
