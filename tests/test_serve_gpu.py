@@ -202,3 +202,44 @@ def test_heavy_iterations_give_the_same_bytes(R, oracle_mod):
                                         rnd.integers(0, n, 1000)]))
         want = oracle_mod.at(a, (off + idx).astype(np.uint64), dt)
         assert np.array_equal(got[idx], _obits(want))
+
+
+def test_concurrent_clients(R, oracle_mod):
+    """Four host threads submit, wait for, read and release their own requests
+    at once (the library's calls run without the interpreter lock); every
+    result is the bytes of that request alone."""
+    import threading
+    srv = R.Server(pool_bytes=256 << 20, release_after_s=-1.0)
+    errors, checked = [], []
+
+    def client(k):
+        try:
+            rnd = np.random.default_rng(100 + k)
+            for i in range(120):
+                a = int(rnd.integers(M + 100, 2 ** 53))
+                off = int(rnd.integers(0, 2 ** 40))
+                n = int(rnd.integers(1, 200000))
+                dt = ("f64", "f32", "u64")[int(rnd.integers(0, 3))]
+                rid = srv.submit(a, off, n, dt)
+                srv.wait(rid, 60.0)
+                got = _bits(srv.read(rid, n, dt))
+                srv.release(rid)
+                if i % 10 == 0:
+                    want = oracle_mod.generate(a, off, n, dt)
+                    if not np.array_equal(got, _obits(want)):
+                        errors.append((k, i, a, off, n, dt))
+                    checked.append(1)
+        except Exception as e:  # surfaced below
+            errors.append((k, repr(e)))
+
+    threads = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(300)
+    assert not any(t.is_alive() for t in threads)
+    assert not errors, errors[:3]
+    assert len(checked) == 48
+    st = srv.stats()
+    assert st["completed"] == 480 and st["pool_in_use"] == 0
+    srv.close()
