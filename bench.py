@@ -345,7 +345,9 @@ def measure_m40(rng, stream, peaks, steps: int):
                          "truncated variates, into device memory",
              "launches": steps, "ms_per_launch": ms, "variates_per_s": n / (ms / 1e3),
              "GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"],
-             "tune": rng.resolve_tune40(n, "f64")}
+             "tune": rng.resolve_tune40(n, "f64"),
+             "traffic": profiled_value("traffic_bytes_per_launch", "m40_f64_2e28", "m40"),
+             "algorithmic_bytes_per_launch": 8.0 * n}
     ipv = profiled_value("inst_per_variate", "m40_2e25", "m40")
     if ipv is not None:
         peak = 152 * 4 * 32 * 2.07e9

@@ -8,7 +8,7 @@
 #include <new>
 #include <vector>
 
-#include "bcn_internal.h"
+#include "bcn_host.h"
 #include "bcn_math.cuh"
 
 struct bcn_stream {

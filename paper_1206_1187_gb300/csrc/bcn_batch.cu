@@ -21,6 +21,7 @@
 
 #include "bcn_batch.cuh"
 #include "bcn_gen.cuh"
+#include "bcn_host.h"
 
 struct bcn_batch {
   uint32_t nstreams;

@@ -6,6 +6,7 @@
 #include <utility>
 
 #include "bcn_bulk.cuh"
+#include "bcn_host.h"
 #include "bcn_math.cuh"
 
 namespace bcn {

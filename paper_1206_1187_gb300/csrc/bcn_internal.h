@@ -56,14 +56,6 @@ rng_status enable_smem(const void* fn, int device, size_t bytes);
 // The tuning installed by rng_set_auto_tune for dtype dt (zeros if none), or
 // the one BCN_RNG_TUNE forces for every dtype when that variable is set.
 rng_tune auto_defaults(int dt);
-// RNG_OK, or RNG_EINVAL with the message when BCN_RNG_TUNE is set but does
-// not parse (every call that takes defaults then fails loudly).
-rng_status env_tune_check();
-
-// The library's device and pinned-host allocations go through these, so a
-// test can make them fail (rng_debug_fail_allocations) as if memory ran out.
-cudaError_t dev_malloc(void** p, size_t bytes);
-cudaError_t pinned_malloc(void** p, size_t bytes);
 
 // Fill in every zero field of `tune` for a bulk call of n elements of dt.
 rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* out,

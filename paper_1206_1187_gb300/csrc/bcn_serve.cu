@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "bcn_batch.cuh"
+#include "bcn_host.h"
 #include "bcn_math.cuh"
 #include "bcn_pool.h"
 

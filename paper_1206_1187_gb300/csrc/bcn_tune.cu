@@ -11,7 +11,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "bcn_internal.h"
+#include "bcn_host.h"
 #include "bcn_math.cuh"
 
 namespace bcn {
