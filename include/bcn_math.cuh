@@ -461,9 +461,26 @@ __device__ __forceinline__ uint64_t shared_advance(uint64_t z) {
 }
 
 // FP64-pipe conversion: exact int->double, then one RN multiply (no FMA).
+// Both operations run on the FP64 pipe and none on the integer pipes, which
+// is what a kernel bound by its integer work wants from it.
 __device__ __forceinline__ uint64_t f64_bits_fp64(uint64_t z) {
   double v = __dmul_rn(__ull2double_rn(z), kR3i);
   return (uint64_t)__double_as_longlong(v);
+}
+
+// The same value from one fused multiply-add, for conversions made entirely
+// on the FP64 pipe (where that pipe binds).  D = 2^52 + (z mod 2^52) is an
+// exact double built from z's words (high word 0x43300000 | (z1 & 0xFFFFF)):
+// it equals 2^52 + z below 2^52 and z itself from 2^52 up.  With off =
+// -2^52*r3i in the first case (exact: r3i scaled by a power of two) and 0 in
+// the second, D*r3i + off = z*r3i exactly, and the FMA rounds that once:
+// RN(z * r3i), with half the FP64-pipe work of the form above.
+constexpr double kR3iTimes2p52 = kR3i * 4503599627370496.0;  // 2^52 * r3i
+__device__ __forceinline__ uint64_t f64_bits_fp64_fma(uint64_t z) {
+  const uint32_t z1 = (uint32_t)(z >> 32);
+  const double d = __hiloint2double((int)(0x43300000u | (z1 & 0xFFFFFu)), (int)(uint32_t)z);
+  const double off = z1 >= 0x100000u ? 0.0 : -kR3iTimes2p52;
+  return (uint64_t)__double_as_longlong(__fma_rn(d, kR3i, off));
 }
 
 // FP32 variate: the FP64 variate truncated toward zero.  Every variate is

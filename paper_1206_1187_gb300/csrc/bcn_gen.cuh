@@ -25,7 +25,7 @@ __device__ __forceinline__ typename Word<DT>::type to_word(uint64_t z, uint64_t 
       p_from_barrett_product(z, phi, plo, qh, ql);
       bits = f64_bits_from_p(qh, ql);
     } else {
-      bits = f64_bits_fp64(z);
+      bits = f64_bits_fp64_fma(z);  // every conversion on the FP64 pipe
     }
     if constexpr (DT == DT_F64) return bits;
     else return f32_bits_from_f64_bits(bits);
@@ -45,7 +45,7 @@ struct Gen {
         z = shared_advance(z);
         return w;
       } else if constexpr (CONV == CV_FP64) {
-        const uint64_t bits = f64_bits_fp64(z);
+        const uint64_t bits = f64_bits_fp64_fma(z);
         z = shared_advance(z);
         if constexpr (DT == DT_F64) return bits;
         else return f32_bits_from_f64_bits(bits);

@@ -389,3 +389,28 @@ def test_fused_fast_variate_image():
         w3 = funnel_l(mh, 0, j)
         image = (w3 << 96) | (w2 << 64) | (w1 << 32)
         assert Fraction(image, 2 ** 105) == Fraction(v), v
+
+
+def f64_of_bits(b: int) -> float:
+    return struct.unpack("<d", struct.pack("<Q", b))[0]
+
+
+def test_fp64_pipe_conversion_by_one_fused_multiply_add():
+    """The FP64-pipe conversion in one FMA: D = 2^52 + (z mod 2^52), whose bits
+    are the high word 0x43300000 | (z1 & 0xFFFFF) over the low word z0, is an
+    exact double; fma(D, r3i, off) with off = -2^52*r3i when z < 2^52 and 0
+    otherwise rounds D*r3i + off = z*r3i once, so it is RN(z * r3i)."""
+    off_bits = f64_bits(-(2.0 ** 52) * R3I)
+    assert Fraction(f64_of_bits(off_bits)) == -Fraction(2 ** 52) * Fraction(R3I)  # exact
+    extra = [2 ** 52 - 1, 2 ** 52, 2 ** 52 + 1, (2 ** 52) - (2 ** 20), 2 ** 52 + 2 ** 32,
+             M - 1, 1, 2 ** 32 - 1, 2 ** 32, 2 ** 32 + 1]
+    for z in states(30000, seed=21) + extra:
+        z0, z1 = z & MASK32, z >> 32
+        hi = 0x43300000 | (z1 & 0xFFFFF)
+        d = f64_of_bits((hi << 32) | z0)
+        big = z1 >= 0x100000  # z >= 2^52
+        assert Fraction(d) == (z if big else 2 ** 52 + z)  # D is exact
+        off = Fraction(0) if big else Fraction(f64_of_bits(off_bits))
+        exact = Fraction(d) * Fraction(R3I) + off
+        assert exact == Fraction(z) * Fraction(R3I)
+        assert f64_bits(float(exact)) == rn_bits(z)  # one rounding of the same value
