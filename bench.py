@@ -397,12 +397,15 @@ def measure_serving(rng, n_requests: int = 20000):
 
 
 def paper_table(rng, n: int = N_DEFAULT, reps: int = 20):
-    """The paper's rate tables redone on this GPU (Table 1 and Table 2 of Sec. 3):
-    every reduction in the per-thread layout (each thread writes consecutive
-    positions, the paper's uncoalesced 'naive' kernels, 4096 variates per
-    thread) and in the coalesced tiled layout, plus the Constant kernel, at
-    n = 2^28 FP64; the net generation rate subtracts the Constant kernel's time
-    (Table 2's RunTime - ConstantUnrolled)."""
+    """The paper's rate tables redone on this GPU (Table 1 and Table 2 of Sec. 3),
+    with its kernel forms: Naive (each thread writes its own consecutive
+    positions, 4096 variates per thread), Coalesced (the paper's strided
+    writes: a thread's outputs one step of T threads apart, Sec. 2.2) and
+    Unrolled (the same, generation loop unrolled by eight), for every reduction
+    and the Constant kernel, at n = 2^28 FP64; each kernel at its best block of
+    128..512 threads, as the paper times every block size and keeps the best.
+    Tiled rows add this library's in-order layout.  Net rates subtract the
+    Constant kernel of the same form (Table 2's RunTime - ConstantUnrolled)."""
     import torch
     out = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -420,23 +423,38 @@ def paper_table(rng, n: int = N_DEFAULT, reps: int = 20):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    rows = []
-    const = {}
-    for layout, label in (("direct", "Naive"), ("tiled", "Coalesced")):
-        t = rng.make_tune(layout=layout)
-        ms = timed(lambda: rng.fill_constant(n, "f64", 0.5, out=out, tune=t, stream=stream))
-        const[layout] = ms
-        rows.append({"method": f"Constant{label}", "ms": ms, "gnum_s": n / ms / 1e6})
+    forms = (("Naive", dict(layout="direct"), (128, 256, 384, 512)),
+             ("Coalesced", dict(layout="strided", unit=1), (128, 256, 384, 512)),
+             ("Unrolled", dict(layout="strided", unit=8), (128, 256, 384, 512)),
+             ("Tiled", dict(layout="tiled"), (0,)))
+
+    def best(run, base, blocks):
+        res = None
+        for block in blocks:
+            t = rng.make_tune(block=block, **base)
+            ms = timed(lambda: run(t))
+            if res is None or ms < res[0]:
+                res = (ms, block)
+        return res
+
+    rows, const = [], {}
+    for label, base, blocks in forms:
+        ms, block = best(lambda t: rng.fill_constant(n, "f64", 0.5, out=out, tune=t,
+                                                     stream=stream), base, blocks)
+        const[label] = ms
+        rows.append({"method": f"Constant{label}", "block": block, "ms": ms,
+                     "gnum_s": n / ms / 1e6})
     names = {"barrett_classic": "Barrett", "lecuyer": "LCN", "barrett": "BarrettModified",
              "montgomery": "Montgomery", "shared": "BarrettShared"}
     for step, name in names.items():
-        for layout, label in (("direct", ""), ("tiled", "Coalesced")):
-            t = rng.make_tune(step=step, layout=layout)
-            ms = timed(lambda: rng.generate_at_ptr(SEED, 0, n, "f64", out.data_ptr(), tune=t,
-                                                   stream=stream))
-            net = ms - const[layout]
-            rows.append({"method": name + label, "ms": ms, "gnum_s": n / ms / 1e6,
-                         "net_ms": net, "net_gnum_s": (n / net / 1e6) if net > 0 else None})
+        for label, base, blocks in forms:
+            ms, block = best(lambda t: rng.generate_at_ptr(SEED, 0, n, "f64", out.data_ptr(),
+                                                           tune=t, stream=stream),
+                             dict(base, step=step), blocks)
+            net = ms - const[label]
+            rows.append({"method": name + ("" if label == "Naive" else label), "block": block,
+                         "ms": ms, "gnum_s": n / ms / 1e6, "net_ms": net,
+                         "net_gnum_s": (n / net / 1e6) if net > 0 else None})
     return {"n": n, "dtype": "f64", "reps": reps, "rows": rows,
             "note": "paper: Tesla C2050, BarrettModified 11.44 Gnum/s, ConstantCoalesced "
                     "12.41 Gnum/s (Table 1); BarrettOpt net 122.56 Gnum/s (Table 2)"}

@@ -90,9 +90,19 @@ typedef enum {
   RNG_LAYOUT_TILED = 1,  /* lanes of a warp own consecutive runs of `depth`
                             variates of one tile; the warp's tile is staged in
                             shared memory and written by one bulk async copy */
-  RNG_LAYOUT_DIRECT = 2  /* thread t of T owns [t*n/T, (t+1)*n/T) and stores
+  RNG_LAYOUT_DIRECT = 2, /* thread t of T owns [t*n/T, (t+1)*n/T) and stores
                             each variate itself (the paper's per-thread split,
                             Sec. 1; uncoalesced) */
+  RNG_LAYOUT_STRIDED = 3 /* the paper's coalesced kernels (Sec. 2.2, its
+                            partial-unrolling listing): thread t of T = n/W
+                            makes variates t*W .. t*W+W-1 of the call and
+                            stores variate t*W+j at position j*T+t.  The output
+                            is that PERMUTATION of the sequence, not the
+                            sequence order: W = tune.depth (0 = 4096, the
+                            paper's choice) must divide n, tune.unit is the
+                            loop's unroll factor (1 or 8; 0 = 8, the paper's
+                            "Unrolled" kernels).  Only taken when a call's own
+                            tuning names it, never as a default. */
 } rng_layout;
 
 /* Skip-ahead method for the state at the start of a block (Eq. 2). */
@@ -106,16 +116,19 @@ typedef enum {
  * rng_set_auto_tune for the output type if any, else the shape measured best
  * on GB300 (tiles 31 deep, 896-thread blocks, two chains per lane, one tile
  * buffer per warp; batch plans also 64-tile work units).  Results never
- * depend on these fields; only speed does. */
+ * depend on these fields, only speed does -- except layout =
+ * RNG_LAYOUT_STRIDED, which writes the paper's permuted order. */
 typedef struct {
   uint32_t step;    /* rng_step                                              */
   uint32_t conv;    /* rng_conv                                              */
   uint32_t layout;  /* rng_layout                                            */
   uint32_t skip;    /* rng_skip_method                                       */
-  uint32_t depth;   /* TILED: variates per lane per tile, odd, 1..255        */
+  uint32_t depth;   /* TILED: variates per lane per tile, odd, 1..255;
+                       STRIDED: variates per thread                          */
   uint32_t block;   /* threads per block (TILED: multiple of 32, <= 1024)    */
   uint32_t grid;    /* blocks                                                */
-  uint32_t unit;    /* BATCH: tiles per work unit (0 = choose); else ignored */
+  uint32_t unit;    /* BATCH: tiles per work unit (0 = choose); STRIDED: loop
+                       unroll factor 1 or 8 (0 = 8); else ignored            */
   uint32_t chains;  /* TILED, forward steps: independent chains per lane, 1
                        or 2 (0 = choose); 2 splits each lane's run in halves */
   uint32_t buffers; /* TILED and BATCH: shared-memory tile buffers per warp,
@@ -441,7 +454,8 @@ rng_status rng_autotune_bulk(uint64_t n, rng_dtype dt, void *out, void *cuda_str
 
 /* Install `t` as the choice for the zero fields of later calls of dtype dt
  * (its grid is ignored: the grid follows n).  NULL restores the built-in
- * choice.  Process-wide; results never change, only speed.
+ * choice.  Process-wide; results never change, only speed (a tuning naming
+ * RNG_LAYOUT_STRIDED, which permutes the output, is RNG_EINVAL here).
  *
  * The environment variable BCN_RNG_TUNE, when set, overrides every installed
  * tuning for the 3^33 generator's calls: it is read once, on the first call
@@ -454,7 +468,7 @@ rng_status rng_set_auto_tune(rng_dtype dt, const rng_tune *t);
 
 /* Read a tuning from text: comma-separated key=value pairs with the keys
  * step (barrett, montgomery, shared, lecuyer, barrett_classic), conv (int,
- * fp64), layout (tiled, direct), skip (table, sqmul), depth, block, grid,
+ * fp64), layout (tiled, direct, strided), skip (table, sqmul), depth, block, grid,
  * unit, chains and buffers (decimal; enum fields also accept their numbers).
  * Fields not named are 0; spaces around pairs are allowed.  RNG_EINVAL for an
  * unknown key or a bad value.  Host-only; checks no ranges (a launch does). */

@@ -137,6 +137,21 @@ def generate(a: int, j: int, n: int, dtype: str = "f64") -> np.ndarray:
     return out
 
 
+def generate_strided(a: int, j: int, n: int, dtype: str = "f64", per: int = 4096) -> np.ndarray:
+    """The paper's coalesced output order (Sec. 2.2): with T = n / per threads,
+    thread t makes variates j + t*per .. j + t*per + per - 1 (its block of the
+    sequence) and writes variate j + t*per + k to position k*T + t, i.e. its
+    k-th output at its start index plus k times the step T."""
+    if per <= 0 or n % per:
+        raise ValueError(f"n = {n} is not a multiple of {per} variates per thread")
+    seq = generate(a, j, n, dtype)
+    threads = n // per
+    out = np.empty_like(seq)
+    for k in range(per):  # every thread's k-th variate, threads in order
+        out[k * threads:(k + 1) * threads] = seq[k::per]
+    return out
+
+
 def generate_mt(a: int, j: int, n: int, dtype: str = "f64", threads: int = 1,
                 out: np.ndarray | None = None) -> np.ndarray:
     """Same as generate(), split over host threads by skip-ahead (timing mode)."""

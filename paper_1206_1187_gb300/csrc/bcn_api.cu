@@ -354,8 +354,9 @@ rng_status rng_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune* in, rng_tu
   out->depth = L.depth;
   out->block = L.block;
   out->grid = L.grid;
-  out->unit = 0;
-  out->chains = L.chains;
+  const bool strided = L.layout == RNG_LAYOUT_STRIDED;
+  out->unit = strided ? L.chains : 0;  // the strided layout's unroll factor
+  out->chains = strided ? 0 : L.chains;
   out->buffers = L.buffers;
   return RNG_OK;
 }

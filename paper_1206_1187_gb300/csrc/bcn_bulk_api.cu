@@ -7,6 +7,7 @@
 
 #include "bcn_bulk.cuh"
 #include "bcn_host.h"
+#include "bcn_strided.cuh"
 #include "bcn_math.cuh"
 
 namespace bcn {
@@ -46,7 +47,11 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
     const rng_status env = env_tune_check();
     if (env != RNG_OK) return env;
     const rng_tune d = auto_defaults(dt);
-    const bool same_layout = !t.layout || !d.layout || t.layout == d.layout;
+    if (d.layout == RNG_LAYOUT_STRIDED)
+      return set_error(RNG_EINVAL, "the strided layout permutes the output; only a call's own "
+                                   "tuning may name it, not a default");
+    const bool same_layout = t.layout != RNG_LAYOUT_STRIDED &&
+                             (!t.layout || !d.layout || t.layout == d.layout);
     if (!t.step) t.step = d.step;
     if (!t.conv) t.conv = d.conv;
     if (!t.skip) t.skip = d.skip;
@@ -64,7 +69,8 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   L.step = constant ? ST_CONST : (t.step ? (int)t.step : ST_SHARED);
   L.conv = t.conv ? (int)t.conv : CV_INT;
   L.skip = t.skip ? (int)t.skip : SK_TABLE;
-  if (L.layout != RNG_LAYOUT_TILED && L.layout != RNG_LAYOUT_DIRECT)
+  if (L.layout != RNG_LAYOUT_TILED && L.layout != RNG_LAYOUT_DIRECT &&
+      L.layout != RNG_LAYOUT_STRIDED)
     return set_error(RNG_EINVAL, "tune.layout %u is not a layout", t.layout);
   if (!constant && L.step != ST_BARRETT && L.step != ST_MONT && L.step != ST_SHARED &&
       L.step != ST_LECUYER && L.step != ST_BCLASSIC)
@@ -81,6 +87,32 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   rng_status st = device_info(&di);
   if (st != RNG_OK) return st;
   if (t.chains > 2) return set_error(RNG_EINVAL, "tune.chains %u must be 0, 1 or 2", t.chains);
+  if (L.layout == RNG_LAYOUT_STRIDED) {  // the paper's coalesced kernels (Sec. 2.2)
+    L.depth = t.depth ? t.depth : 4096;   // W: variates per thread, the paper's choice
+    L.chains = t.unit ? t.unit : 8;       // here: the generation loop's unroll factor
+    if (L.chains != 1 && L.chains != 8)
+      return set_error(RNG_EINVAL, "tune.unit %u: the strided layout unrolls by 1 or 8", t.unit);
+    if (n % L.depth != 0)
+      return set_error(RNG_EINVAL, "the strided layout needs n = %llu to be a multiple of "
+                                   "tune.depth = %u variates per thread",
+                       (unsigned long long)n, L.depth);
+    const uint64_t threads = n / L.depth;
+    L.block = t.block ? t.block : 512;  // the paper's best block on its GPU
+    if (L.block == 0 || L.block > 1024)
+      return set_error(RNG_EINVAL, "tune.block %u must be in 1..1024", L.block);
+    const uint64_t need = (threads + L.block - 1) / L.block;
+    if (t.grid && (uint64_t)t.grid < need)
+      return set_error(RNG_EINVAL, "tune.grid %u leaves threads of the strided layout out",
+                       t.grid);
+    if (need > 0x7fffffffull) return set_error(RNG_ERANGE, "too many threads for one launch");
+    L.grid = t.grid ? t.grid : (uint32_t)need;
+    L.buffers = 0;
+    L.smem_bytes = 0;
+    if (!pick_strided(dt, L.step, L.conv, L.chains))
+      return set_error(RNG_EINVAL, "no kernel for this combination");
+    *out = L;
+    return RNG_OK;
+  }
   L.chains = 1;
   const uint32_t want_chains = t.chains ? t.chains : kDefChains;
   if (L.layout == RNG_LAYOUT_TILED && (L.step == ST_SHARED || L.step == ST_BARRETT) &&
@@ -152,10 +184,25 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
 
 rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t n,
                        void* out, uint64_t const_bits, cudaStream_t cs) {
-  const void* fn = pick_kernel(L.layout, L.dt, L.step, L.conv, (int)L.chains, L.depth);
-  if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   const uint64_t ebase = (L.step == ST_CONST) ? 0 : host_exponent_base(seed, i0);
   cudaError_t e;
+  if (L.layout == RNG_LAYOUT_STRIDED) {
+    const void* sf = pick_strided(L.dt, L.step, L.conv, L.chains);
+    if (!sf || n % L.depth != 0) return set_error(RNG_EINVAL, "strided launch does not fit n");
+    StridedParams p;
+    p.out = static_cast<unsigned char*>(out);
+    p.nthreads = n / L.depth;
+    p.per = L.depth;
+    p.ebase = ebase;
+    p.cbits = const_bits;
+    p.skip = (uint32_t)L.skip;
+    void* args[] = {&p};
+    e = cudaLaunchKernel(sf, dim3(L.grid), dim3(L.block), args, 0, cs);
+    if (e != cudaSuccess) return cuda_error(e, "strided kernel launch");
+    return RNG_OK;
+  }
+  const void* fn = pick_kernel(L.layout, L.dt, L.step, L.conv, (int)L.chains, L.depth);
+  if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   if (L.layout == RNG_LAYOUT_TILED) {
     DeviceInfo di;
     rng_status st = device_info(&di);

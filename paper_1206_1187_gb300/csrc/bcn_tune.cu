@@ -25,17 +25,18 @@ static bool parse_tune(const char* text, rng_tune* out, char* err, size_t errlen
   static const char* const kSteps[] = {"", "barrett", "montgomery", "shared", "lecuyer",
                                        "barrett_classic"};
   static const char* const kConvs[] = {"", "int", "fp64"};
-  static const char* const kLayouts[] = {"", "tiled", "direct"};
+  static const char* const kLayouts[] = {"", "tiled", "direct", "strided"};
   static const char* const kSkips[] = {"", "table", "sqmul"};
+  typedef uint32_t rng_tune::*Member;
   struct Field {
     const char* key;
-    uint32_t rng_tune::*member;
+    Member member;
     const char* const* names;
     int nnames;
   };
   static const Field kFields[] = {
       {"step", &rng_tune::step, kSteps, 6},       {"conv", &rng_tune::conv, kConvs, 3},
-      {"layout", &rng_tune::layout, kLayouts, 3}, {"skip", &rng_tune::skip, kSkips, 3},
+      {"layout", &rng_tune::layout, kLayouts, 4}, {"skip", &rng_tune::skip, kSkips, 3},
       {"depth", &rng_tune::depth, nullptr, 0},    {"block", &rng_tune::block, nullptr, 0},
       {"grid", &rng_tune::grid, nullptr, 0},      {"unit", &rng_tune::unit, nullptr, 0},
       {"chains", &rng_tune::chains, nullptr, 0},  {"buffers", &rng_tune::buffers, nullptr, 0},
@@ -140,6 +141,8 @@ rng_status rng_parse_tune(const char* text, rng_tune* out) {
 
 rng_status rng_set_auto_tune(rng_dtype dt, const rng_tune* t) {
   if ((int)dt < 0 || (int)dt > 2) return set_error(RNG_EINVAL, "dtype %d", (int)dt);
+  if (t && t->layout == RNG_LAYOUT_STRIDED)
+    return set_error(RNG_EINVAL, "the strided layout permutes the output and cannot be a default");
   std::lock_guard<std::mutex> lock(g_auto_mu);
   if (t) {
     g_auto[dt] = *t;

@@ -31,7 +31,7 @@ STATUS = {0: "RNG_OK", 1: "RNG_EINVAL", 2: "RNG_ERANGE", 3: "RNG_ENOMEM",
 STEP = {"auto": 0, "barrett": 1, "montgomery": 2, "shared": 3, "lecuyer": 4,
         "barrett_classic": 5}
 CONV = {"auto": 0, "int": 1, "fp64": 2}
-LAYOUT = {"auto": 0, "tiled": 1, "direct": 2}
+LAYOUT = {"auto": 0, "tiled": 1, "direct": 2, "strided": 3}
 SKIP = {"auto": 0, "table": 1, "sqmul": 2}
 
 

@@ -369,3 +369,42 @@ def test_host_threads_generate_concurrently(R, oracle_mod):
             n, dt = 200003 + j, ("f64", "f32", "u64")[j % 3]
             assert_same(out, oracle_mod.generate(a, pos, n, dt), f"thread {k} call {j}")
             pos += n
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "u64"])
+def test_paper_strided_layout_matches_the_oracle(R, oracle_mod, dtype):
+    """The paper's coalesced kernels (RNG_LAYOUT_STRIDED): thread t of T makes
+    its block of W variates and writes them T apart.  Every step variant,
+    both conversions, unrolled by 1 and by 8, gives the oracle's permuted
+    order bit for bit."""
+    a, off = M + 7777, 4242
+    per, threads = 64, 1000
+    n = per * threads
+    want = oracle_mod.generate_strided(a, off, n, dtype, per=per)
+    for step in ("shared", "barrett", "montgomery", "lecuyer", "barrett_classic"):
+        for conv in (("int", "fp64") if dtype != "u64" else ("int",)):
+            for unit in (1, 8):
+                t = R.make_tune(step=step, conv=conv, layout="strided", depth=per, unit=unit,
+                                block=96)
+                out = R.generate_at(a, off, n, dtype, tune=t)
+                assert_same(out, want, f"{step} {conv} unroll {unit}")
+
+
+def test_paper_strided_layout_at_the_papers_shape(R, oracle_mod):
+    """4096 variates per thread and 512-thread blocks (the paper's C2050
+    configuration), the constant kernel in the same layout, and the checks:
+    n must be a multiple of W, and no default may take this layout."""
+    a, n = M + 12345, 1 << 22
+    r = R.resolve_tune(n, "f64", R.make_tune(layout="strided"))
+    assert (r["layout"], r["depth"], r["block"], r["grid"]) == ("strided", 4096, 512, 2)
+    out = R.generate_at(a, 0, n, "f64", tune=R.make_tune(layout="strided"))
+    assert_same(out, oracle_mod.generate_strided(a, 0, n, "f64", per=4096), "paper shape")
+    import torch
+    c = R.fill_constant(n, "f32", 0.25, tune=R.make_tune(layout="strided", unit=1))
+    assert bool(torch.all(c == 0.25))
+    with pytest.raises(R.RNGError) as e:
+        R.generate_at(a, 0, n + 3, "f64", tune=R.make_tune(layout="strided"))
+    assert e.value.status == 1
+    with pytest.raises(R.RNGError) as e:
+        R.set_auto_tune("f64", R.make_tune(layout="strided"))
+    assert e.value.status == 1

@@ -240,6 +240,25 @@ def test_threaded_split_matches_single_thread(oracle_mod):
             assert np.array_equal(oracle_mod.generate_mt(a, 11, n, dt, t), one)
 
 
+def test_strided_order_is_the_papers_indexing(oracle_mod):
+    """The coalesced kernels of Sec. 2.2 write a thread's i-th variate at its
+    start index plus i times the step (the number of threads); the oracle's
+    strided order is checked against that indexing written out as loops."""
+    a, j = M + 31337, 99
+    for per, threads in ((4, 3), (8, 5), (16, 1), (1, 7)):
+        n = per * threads
+        seq = oracle_mod.generate(a, j, n, "u64")
+        want = np.zeros(n, dtype=np.uint64)
+        for t in range(threads):            # thread t: start index t, step `threads`
+            for i in range(per):            # its i-th variate, number t*per + i
+                want[t + i * threads] = seq[t * per + i]
+        got = oracle_mod.generate_strided(a, j, n, "u64", per=per)
+        assert np.array_equal(got, want), (per, threads)
+        assert sorted(got.tolist()) == sorted(seq.tolist())  # a permutation
+    with pytest.raises(ValueError):
+        oracle_mod.generate_strided(a, j, 10, "f64", per=4)
+
+
 # ------------------------------------------------------ Monte-Carlo consumer
 def test_mc_matches_python_floats_and_fractions(oracle_mod):
     a = M + 100
