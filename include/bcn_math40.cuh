@@ -111,36 +111,74 @@ __device__ __forceinline__ uint64_t quot40(uint64_t z) {
 // (the dropped partial products z0*Rlo and z1*(Rlo mod 2^32) contribute less
 // than 2^32 + 2^32 + 1 there), so floor(T / 2^64) is the quotient unless the
 // low word f of T lies within 2^34 of 2^64.  Five 32x32->64-bit products in
-// place of the twelve of the exact form.  Returns the quotient estimate and
-// the high word of f; the caller treats fhi >= 0xFFFFFFFC as "not decided"
-// and redoes the work with quot40.
+// place of the twelve of the exact form, summed in 32-bit limbs by
+// add-with-carry chains: limb 0 only passes its carry on, limb 1 is the high
+// word of f, limbs 2-3 the quotient (T < 2^118, so nothing leaves limb 3).
+// Returns the quotient estimate and the high word of f; the caller treats
+// fhi >= 0xFFFFFFFC as "not decided" and redoes the work with quot40.
 __device__ __forceinline__ uint64_t quot40_fast(uint64_t z, uint32_t& fhi) {
   constexpr uint32_t h0 = (uint32_t)k40Rhi, h1 = (uint32_t)(k40Rhi >> 32);
   constexpr uint32_t r1 = (uint32_t)(k40Rlo >> 32);
-  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
-  const uint64_t p00 = (uint64_t)z0 * h0;
-  const uint64_t p01 = (uint64_t)z0 * h1;
-  const uint64_t p10 = (uint64_t)z1 * h0;
-  const uint64_t p11 = (uint64_t)z1 * h1;
-  const uint64_t b = (uint64_t)z1 * r1;
-  const uint64_t lo = p00 + b;
-  const uint64_t c0 = lo < p00 ? 1 : 0;
-  const uint64_t mid = p01 + p10;                  // weight 2^32
-  const uint64_t cm = mid < p10 ? (1ull << 32) : 0;  // its carry, weight 2^96
-  const uint64_t f = lo + (mid << 32);
-  const uint64_t c1 = f < lo ? 1 : 0;
-  fhi = (uint32_t)(f >> 32);
-  return p11 + (mid >> 32) + cm + c0 + c1;
+  const uint32_t a0 = (uint32_t)z, a1 = (uint32_t)(z >> 32);
+  uint32_t s1, s2, s3;
+  asm("{\n\t"
+      ".reg .u32 w0, w1, u0, u1, v0, v1, x0, x1, y0, y1, c2, t0;\n\t"
+      ".reg .u64 w, u, v, x, y;\n\t"
+      "mul.wide.u32 w, %3, %5;\n\t"  // z0*h0     at limbs 0-1
+      "mul.wide.u32 u, %4, %7;\n\t"  // z1*r1     at limbs 0-1
+      "mul.wide.u32 v, %3, %6;\n\t"  // z0*h1     at limbs 1-2
+      "mul.wide.u32 x, %4, %5;\n\t"  // z1*h0     at limbs 1-2
+      "mul.wide.u32 y, %4, %6;\n\t"  // z1*h1     at limbs 2-3
+      "mov.b64 {w0, w1}, w;\n\t"
+      "mov.b64 {u0, u1}, u;\n\t"
+      "mov.b64 {v0, v1}, v;\n\t"
+      "mov.b64 {x0, x1}, x;\n\t"
+      "mov.b64 {y0, y1}, y;\n\t"
+      "add.cc.u32 t0, w0, u0;\n\t"   // limbs 0-1 of the two low products
+      "addc.cc.u32 %0, w1, u1;\n\t"
+      "addc.u32 c2, 0, 0;\n\t"
+      "add.cc.u32 %0, %0, v0;\n\t"   // + z0*h1, z1*h1
+      "addc.cc.u32 %1, v1, y0;\n\t"
+      "addc.u32 %2, y1, 0;\n\t"
+      "add.cc.u32 %0, %0, x0;\n\t"   // + z1*h0
+      "addc.cc.u32 %1, %1, x1;\n\t"
+      "addc.u32 %2, %2, 0;\n\t"
+      "add.cc.u32 %1, %1, c2;\n\t"   // + the first chain's carry into limb 2
+      "addc.u32 %2, %2, 0;\n\t"
+      "}"
+      : "=r"(s1), "=r"(s2), "=r"(s3)
+      : "r"(a0), "r"(a1), "r"(h0), "r"(h1), "r"(r1));
+  fhi = s1;
+  return ((uint64_t)s3 << 32) | s2;
 }
 
 // The variate bits of bits40 when q0 >= 2^32 (a variate of at least 2^-21;
 // the caller routes smaller ones to the exact path): q0's leading one is in
 // its high word, and the digits taken from q1 come from q1's high word only.
+// On 32-bit words: the mantissa's high word is q0 funnel-shifted left by t,
+// its low word q0's low word funnel-shifted over q1's high word (placed at
+// the top of a word), and (1032 - c) << 20, c = t + 11 the leading zeros of
+// q0's high word, puts the exponent on the high word (the mantissa's leading
+// one then lifts it by one).
 __device__ __forceinline__ uint64_t bits40_fast(uint64_t q0, uint64_t q1) {
-  const uint32_t t = (uint32_t)__clz((int)(uint32_t)(q0 >> 32)) - 11u;  // 0..20
-  const uint64_t mant = (q0 << t) | (uint64_t)((uint32_t)(q1 >> 32) >> (21u - t));
-  return ((uint64_t)(1021u - t) << 52) + mant;
+  const uint32_t q0l = (uint32_t)q0, q0h = (uint32_t)(q0 >> 32), q1h = (uint32_t)(q1 >> 32);
+  uint32_t hi, lo;
+  asm("{\n\t"
+      ".reg .u32 c, t, x, mh, ew;\n\t"
+      "clz.b32 c, %3;\n\t"
+      "sub.u32 t, c, 11;\n\t"                 // 0..20
+      "shf.l.clamp.b32 mh, %2, %3, t;\n\t"
+      "shl.b32 x, %4, 11;\n\t"
+      "shf.l.clamp.b32 %1, x, %2, t;\n\t"
+      "shl.b32 ew, c, 20;\n\t"
+      "sub.u32 ew, 0x40800000, ew;\n\t"       // (1032 - c) << 20
+      "add.u32 %0, mh, ew;\n\t"
+      "}"
+      : "=r"(hi), "=r"(lo)
+      : "r"(q0l), "r"(q0h), "r"(q1h));
+  return ((uint64_t)hi << 32) | lo;
 }
+static_assert((1032u << 20) == 0x40800000u, "exponent constant of bits40_fast");
 
 // Eq. 3 with the quotient q of z: 2^53 z - q 3^40, which lies in [1, 3^40),
 // so arithmetic modulo 2^64 gives it exactly.

@@ -246,3 +246,78 @@ def test_fast_conversion_matches_the_exact_one():
         q1 = (z1 << 53) // M40
         assert bits_fast_model(q0, q1) == bits_model(q0, q1), z
         assert f64_from_bits(bits_fast_model(q0, q1)) == trunc_quotient(z)
+
+
+def quot_fast_chain_model(z):
+    """The same T from the same five products, summed in 32-bit limbs with
+    add-with-carry chains (the kernel's PTX form): limb 0 only feeds its
+    carry, limb 1 is the high word of T mod 2^64, limbs 2-3 the quotient."""
+    m32 = 0xFFFFFFFF
+    a0, a1 = z & m32, z >> 32
+    h0, h1, r1 = H0, H1, RL1
+    w = a0 * h0
+    u = a1 * r1
+    v = a0 * h1
+    x = a1 * h0
+    y = a1 * h1
+    w0, w1, u0, u1 = w & m32, w >> 32, u & m32, u >> 32
+    v0, v1, x0, x1, y0, y1 = v & m32, v >> 32, x & m32, x >> 32, y & m32, y >> 32
+
+    def addc(p, q, cin):  # one 32-bit add with carry in and out
+        s = p + q + cin
+        return s & m32, s >> 32
+
+    _, c = addc(w0, u0, 0)           # chain A: limb 0, limb 1, carry into limb 2
+    s1, c = addc(w1, u1, c)
+    c2, _ = addc(0, 0, c)
+    s1, c = addc(s1, v0, 0)          # chain B: + a0*h1 at limb 1, + a1*h1 at limb 2
+    s2, c = addc(v1, y0, c)
+    s3, _ = addc(y1, 0, c)
+    s1, c = addc(s1, x0, 0)          # chain C: + a1*h0 at limb 1
+    s2, c = addc(s2, x1, c)
+    s3, _ = addc(s3, 0, c)
+    s2, c = addc(s2, c2, 0)          # chain D: chain A's carry into limb 2
+    s3, _ = addc(s3, 0, c)
+    assert s3 < 2 ** 32              # T < 2^118: no carry out of limb 3
+    return (s3 << 32) | s2, s1
+
+
+def test_fast_quotient_carry_chains_match():
+    zs = states(40000, 17) + undecided_states(300) + [2 ** 64 - 1, M40 - 1, 2 ** 63,
+                                                      (2 ** 32 - 1) << 32, 2 ** 32 - 1]
+    for z in zs:
+        assert quot_fast_chain_model(z) == quot_fast_model(z), z
+
+
+def bits_fast_funnel_model(q0, q1):
+    """bits40_fast on 32-bit words (the kernel's PTX form): the mantissa's
+    high word is a funnel shift of q0's words by t, its low word a funnel
+    shift of q0's low word over q1's high word placed at the top of a word,
+    and the exponent joins the high word."""
+    m32 = 0xFFFFFFFF
+    q0l, q0h, q1h = q0 & m32, q0 >> 32, q1 >> 32
+
+    def shf_l(lo, hi, s):  # high word of (hi:lo) << s, s in [0, 31]
+        return (((hi << 32) | lo) << s >> 32) & m32
+
+    c = 32 - q0h.bit_length()
+    t = c - 11
+    mh = shf_l(q0l, q0h, t)
+    ml = shf_l((q1h << 11) & m32, q0l, t)
+    hi = (mh + ((1032 - c) << 20)) & m32
+    return (hi << 32) | ml
+
+
+def test_fast_conversion_funnel_form_matches():
+    for z in states(30000, 19):
+        q0 = (z << 53) // M40
+        if q0 < 2 ** 32:
+            continue
+        q1 = ((((z << 53) - q0 * M40)) << 53) // M40
+        assert bits_fast_funnel_model(q0, q1) == bits_fast_model(q0, q1), z
+    for t in range(21):  # every shift, with extreme low words
+        for q0l in (0, 1, 0xFFFFFFFF, 0x80000000):
+            for q1h in (0, 1, (1 << 21) - 1, 1 << 20):
+                q0 = ((1 << (20 - t)) << 32) | q0l
+                q1 = q1h << 32
+                assert bits_fast_funnel_model(q0, q1) == bits_fast_model(q0, q1), (t, q0l, q1h)
