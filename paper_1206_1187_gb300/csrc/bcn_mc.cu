@@ -97,6 +97,17 @@ __device__ __forceinline__ Terms variate_terms_fp64(uint64_t bits) {
   return t;
 }
 
+// The fast-grid image of RN(v*v) for a variate v >= 2^-20, as every variate
+// of a kept chunk is: RN(v*v) >= 2^-40, so its image on the 2^-157 grid is
+// M2 << k with k = e2 - 918 >= 65, and RN(v*v) * 2^93 = M2 << (e2 - 982)
+// exactly, with no branch on the square's size.
+__device__ __forceinline__ void square_fast_fp64(uint64_t bits, uint64_t& q0, uint64_t& q1) {
+  const double v = __longlong_as_double((long long)bits);
+  const uint64_t sb = (uint64_t)__double_as_longlong(__dmul_rn(v, v));
+  const uint64_t m2 = (sb & ((1ull << 52) - 1)) | (1ull << 52);
+  shl128(m2, (uint32_t)(sb >> 52) - 982u, q0, q1);
+}
+
 // hits += [ (r1:r0) <= (lim1:lim0) ]: the borrow of (r1:r0) - (lim1:lim0) - 1
 // (one subtract-with-borrow chain instead of three 64-bit compares).
 __device__ __forceinline__ void count_hit(uint32_t& hits, uint64_t r0, uint64_t r1,
@@ -195,6 +206,19 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
     auto pair = [&](bool exact, uint32_t& qmin) {
       const uint64_t bx = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
       const uint64_t by = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
+      if constexpr (FP64SQ) {
+        if (!exact) {  // a kept chunk: both squares on the fast grid, no branch
+          uint64_t xq0, xq1, yq0, yq1;
+          square_fast_fp64(bx, xq0, xq1);
+          square_fast_fp64(by, yq0, yq1);
+          add_variate_fast(a0, a1, bx);
+          add_variate_fast(a0, a1, by);
+          add128(xq0, xq1, yq0, yq1);
+          count_hit(hits, xq0, xq1, lim0 + 1, lim1);
+          add128(h0, h1, xq0, xq1);
+          return;
+        }
+      }
       const Terms x = FP64SQ ? variate_terms_fp64(bx) : variate_terms(bx);
       const Terms y = FP64SQ ? variate_terms_fp64(by) : variate_terms(by);
       if (exact) {
@@ -217,8 +241,10 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
       }
     };
     // Chunks of kChunk pairs with the branch-free conversion; a lane whose
-    // chunk met a variate below 2^-21 (about one chunk in 2^14) restores the
-    // chunk's starting point and redoes it exactly.
+    // chunk met a variate below 2^-20 (a quotient window below 2^33, about
+    // one chunk in 2^13) restores the chunk's starting point and redoes it
+    // exactly.  Every variate of a kept chunk is then at least 2^-20, so its
+    // square lies on the fast grid and its image has a zero low word.
     constexpr uint32_t kChunk = 64;
     uint64_t j = j0;
     for (; j + kChunk <= j1; j += kChunk) {
@@ -227,7 +253,7 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
       uint32_t qmin = 0xffffffffu;
 #pragma unroll 4
       for (uint32_t k = 0; k < kChunk; ++k) pair(false, qmin);
-      if (__builtin_expect(qmin == 0, 0)) {
+      if (__builtin_expect(qmin < 2, 0)) {
         z = zs; a0 = sa0; a1 = sa1; h0 = sh0; h1 = sh1; l0 = sl0; l1 = sl1; hits = shits;
         uint32_t unused = 0;
         for (uint32_t k = 0; k < kChunk; ++k) pair(true, unused);

@@ -414,3 +414,27 @@ def test_fp64_pipe_conversion_by_one_fused_multiply_add():
         exact = Fraction(d) * Fraction(R3I) + off
         assert exact == Fraction(z) * Fraction(R3I)
         assert f64_bits(float(exact)) == rn_bits(z)  # one rounding of the same value
+
+
+def test_fused_chunk_rule_makes_every_square_fast():
+    """A fused-consumer chunk is kept when the top word of every step's 53-bit
+    quotient window is at least 2 (q >= 2^33): then z*r3i >= 2^-20, so
+    v = RN(z*r3i) >= 2^-20 and RN(v*v) >= 2^-40, whose exponent puts its
+    2^-157-grid image at least 2^64 up (k = e2 - 918 >= 65): every square of
+    a kept chunk takes the fast (exact 2^-93 grid) form.  At 2^-21 that
+    would fail (k = 63 occurs)."""
+    edge = ((2 ** 33) * M) >> 53  # states around the 2^-20 boundary
+    kept = 0
+    for z in states(30000, 23) + [edge + d for d in range(-3, 4)]:
+        if not 0 < z < M:
+            continue
+        q = (z * K) >> 53  # the step's 53-bit quotient window, floor(z*K / 2^53)
+        v = float(Fraction(z) * Fraction(R3I))
+        e2 = f64_bits(v * v) >> 52
+        if q >> 32 >= 2:
+            kept += 1
+            assert Fraction(z) * Fraction(R3I) >= Fraction(1, 2 ** 20)
+            assert v >= 2.0 ** -20 and e2 - 918 >= 65
+    assert kept > 29000
+    v21 = 2.0 ** -21
+    assert (f64_bits(v21 * v21) >> 52) - 918 == 63
