@@ -27,6 +27,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -39,6 +41,13 @@ N_DEFAULT = 1 << 28
 WORKLOAD = ("single stream, start index a = 3^33+12345, n = 2^28 FP64 uniforms (2 GiB) "
             "per GPU per step; rank r generates variates r*n..(r+1)*n-1 of the sequence")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+E2E_INPUT_BYTES = 3 * 8  # seed, offset, n: the only inputs of a generation step
+L2_NOTE = "each step writes 2 GiB (> 126 MB L2); no flush needed"
+
+
+def workload_config(n: int) -> dict:
+    """The `config` object of the JSON line, identical for both arms."""
+    return {"workload": WORKLOAD, "n": n, "seed": SEED, "l2": L2_NOTE}
 
 
 def parse_args():
@@ -212,6 +221,119 @@ def cpu_baseline(seconds: float, dtype: str = "f64"):
                       f"{dt:.2f} s wall",
             "single_thread": {"value": one / dt1, "unit": UNIT, "cores": 1,
                               "sample": f"first {one} variates, one thread"}}
+
+
+def _on_host_threads(fn, tasks, cores: int) -> float:
+    """Run fn(task) for every task on `cores` host threads (the oracle's C calls
+    release the interpreter lock); returns the wall time in seconds."""
+    import concurrent.futures
+    t = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(fn, tasks))
+    return time.perf_counter() - t
+
+
+def _chunks(lo: int, hi: int, parts: int):
+    return [(lo + (hi - lo) * k // parts, lo + (hi - lo) * (k + 1) // parts)
+            for k in range(parts)]
+
+
+def cpu_baseline_batched(nsample: int = 64):
+    """The oracle on the first `nsample` streams of the batched workload, one
+    stream per task on all host cores; extrapolated to the 4096 streams."""
+    import oracle
+    from paper_1206_1187_gb300 import inputs
+    starts, counts, dtypes = inputs.batch_streams()
+    cores = os.cpu_count() or 1
+    # each stream cut into pieces of at most 2^20 variates (skip-ahead), so that
+    # the long streams spread over all threads
+    piece = 1 << 20
+    tasks = [(s, lo, min(lo + piece, int(counts[s]))) for s in range(nsample)
+             for lo in range(0, int(counts[s]), piece)]
+    dt = _on_host_threads(lambda t: oracle.generate(int(starts[t[0]]), t[1], t[2] - t[1],
+                                                    dtypes[t[0]]), tasks, cores)
+    done = int(sum(int(counts[s]) for s in range(nsample)))
+    total = int(counts.astype(np.float64).sum())
+    rate = done / dt
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"streams 0..{nsample - 1} of the 4096 ({done} variates, FP64/FP32 "
+                      f"alternating), in pieces of up to 2^20 on {cores} threads; {dt:.2f} s wall",
+            "extrapolated_s_for_4096_streams": total / rate}
+
+
+def cpu_baseline_fused():
+    """The oracle's fused statistics on the parity subsample of the fused
+    workload: blocks 0, 4096, 8192, ... (256 blocks x 2^16 = 2^24 variates)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    a, length = 3 ** 33 + 100, 1 << 16
+    blocks = np.arange(0, 1 << 20, 4096, dtype=np.uint64)
+    parts = [blocks[lo:hi] for lo, hi in _chunks(0, blocks.size, cores) if hi > lo]
+    dt = _on_host_threads(lambda b: oracle.mc(a, length, b), parts, cores)
+    variates = blocks.size * length
+    rate = variates / dt
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{blocks.size} blocks (every 4096th) x 2^16 = {variates} variates of "
+                      f"the 2^36, split over {cores} threads; {dt:.2f} s wall",
+            "extrapolated_s_for_2e36": (1 << 36) / rate}
+
+
+def cpu_baseline_m40(seconds: float = 4.0):
+    """The 3^40 oracle on a prefix of the 3^40 workload, split over all host
+    cores by offset (skip-ahead)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    a = 3 ** 40 + 12345
+    trial = 1 << 16
+    t = time.perf_counter()
+    oracle.generate40(a, 0, trial, "f64")
+    rate1 = trial / max(time.perf_counter() - t, 1e-9)
+    n = int(min(max(rate1 * cores * seconds, 1 << 20), 1 << 28))
+    dt = _on_host_threads(lambda r: oracle.generate40(a, r[0], r[1] - r[0], "f64"),
+                          _chunks(0, n, cores), cores)
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} FP64 variates of a = 3^40+12345, split over {cores} threads "
+                      f"by offset; {dt:.2f} s wall",
+            "extrapolated_s_for_2e28": (1 << 28) / (n / dt)}
+
+
+def measure_config1(rng, stream, steps: int):
+    """The small single-stream case (a = 3^33+100, n = 10^6 FP64, 8 MB), which
+    fits in L2 and is launch-bound: device rate, and the oracle on the host."""
+    import torch
+    a, n = 3 ** 33 + 100, 10 ** 6
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        rng.generate_at(a, 0, n, "f64", out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rng.generate_at(a, 0, n, "f64", out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "single stream a = 3^33+100, n = 10^6 FP64 (8 MB, fits in L2; "
+                        "back-to-back launches without a flush)",
+            "launches": steps, "ms_per_launch": ms, "variates_per_s": n / (ms / 1e3)}
+
+
+def cpu_baseline_config1():
+    """The oracle on the whole small single-stream case, on all host cores and on one."""
+    import oracle
+    a, n = 3 ** 33 + 100, 10 ** 6
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    oracle.generate(a, 0, n, "f64")
+    dt1 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.generate_mt(a, 0, n, "f64", threads=cores)
+    dtn = time.perf_counter() - t
+    return {"value": n / dtn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the whole workload, {cores} threads; {dtn:.3f} s",
+            "single_thread": {"value": n / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"the whole workload; {dt1:.3f} s"}}
 
 
 def measure_batched(rng, stream, achieved_gbs: float, steps: int):
@@ -488,8 +610,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": args.n, "seed": SEED,
-                   "sample_per_step": sample},
+        "config": workload_config(args.n),
+        "sample_per_step": sample,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{sample} consecutive FP64 variates of the workload's "
                                    f"stream per step, {cores} threads"},
@@ -605,7 +727,9 @@ def run_ours(args):
     e2e_s = shard.max_over_ranks(statistics.median(step_s), device=dev)
     copy_gbs = 8.0 * n / statistics.median(copy_s) / 1e9
     e2e_gbs = 8.0 * n / e2e_s / 1e9
-    e2e = {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+    e2e = {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": E2E_INPUT_BYTES,
+           "h2d_what": "the step's whole input: seed, offset and n (three 8-byte scalars), "
+                       "passed by value as kernel parameters with the launches",
            "d2h_bytes_per_step": 8 * n, "d2h_GBps": e2e_gbs,
            "d2h_copy_ceiling_GBps": copy_gbs, "frac_of_d2h_copy": e2e_gbs / copy_gbs,
            "steps": e2e_steps, "step_ms": [round(x * 1e3, 3) for x in step_s],
@@ -636,6 +760,20 @@ def run_ours(args):
                                   steps=max(min(args.steps // 20, 50), 5))
 
 
+    config1 = None
+    if rank == 0:
+        config1 = measure_config1(rng, stream, steps=max(min(args.steps, 50), 5))
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle beside every form, on bounded samples of each workload
+        if batched is not None:
+            batched["cpu_baseline"] = cpu_baseline_batched()
+        if fused is not None:
+            fused["cpu_baseline"] = cpu_baseline_fused()
+        if m40 is not None:
+            m40["cpu_baseline"] = cpu_baseline_m40()
+        if config1 is not None:
+            config1["cpu_baseline"] = cpu_baseline_config1()
+
     if rank == 0:
         peaks = load_peaks()
         bytes_per_launch = 8.0 * n
@@ -652,8 +790,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64", "output_dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "seed": SEED, "tune": tune,
-                       "l2": "each step writes 2 GiB (> 126 MB L2); no flush needed"},
+            "config": workload_config(n),
+            "tune": tune,
             "roofline": roofline,
             "write_ceiling": {"kernel": "constant fill, same tiled store path (Sec. 3.2), "
                                         "better of two tile shapes",
@@ -664,6 +802,8 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
+        if config1 is not None:
+            line["config_1e6"] = config1
         if batched is not None:
             line["batched"] = batched
         if fused is not None:

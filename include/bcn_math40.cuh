@@ -106,52 +106,6 @@ __device__ __forceinline__ uint64_t quot40(uint64_t z) {
   return ahi + (alo + bhi < alo ? 1 : 0);
 }
 
-// The quotient's fast form.  T = z*Rhi + z1*r1, with z1 and r1 the high
-// 32-bit words of z and Rlo, falls short of z*R / 2^64 by less than 2^33 + 2
-// (the dropped partial products z0*Rlo and z1*(Rlo mod 2^32) contribute less
-// than 2^32 + 2^32 + 1 there), so floor(T / 2^64) is the quotient unless the
-// low word f of T lies within 2^34 of 2^64.  Five 32x32->64-bit products in
-// place of the twelve of the exact form, summed in 32-bit limbs by
-// add-with-carry chains: limb 0 only passes its carry on, limb 1 is the high
-// word of f, limbs 2-3 the quotient (T < 2^118, so nothing leaves limb 3).
-// Returns the quotient estimate and the high word of f; the caller treats
-// fhi >= 0xFFFFFFFC as "not decided" and redoes the work with quot40.
-__device__ __forceinline__ uint64_t quot40_fast(uint64_t z, uint32_t& fhi) {
-  constexpr uint32_t h0 = (uint32_t)k40Rhi, h1 = (uint32_t)(k40Rhi >> 32);
-  constexpr uint32_t r1 = (uint32_t)(k40Rlo >> 32);
-  const uint32_t a0 = (uint32_t)z, a1 = (uint32_t)(z >> 32);
-  uint32_t s1, s2, s3;
-  asm("{\n\t"
-      ".reg .u32 w0, w1, u0, u1, v0, v1, x0, x1, y0, y1, c2, t0;\n\t"
-      ".reg .u64 w, u, v, x, y;\n\t"
-      "mul.wide.u32 w, %3, %5;\n\t"  // z0*h0     at limbs 0-1
-      "mul.wide.u32 u, %4, %7;\n\t"  // z1*r1     at limbs 0-1
-      "mul.wide.u32 v, %3, %6;\n\t"  // z0*h1     at limbs 1-2
-      "mul.wide.u32 x, %4, %5;\n\t"  // z1*h0     at limbs 1-2
-      "mul.wide.u32 y, %4, %6;\n\t"  // z1*h1     at limbs 2-3
-      "mov.b64 {w0, w1}, w;\n\t"
-      "mov.b64 {u0, u1}, u;\n\t"
-      "mov.b64 {v0, v1}, v;\n\t"
-      "mov.b64 {x0, x1}, x;\n\t"
-      "mov.b64 {y0, y1}, y;\n\t"
-      "add.cc.u32 t0, w0, u0;\n\t"   // limbs 0-1 of the two low products
-      "addc.cc.u32 %0, w1, u1;\n\t"
-      "addc.u32 c2, 0, 0;\n\t"
-      "add.cc.u32 %0, %0, v0;\n\t"   // + z0*h1, z1*h1
-      "addc.cc.u32 %1, v1, y0;\n\t"
-      "addc.u32 %2, y1, 0;\n\t"
-      "add.cc.u32 %0, %0, x0;\n\t"   // + z1*h0
-      "addc.cc.u32 %1, %1, x1;\n\t"
-      "addc.u32 %2, %2, 0;\n\t"
-      "add.cc.u32 %1, %1, c2;\n\t"   // + the first chain's carry into limb 2
-      "addc.u32 %2, %2, 0;\n\t"
-      "}"
-      : "=r"(s1), "=r"(s2), "=r"(s3)
-      : "r"(a0), "r"(a1), "r"(h0), "r"(h1), "r"(r1));
-  fhi = s1;
-  return ((uint64_t)s3 << 32) | s2;
-}
-
 // The variate bits of bits40 when q0 >= 2^32 (a variate of at least 2^-21;
 // the caller routes smaller ones to the exact path): q0's leading one is in
 // its high word, and the digits taken from q1 come from q1's high word only.
@@ -225,6 +179,57 @@ __device__ __forceinline__ uint64_t bits40(uint64_t q0, uint64_t q1) {
   const uint32_t t = (uint32_t)__clzll((long long)q0) - 11u;
   const uint64_t mant = (q0 << t) | (q1 >> (53u - t));  // in [2^52, 2^53)
   return ((uint64_t)(1021u - t) << 52) + mant;          // the leading one lifts the exponent
+}
+
+// Eq. 3 run backwards (Montgomery-style, R = 2^53) with its exact quotient.
+// For consecutive states z_(k-1), z_k = 2^53 z_(k-1) - Q 3^40 with
+// Q = floor(2^53 z_(k-1) / 3^40) < 2^53:
+//   Q = (z_k * m') mod 2^53                      (m' = -3^-40 mod 2^53),
+//   z_(k-1) = (z_k + Q 3^40) / 2^53              (an exact division).
+// So one step back yields the previous state and the quotient digit that
+// the forward step would have had to estimate: no undecided band.  S = z_k +
+// Q 3^40 < 2^117 is summed on 32-bit limbs.  Its low 53 bits are zero, so
+// limb 0 is zero and carries 1 into limb 1 exactly when the low word of z_k
+// is non-zero (the low word of Q 3^40 then being its complement), and the
+// product's own low word is never formed.
+constexpr uint64_t k40Mp = (0 - inv_mod_2_64(k40M)) & kMask53;  // -3^-40 mod 2^53
+static_assert(((k40M * k40Mp + 1) & kMask53) == 0, "3^40 * m' = -1 mod 2^53");
+__device__ __forceinline__ uint64_t back40(uint64_t z, uint64_t& q) {
+  constexpr uint32_t mp0 = (uint32_t)k40Mp, mp1 = (uint32_t)(k40Mp >> 32);
+  constexpr uint32_t m0 = (uint32_t)k40M, m1 = (uint32_t)(k40M >> 32);
+  uint32_t r0, r1, u0, u1;
+  // outputs are written last: no output register may share an input's
+  asm("{\n\t"
+      ".reg .u32 a0, a1, q0, q1, th, h0, x, l1, l2, l3;\n\t"
+      ".reg .u64 t;\n\t"
+      "mov.u32 a0, %4;\n\t"
+      "mov.u32 a1, %5;\n\t"
+      "mul.wide.u32 t, a0, %6;\n\t"            // Q = z m' mod 2^53
+      "mov.b64 {q0, th}, t;\n\t"
+      "mad.lo.u32 th, a0, %7, th;\n\t"
+      "mad.lo.u32 th, a1, %6, th;\n\t"
+      "and.b32 q1, th, 0x1FFFFF;\n\t"
+      "mul.hi.u32 h0, q0, %8;\n\t"             // S = z + Q m from limb 1 up
+      "add.cc.u32 x, a0, 0xFFFFFFFF;\n\t"      // carry = (low word of z != 0)
+      "addc.cc.u32 l1, h0, a1;\n\t"
+      "addc.u32 l2, 0, 0;\n\t"
+      "mad.lo.cc.u32 l1, q0, %9, l1;\n\t"
+      "madc.hi.cc.u32 l2, q0, %9, l2;\n\t"
+      "addc.u32 l3, 0, 0;\n\t"
+      "mad.lo.cc.u32 l1, q1, %8, l1;\n\t"
+      "madc.hi.cc.u32 l2, q1, %8, l2;\n\t"
+      "addc.u32 l3, l3, 0;\n\t"
+      "mad.lo.cc.u32 l2, q1, %9, l2;\n\t"
+      "madc.hi.u32 l3, q1, %9, l3;\n\t"
+      "shf.r.clamp.b32 %0, l1, l2, 21;\n\t"    // z_(k-1) = S >> 53
+      "shf.r.clamp.b32 %1, l2, l3, 21;\n\t"
+      "mov.u32 %2, q0;\n\t"
+      "mov.u32 %3, q1;\n\t"
+      "}"
+      : "=r"(r0), "=r"(r1), "=r"(u0), "=r"(u1)
+      : "r"((uint32_t)z), "r"((uint32_t)(z >> 32)), "n"(mp0), "n"(mp1), "n"(m0), "n"(m1));
+  q = ((uint64_t)u1 << 32) | u0;
+  return ((uint64_t)r1 << 32) | r0;
 }
 
 // A variate below 2^-53 (q0 == 0, about once in 2^53 variates): its leading

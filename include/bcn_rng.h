@@ -302,7 +302,9 @@ rng_status rng40_resolve_tune(uint64_t n, rng_dtype dt, const rng_tune *tune, rn
  * sequence seeded with a start index, as rng_generate_at) whose outputs are
  * placed in one device pool the server owns.  A scheduler thread admits
  * waiting requests in arrival order when a request slot is free and the pool
- * has room for the output (memory-based admission), packs the next chunk of
+ * has room for the output (memory-based admission; a request that does not
+ * fit may be passed by later ones that do for up to admit_bypass_s seconds,
+ * after which nothing passes it until it is admitted), packs the next chunk of
  * every admitted request into one work table per iteration and launches the
  * batched kernel, with up to `inflight` iterations on separate CUDA streams so
  * work admitted later overlaps earlier work on the device.  Each chunk is a
@@ -327,12 +329,26 @@ typedef struct {
                               for light iterations, deep tiles in wide blocks
                               (one buffer per warp) once an iteration holds two
                               such tiles for every warp of the GPU            */
+  double admit_bypass_s;   /* how long a queued request that does not fit the
+                              pool may be passed by later requests that do:
+                              > 0 that many seconds; < 0 never (strict arrival
+                              order); 0 = 0.05 s when release_after_s >= 0,
+                              never when the caller releases results (a client
+                              consuming results in order could otherwise wait
+                              on a request whose space is held by unreleased
+                              requests that passed it)                       */
 } rng_server_config;
 
 typedef struct {
   uint64_t submitted, completed, iterations, items, max_items_seen;
   uint64_t peak_active, peak_pool_bytes, bytes_done, pool_in_use, pool_bytes;
   uint64_t heavy_iterations;  /* iterations launched with the throughput shape */
+  uint64_t admitted_out_of_order; /* admissions that passed a waiting request  */
+  uint64_t bypassed;          /* admission passes that found the oldest waiting
+                                 request too large for the pool and went on   */
+  uint64_t loop_gap_max_us;   /* longest interval between two passes of the
+                                 scheduler loop, its own idle waits excluded  */
+  uint64_t launch_max_us;     /* longest staging + launch of one iteration    */
 } rng_server_stats;
 
 /* Request states reported by rng_server_status. */
@@ -361,10 +377,17 @@ rng_status rng_server_status(bcn_server *s, uint64_t id, int *state, double *lat
 /* Block until the request is done (RNG_ETIMEOUT after timeout_s). */
 rng_status rng_server_wait(bcn_server *s, uint64_t id, double timeout_s);
 /* Copy a done request's result (n elements of its dtype) to `dst` (host or
- * device memory of at least dst_bytes); synchronous. */
+ * device memory of at least dst_bytes); synchronous.  The result's pool range
+ * stays the request's until the copy returns: a release that falls due during
+ * the copy (release_after_s >= 0, or rng_server_release from another thread)
+ * takes effect when it ends. */
 rng_status rng_server_read(bcn_server *s, uint64_t id, void *dst, uint64_t dst_bytes);
-/* The device address of a done request's result inside the pool (valid until
- * it is released). */
+/* The device address of a done request's result inside the pool, valid until
+ * the request is released.  With release_after_s >= 0 the server releases it
+ * release_after_s seconds after completion, whatever the caller is doing with
+ * the address; callers that keep the address use release_after_s < 0 and
+ * rng_server_release, or rng_server_read, which holds the range while it
+ * copies. */
 rng_status rng_server_result_ptr(bcn_server *s, uint64_t id, void **dev_ptr);
 /* Free a done request's pool range now. */
 rng_status rng_server_release(bcn_server *s, uint64_t id);
@@ -427,6 +450,34 @@ rng_status rng_pool_destroy(bcn_pool *p);
 rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblocks, uint64_t len,
                           uint64_t *hits_total, uint64_t *hits, double *sum, double *sumsq,
                           void *cuda_stream, const rng_tune *tune);
+
+/* rng_consume_mc that also returns the call's exact totals over all its
+ * blocks in a form that adds without rounding across calls, GPUs and
+ * processes -- the one exchange the paper's parallel split (Sec. 1) needs
+ * when the blocks of one sequence are spread over ranks: the ranks add their
+ * word arrays element by element (an integer all-reduce, exact and
+ * order-free) and round once with rng_mc_round_totals.
+ *   totals: caller-owned device array of RNG_MC_TOTAL_WORDS uint64 words,
+ *   8-byte aligned (NULL: plain rng_consume_mc), zeroed by the call.  For
+ *   k < 4, word k is the sum over the call's blocks of bits 32k..32k+31 of
+ *   the block's exact sum of v * 2^105; for k < 6, word 4+k the same of the
+ *   block's exact sum of RN(v*v) * 2^157.  So the words T stand for
+ *     sum of v      = (T[0] + T[1] 2^32 + T[2] 2^64 + T[3] 2^96) * 2^-105,
+ *     sum of RN(v^2) = (T[4] + T[5] 2^32 + ... + T[9] 2^160) * 2^-157.
+ *   Each word gains less than 2^32 per block, so word arrays stay exact for
+ *   up to 2^32 blocks in all (a call of more blocks is RNG_ERANGE).
+ * Other arguments, outputs and errors as rng_consume_mc. */
+#define RNG_MC_TOTAL_WORDS 10
+rng_status rng_consume_mc_totals(uint64_t start_index, uint64_t block0, uint64_t nblocks,
+                                 uint64_t len, uint64_t *hits_total, uint64_t *hits, double *sum,
+                                 double *sumsq, uint64_t *totals, void *cuda_stream,
+                                 const rng_tune *tune);
+
+/* Host only: round a totals word array (one call's, or the element-wise sum
+ * of several calls' arrays, which must stay within 2^32 blocks in all) to
+ * *sum = RN(exact sum of the variates) and *sumsq = RN(exact sum of their
+ * RN(v*v)), round-to-nearest-even.  RNG_EINVAL for a NULL pointer. */
+rng_status rng_mc_round_totals(const uint64_t *totals, double *sum, double *sumsq);
 
 /* Run a kernel written only against the device-side API (bcn_device.cuh):
  * `threads` threads each create their own generator at their first variate

@@ -41,7 +41,10 @@ def bulk_candidates(dtype: str) -> list[dict]:
     # wide blocks: with one tile buffer per warp, up to 28 warps of depth-31 tiles
     # share an SM's shared memory
     if dtype != "u64":
-        for depth, blocks in ((15, (768, 1024)), (31, (640, 768, 896))):
+        wide = [(15, (768, 1024)), (31, (640, 768, 896))]
+        if dtype == "f32":  # FP32 tiles are half the bytes: deeper ones fit
+            wide += [(47, (768, 896, 1024)), (63, (512, 640, 768, 896))]
+        for depth, blocks in wide:
             for block in blocks:
                 cands.append(dict(step="shared", conv="int", layout="tiled", depth=depth,
                                   block=block, chains=2, buffers=1))

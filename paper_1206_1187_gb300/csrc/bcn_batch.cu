@@ -60,11 +60,15 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const
   if (ntiles > 0) {
     const uint64_t first = s0 + (uint64_t)lane * c;
     if constexpr (ILP == 2) {
-      Gen<DT, STEP, CONV> a = lane_chain<DT, STEP, CONV>(d.ebase, first, c, p.skip);
-      Gen<DT, STEP, CONV> b = lane_chain<DT, STEP, CONV>(d.ebase, first + c / 2 + 1, c, p.skip);
-      warp_tiles2<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.jump_a, p.jump_aq, p.jump_b,
-                                          p.jump_bq, a, b, reinterpret_cast<W*>(buf0_bytes),
-                                          issued, lane, p.nbuf);
+      Gen<DT, STEP, CONV> a{0}, b{0};
+      lane_chains2<DT, STEP, CONV>(d.ebase, first, c, p.skip, a, b);
+      constexpr bool back = kBackF32<DT, STEP, CONV>;
+      warp_tiles2<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, back ? p.back_a : p.jump_a,
+                                          back ? p.back_aq : p.jump_aq,
+                                          back ? p.back_b : p.jump_b,
+                                          back ? p.back_bq : p.jump_bq, a, b,
+                                          reinterpret_cast<W*>(buf0_bytes), issued, lane,
+                                          p.nbuf);
     } else {
       Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(d.ebase, first, c, p.skip);
       warp_tiles<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.jump, p.jump_q, g,
@@ -139,11 +143,14 @@ void batch_fill_jumps(BatchParams& p, int step, uint32_t depth) {
   const uint64_t stride = (step == ST_MONT) ? 33ull : 31ull;
   p.jump = host_pow2((53ull * stride * depth) % kP);
   p.jump_q = host_mulmod_quotient(p.jump);
-  const uint64_t h = depth / 2;
-  p.jump_a = host_pow2((53ull * (32ull * depth - h - 1)) % kP);
+  p.jump_a = host_pow2((53ull * chain_jump_a(false, depth)) % kP);
   p.jump_aq = host_mulmod_quotient(p.jump_a);
-  p.jump_b = host_pow2((53ull * (31ull * depth + h + 1)) % kP);
+  p.jump_b = host_pow2((53ull * chain_jump_b(false, depth)) % kP);
   p.jump_bq = host_mulmod_quotient(p.jump_b);
+  p.back_a = host_pow2((53ull * chain_jump_a(true, depth)) % kP);
+  p.back_aq = host_mulmod_quotient(p.back_a);
+  p.back_b = host_pow2((53ull * chain_jump_b(true, depth)) % kP);
+  p.back_bq = host_mulmod_quotient(p.back_b);
 }
 
 static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {

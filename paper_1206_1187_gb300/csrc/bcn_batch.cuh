@@ -22,6 +22,7 @@ struct BatchParams {
   uint64_t jump;
   uint64_t jump_q;       // floor(jump * 2^64 / m)
   uint64_t jump_a, jump_aq, jump_b, jump_bq;  // two chains per lane
+  uint64_t back_a, back_aq, back_b, back_bq;  // two backward FP32 chains per lane
   uint32_t nstreams;
   uint32_t depth;
   uint32_t unit_tiles;

@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
     const uint64_t first = p.head + t0 * tile_elems + (uint64_t)lane * c;
     uint32_t issued = 0;
     if constexpr (ILP == 2) {
-      Gen<DT, STEP, CONV> a = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
-      Gen<DT, STEP, CONV> b = lane_chain<DT, STEP, CONV>(p.ebase, first + c / 2 + 1, c, p.skip);
+      Gen<DT, STEP, CONV> a{0}, b{0};
+      lane_chains2<DT, STEP, CONV>(p.ebase, first, c, p.skip, a, b);
       warp_tiles2<DT, STEP, CONV, CDEPTH>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump_a,
                                           p.jump_aq, p.jump_b, p.jump_bq, a, b, buf0, issued,
                                           lane, p.nbuf);
@@ -94,6 +94,10 @@ static const void* pick_ilp(int layout, int ilp, uint32_t depth) {
       if (depth == 9) return (const void*)tiled_kernel<DT, ST, CV, 2, 9>;
       if (depth == 15) return (const void*)tiled_kernel<DT, ST, CV, 2, 15>;
       if (depth == 31) return (const void*)tiled_kernel<DT, ST, CV, 2, 31>;
+      if constexpr (DT == DT_F32) {  // FP32 tiles are half the bytes: deeper ones fit
+        if (depth == 47) return (const void*)tiled_kernel<DT, ST, CV, 2, 47>;
+        if (depth == 63) return (const void*)tiled_kernel<DT, ST, CV, 2, 63>;
+      }
     }
   }
   if constexpr (ST == ST_BARRETT || ST == ST_SHARED)

@@ -35,9 +35,13 @@ static uint64_t tile_count(uint64_t n, uint64_t head, uint32_t depth) {
 
 // The launch shape for fields left zero when no tuning is installed: the
 // shape the autotuner picks on GB300 for 2^28 variates of every output type
-// (FP64 756, FP32 765, raw states 821 G/s there, against 573, 628 and 704
-// with 15-deep tiles in 256-thread blocks).
+// (FP64 756, raw states 821 G/s there, against 573 and 704 with 15-deep tiles
+// in 256-thread blocks).  FP32 tiles are half the bytes, so FP32 takes tiles
+// twice as deep in the same shared memory: fewer tile jumps and votes per
+// variate.
 constexpr uint32_t kDefDepth = 31, kDefBlock = 896, kDefChains = 2, kDefBuffers = 1;
+constexpr uint32_t kDefDepthF32 = 63;
+inline uint32_t def_depth(int dt) { return dt == DT_F32 ? kDefDepthF32 : kDefDepth; }
 
 rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* out,
                         bool constant) {
@@ -116,13 +120,13 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   L.chains = 1;
   const uint32_t want_chains = t.chains ? t.chains : kDefChains;
   if (L.layout == RNG_LAYOUT_TILED && (L.step == ST_SHARED || L.step == ST_BARRETT) &&
-      want_chains == 2 && (t.depth ? t.depth : kDefDepth) >= 3)
+      want_chains == 2 && (t.depth ? t.depth : def_depth(dt)) >= 3)
     L.chains = 2;
-  const uint32_t depth0 = L.layout == RNG_LAYOUT_TILED ? (t.depth ? t.depth : kDefDepth) : 0;
+  const uint32_t depth0 = L.layout == RNG_LAYOUT_TILED ? (t.depth ? t.depth : def_depth(dt)) : 0;
   const void* fn = pick_kernel(L.layout, dt, L.step, L.conv, (int)L.chains, depth0);
   if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   if (L.layout == RNG_LAYOUT_TILED) {
-    L.depth = t.depth ? t.depth : kDefDepth;
+    L.depth = t.depth ? t.depth : def_depth(dt);
     L.block = t.block ? t.block : kDefBlock;
     if (L.depth % 2 == 0 || L.depth > kMaxDepth)
       return set_error(RNG_EINVAL, "tune.depth %u must be odd and at most %u", L.depth,
@@ -218,10 +222,11 @@ rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t
     const uint64_t stride = (L.step == ST_MONT) ? 33ull : 31ull;
     p.jump = host_pow2((53ull * stride * L.depth) % kP);
     p.jump_q = host_mulmod_quotient(p.jump);
-    const uint64_t h = L.depth / 2;
-    p.jump_a = host_pow2((53ull * (32ull * L.depth - h - 1)) % kP);
+    // FP32 with the shared step on two chains runs the backward step
+    const bool back = L.dt == DT_F32 && L.step == ST_SHARED && L.conv == CV_INT && L.chains == 2;
+    p.jump_a = host_pow2((53ull * chain_jump_a(back, L.depth)) % kP);
     p.jump_aq = host_mulmod_quotient(p.jump_a);
-    p.jump_b = host_pow2((53ull * (31ull * L.depth + h + 1)) % kP);
+    p.jump_b = host_pow2((53ull * chain_jump_b(back, L.depth)) % kP);
     p.jump_bq = host_mulmod_quotient(p.jump_b);
     p.cbits = const_bits;
     p.depth = L.depth;

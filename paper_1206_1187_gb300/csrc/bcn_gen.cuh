@@ -142,6 +142,10 @@ __device__ __forceinline__ void wait_buffer_free(uint32_t issued, uint32_t nbuf,
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
+// The buffer a warp fills next (one or two buffers per warp; no division).
+__device__ __forceinline__ uint32_t tile_buffer(uint32_t issued, uint32_t nbuf) {
+  return nbuf == 2 ? (issued & 1u) : 0u;
+}
 
 
 // The shared-quotient step's fast path for a whole run of c variates: no
@@ -202,7 +206,7 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
   const uint32_t tile_elems = 32u * c;
   const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
   for (uint64_t t = 0; t < ntiles; ++t) {
-    W* const buf = buf0 + (issued % nbuf) * tile_elems;
+    W* const buf = buf0 + tile_buffer(issued, nbuf) * tile_elems;
     wait_buffer_free(issued, nbuf, lane);
     W* const mine = buf + lane * c;
     if constexpr (STEP == ST_CONST) {
@@ -297,6 +301,46 @@ __device__ __forceinline__ void shared_run_fast2(typename Word<DT>::type* mine, 
   }
 }
 
+// FP32 output by the backward step with its exact quotient (two chains on
+// y = z - 1): chain b starts one past the run and emits elements c-1 .. h+1,
+// chain a starts at element h+1 and emits h .. 0, so afterwards chain a holds
+// element 0 and chain b element h+1.  Every K-th iteration of chain b takes
+// its conversion on the otherwise idle FP64 pipe (int->double and one
+// round-to-nearest multiply, then truncation to float), the step's own
+// conversion being dropped by the compiler.  A lane whose run needs the exact
+// path (see back_step_f32_ptx) redoes it forward from element 0.
+constexpr uint32_t kBackFp64Every = 6;
+template <int CDEPTH>
+__device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_t& ya,
+                                             uint64_t& yb) {
+  uint32_t qmin = 0xffffffffu;
+  const uint32_t h = CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : c / 2;
+  const uint32_t last = CDEPTH > 0 ? (uint32_t)CDEPTH - 1 : c - 1;
+#pragma unroll
+  for (uint32_t i = 0; i < h; ++i) {
+    if (CDEPTH > 0 && i % kBackFp64Every == kBackFp64Every / 2) {
+      uint32_t unused = 0;
+      back_step_f32_ptx(yb, unused);
+      mine[last - i] = f32_bits_from_f64_bits(f64_bits_fp64(yb + 1));
+    } else {
+      mine[last - i] = back_step_f32_ptx(yb, qmin);
+    }
+    mine[h - i] = back_step_f32_ptx(ya, qmin);
+  }
+  mine[0] = back_step_f32_ptx(ya, qmin);
+  if (__any_sync(0xffffffffu, qmin == 0)) {
+    if (qmin == 0) {
+      uint64_t z = ya + 1;  // element 0, forward
+      for (uint32_t i = 0; i <= last; ++i) mine[i] = f32_bits_from_f64_bits(shared_step_f64(z));
+    }
+    __syncwarp();
+  }
+}
+
+// Whether a two-chain tile loop of this kind runs the backward FP32 step.
+template <int DT, int STEP, int CONV>
+constexpr bool kBackF32 = DT == DT_F32 && STEP == ST_SHARED && CONV == CV_INT;
+
 template <int DT, int STEP, int CONV, int CDEPTH = 0>
 __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict__ out,
                                             uint64_t first, uint64_t ntiles, uint32_t c_rt,
@@ -311,10 +355,12 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
   const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(W);
   const uint32_t h = c >> 1;
   for (uint64_t t = 0; t < ntiles; ++t) {
-    W* const buf = buf0 + (issued % nbuf) * tile_elems;
+    W* const buf = buf0 + tile_buffer(issued, nbuf) * tile_elems;
     wait_buffer_free(issued, nbuf, lane);
     W* const mine = buf + lane * c;
-    if constexpr (STEP == ST_SHARED && CONV == CV_INT && DT != DT_U64) {
+    if constexpr (kBackF32<DT, STEP, CONV>) {
+      back_run_f32<CDEPTH>(reinterpret_cast<uint32_t*>(mine), c, a.z, b.z);
+    } else if constexpr (STEP == ST_SHARED && CONV == CV_INT && DT != DT_U64) {
       shared_run_fast2<DT, CDEPTH>(mine, c, a.z, b.z);
     } else {
 #pragma unroll 4
@@ -332,9 +378,31 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
     }
     ++issued;
     if (t + 1 < ntiles) {
-      a.z = mulmod_pre(a.z, jump_a, jump_aq);
-      b.z = mulmod_pre(b.z, jump_b, jump_bq);
+      if constexpr (kBackF32<DT, STEP, CONV>) {  // the chains hold z - 1
+        a.z = mulmod_pre(a.z + 1, jump_a, jump_aq) - 1;
+        b.z = mulmod_pre(b.z + 1, jump_b, jump_bq) - 1;
+      } else {
+        a.z = mulmod_pre(a.z, jump_a, jump_aq);
+        b.z = mulmod_pre(b.z, jump_b, jump_bq);
+      }
     }
+  }
+}
+
+// Initial states of the two chains of a lane whose first run starts at
+// element `first`: forward chains at elements first and first + h + 1; the
+// backward FP32 chains one past elements h and c - 1, as z - 1.
+template <int DT, int STEP, int CONV>
+__device__ __forceinline__ void lane_chains2(uint64_t ebase, uint64_t first, uint32_t c,
+                                             uint32_t skip, Gen<DT, STEP, CONV>& a,
+                                             Gen<DT, STEP, CONV>& b) {
+  const uint32_t h = c / 2;
+  if constexpr (kBackF32<DT, STEP, CONV>) {
+    a.z = state_of(ebase, first + h + 1, skip) - 1;
+    b.z = state_of(ebase, first + c, skip) - 1;
+  } else {
+    a.z = state_of(ebase, first, skip);
+    b.z = state_of(ebase, first + h + 1, skip);
   }
 }
 

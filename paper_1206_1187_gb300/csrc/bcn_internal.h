@@ -27,6 +27,18 @@ struct BulkLaunch {
   size_t smem_bytes;  // TILED only
 };
 
+// The tile-to-tile jumps (in steps) of a lane's two chains over tiles of
+// 32*c elements (h = c/2): forward chains move from elements h + 1 and c of
+// the lane's run to elements 0 and h + 1 of its run in the next tile,
+// backward ones (the FP32 step that runs Eq. 3 backwards) from elements 0 and
+// h + 1 to h + 1 and c.
+inline uint64_t chain_jump_a(bool backward, uint64_t c) {
+  return backward ? 32 * c + c / 2 + 1 : 32 * c - c / 2 - 1;
+}
+inline uint64_t chain_jump_b(bool backward, uint64_t c) {
+  return backward ? 33 * c - c / 2 - 1 : 31 * c + c / 2 + 1;
+}
+
 // Element size in bytes of an rng_dtype.
 inline size_t dtype_size(int dt) { return dt == DT_F32 ? 4 : 8; }
 

@@ -8,19 +8,22 @@
 // bulk async-copy engine.  Head (before the first 16-byte boundary) and tail
 // (less than a tile) are stored directly by the grid's last warp.
 //
-// Per variate: one quotient floor(2^53 z / 3^40) (three 64-bit partial
-// products), one remainder (one product), and a shift-and-or that joins two
-// consecutive quotients into the truncated FP64 variate.  A chain therefore
-// runs one quotient ahead of the variate it emits: it holds the state after
-// the next variate's state and that variate's quotient.
+// Per variate: one step of Eq. 3 run backwards (back40), which gives the
+// previous state together with its exact quotient digit floor(2^53 z / 3^40),
+// and a shift-and-or that joins two consecutive digits into the truncated
+// FP64 variate.  Lanes walk their runs from the end down, so a chain holds,
+// besides its state, the digit of the state above the variate it emits next.
+// The head and tail, and runs holding a variate below 2^-21, are made forward
+// with the exact quotient.
 #include "bcn_gen.cuh"
 #include "bcn_m40.cuh"
 #include "bcn_math40.cuh"
 
 namespace bcn {
 
-// One chain.  Variates (F64/F32): z is the state after the next variate's
-// state, q the next variate's quotient.  States (U64): z is the next state.
+// One forward chain with the exact quotient (head, tail and the rare runs).
+// Variates (F64/F32): z is the state after the next variate's state, q the
+// next variate's quotient.  States (U64): z is the next state.
 template <int DT>
 struct Chain40 {
   uint64_t z, q;
@@ -32,21 +35,6 @@ struct Chain40 {
       q = quot40(s);
       z = rem40(s, q);
     }
-  }
-  // A variate by the fast quotient and conversion (F64/F32 only).  qmin
-  // tracks the smallest high word of the quotients used as a variate's
-  // leading window (0 means a variate below 2^-21); fmax the largest high
-  // word of the estimates' fractions (>= 0xFFFFFFFC means undecided).
-  __device__ __forceinline__ typename Word<DT>::type next_fast(uint32_t& qmin, uint32_t& fmax) {
-    uint32_t fhi;
-    const uint64_t q1 = quot40_fast(z, fhi);
-    fmax = max(fmax, fhi);
-    const uint64_t bits = bits40_fast(q, q1);
-    z = rem40(z, q1);
-    q = q1;
-    qmin = min(qmin, (uint32_t)(q1 >> 32));
-    if constexpr (DT == DT_F64) return bits;
-    else return f32_bits_from_f64_bits(bits);
   }
   __device__ __forceinline__ typename Word<DT>::type next() {
     if constexpr (DT == DT_U64) {
@@ -64,11 +52,35 @@ struct Chain40 {
   }
 };
 
-// Steps between what a chain holds after emitting the variate before index
-// i and the state of variate i: one for variates (the look-ahead), none for
-// states.
+// One chain run backwards (back40): z is one step past the next state to
+// emit, q (variates only) the quotient digit of z.  A step back gives the
+// previous state and its digit, which leads the variate emitted; z's own
+// digit continues it.  Every digit is exact, so only variates below 2^-21
+// (leading digit's high word zero) leave the fast conversion.
 template <int DT>
-constexpr uint64_t kAhead40 = DT == DT_U64 ? 0 : 1;
+struct Back40 {
+  uint64_t z, q;
+  // Begin with the state s one past (variates: two past) the first element
+  // emitted; for variates one step back gives the digit of the state above.
+  __device__ __forceinline__ void start(uint64_t s) {
+    z = s;
+    if constexpr (DT != DT_U64) z = back40(z, q);
+  }
+  __device__ __forceinline__ typename Word<DT>::type next(uint32_t& qmin) {
+    uint64_t u;
+    const uint64_t zp = back40(z, u);
+    z = zp;
+    if constexpr (DT == DT_U64) {
+      return zp;
+    } else {
+      const uint64_t bits = bits40_fast(u, q);
+      qmin = min(qmin, (uint32_t)(u >> 32));
+      q = u;
+      if constexpr (DT == DT_F64) return bits;
+      else return f32_bits_from_f64_bits(bits);
+    }
+  }
+};
 
 __device__ __forceinline__ uint64_t state_of40(uint64_t ebase, uint64_t idx) {
   return seed_state40(exponent_add40(ebase, idx + 1));
@@ -101,60 +113,46 @@ __global__ void __launch_bounds__(1024) tiled40_kernel(const M40Params p) {
   const uint64_t t0 = gw * p.ntiles / nw;
   const uint64_t t1 = (gw + 1) * p.ntiles / nw;
   if (t0 < t1) {
+    // Backward chains: a single chain emits c-1 .. 0 of the lane's run; two
+    // chains split it, b emitting c-1 .. h+1 and a h .. 0.  Afterwards chain
+    // a holds element 0 (its state), chain b element h+1.
     const uint64_t first = p.head + t0 * tile_elems + (uint64_t)lane * c;
     const uint32_t h = c >> 1;
-    Chain40<DT> a, b;
-    a.start(state_of40(p.ebase, first));
-    if constexpr (ILP == 2) b.start(state_of40(p.ebase, first + h + 1));
+    constexpr uint64_t lead = DT == DT_U64 ? 0 : 1;  // the digit of the state above
+    Back40<DT> a, b;
+    if constexpr (ILP == 2) {
+      a.start(state_of40(p.ebase, first + h + 1 + lead));
+      b.start(state_of40(p.ebase, first + c + lead));
+    } else {
+      a.start(state_of40(p.ebase, first + c + lead));
+    }
     uint32_t issued = 0;
     for (uint64_t t = t0; t < t1; ++t) {
-      W* const buf = buf0 + (issued % p.nbuf) * tile_elems;
+      W* const buf = buf0 + tile_buffer(issued, p.nbuf) * tile_elems;
       wait_buffer_free(issued, p.nbuf, lane);
       W* const mine = buf + lane * c;
-      if constexpr (DT == DT_U64) {
-        if constexpr (ILP == 2) {
+      uint32_t qmin = 0xffffffffu;
+      if constexpr (ILP == 2) {
+        const uint32_t last = CDEPTH > 0 ? (uint32_t)CDEPTH - 1 : c - 1;
 #pragma unroll
-          for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : h); ++i) {
-            mine[i] = a.next();
-            mine[h + 1 + i] = b.next();
-          }
-          mine[h] = a.next();
-        } else {
-#pragma unroll
-          for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH : c); ++i) mine[i] = a.next();
+        for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : h); ++i) {
+          mine[last - i] = b.next(qmin);
+          mine[h - i] = a.next(qmin);
         }
+        mine[0] = a.next(qmin);
       } else {
-        // fast path for the whole run; a lane whose run met an undecided
-        // quotient or a variate below 2^-21 redoes it exactly
-        const Chain40<DT> a0 = a, b0 = b;
-        uint32_t qmin = (uint32_t)(a.q >> 32), fmax = 0;
-        if constexpr (ILP == 2) {
-          qmin = min(qmin, (uint32_t)(b.q >> 32));
 #pragma unroll
-          for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : h); ++i) {
-            mine[i] = a.next_fast(qmin, fmax);
-            mine[h + 1 + i] = b.next_fast(qmin, fmax);
-          }
-          mine[h] = a.next_fast(qmin, fmax);
-        } else {
-#pragma unroll
-          for (uint32_t i = 0; i < (CDEPTH > 0 ? (uint32_t)CDEPTH : c); ++i)
-            mine[i] = a.next_fast(qmin, fmax);
-        }
-        const bool rare = qmin == 0 || fmax >= 0xFFFFFFFCu;
+        for (uint32_t i = (CDEPTH > 0 ? (uint32_t)CDEPTH : c); i-- > 0;) mine[i] = a.next(qmin);
+      }
+      if constexpr (DT != DT_U64) {
+        // a lane whose run holds a variate below 2^-21 redoes it exactly,
+        // forward from element 0
+        const bool rare = qmin == 0;
         if (__any_sync(0xffffffffu, rare)) {
           if (rare) {
-            a = a0;
-            b = b0;
-            if constexpr (ILP == 2) {
-              for (uint32_t i = 0; i < h; ++i) {
-                mine[i] = a.next();
-                mine[h + 1 + i] = b.next();
-              }
-              mine[h] = a.next();
-            } else {
-              for (uint32_t i = 0; i < c; ++i) mine[i] = a.next();
-            }
+            Chain40<DT> f;
+            f.start(a.z);
+            for (uint32_t i = 0; i < c; ++i) mine[i] = f.next();
           }
           __syncwarp();
         }

@@ -9,9 +9,11 @@ namespace bcn {
 struct M40Params {
   unsigned char* out;
   uint64_t n, head, ntiles, ebase;
-  uint64_t jump;    // one chain: Montgomery form of 2^(53 (31c - ahead))
-  uint64_t jump_a;  // two chains: 2^(53 (32c - h - 1 - ahead)) and
-  uint64_t jump_b;  //             2^(53 (31c + h + 1 - ahead)), h = c/2
+  // tile-to-tile jumps of the backward chains, Montgomery form of 2^(53 j),
+  // h = c/2, lead = 1 for variates (0 for states):
+  uint64_t jump;    // one chain: j = 33c + lead
+  uint64_t jump_a;  // two chains: j = 32c + h + 1 + lead and
+  uint64_t jump_b;  //             j = 33c - h - 1 + lead
   uint32_t depth, nbuf;
 };
 

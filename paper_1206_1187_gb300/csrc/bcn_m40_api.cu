@@ -106,7 +106,9 @@ static rng_status launch40(const Launch40& L, uint64_t seed, uint64_t i0, uint64
   const uint64_t ebase = host40_exponent_base(seed, i0);
   cudaError_t e;
   if (L.layout == RNG_LAYOUT_TILED) {
-    const uint64_t ahead = L.dt == DT_U64 ? 0 : 1;
+    // the tiled kernel's chains run backwards and hold, for variates, the
+    // state one above the next element (the digit of which continues it)
+    const uint64_t lead = L.dt == DT_U64 ? 0 : 1;
     const uint64_t c = L.depth, h = c / 2;
     M40Params p;
     p.out = static_cast<unsigned char*>(out);
@@ -114,9 +116,9 @@ static rng_status launch40(const Launch40& L, uint64_t seed, uint64_t i0, uint64
     p.head = head_elems(out, dtype_size(L.dt), n);
     p.ntiles = n > p.head ? (n - p.head) / (32ull * c) : 0;
     p.ebase = ebase;
-    p.jump = jump40(31 * c - ahead);
-    p.jump_a = jump40(32 * c - h - 1 - ahead);
-    p.jump_b = jump40(31 * c + h + 1 - ahead);
+    p.jump = jump40(33 * c + lead);          // element 0 -> element c of the next run
+    p.jump_a = jump40(32 * c + h + 1 + lead); // element 0 -> element h+1 of the next run
+    p.jump_b = jump40(33 * c - h - 1 + lead); // element h+1 -> element c of the next run
     p.depth = L.depth;
     p.nbuf = L.buffers;
     void* args[] = {&p};

@@ -283,6 +283,14 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
     p.sumsq[b] = round_words(w0, w1, w2, 157);
     if (p.hits) p.hits[b] = hits;
     atomicAdd(p.hits_total, (unsigned long long)hits);
+    if (p.totals) {  // exact totals over the call: every 32-bit piece into its own word
+      const uint64_t words[kMcSumWords + kMcSqWords] = {a0, a0 >> 32, a1, a1 >> 32,
+                                                          w0, w0 >> 32, w1, w1 >> 32,
+                                                          w2, w2 >> 32};
+#pragma unroll
+      for (uint32_t k = 0; k < kMcSumWords + kMcSqWords; ++k)
+        atomicAdd(&p.totals[k], (unsigned long long)(words[k] & 0xFFFFFFFFull));
+    }
   }
 }
 

@@ -9,8 +9,15 @@
 //      when the caller releases it);
 //   2. admit waiting requests in arrival order while a request slot is free
 //      and the pool has a free range for the request's output (memory-based
-//      admission: a request that does not fit waits, and so do those behind
-//      it);
+//      admission).  A request that does not fit waits; a later one that does
+//      fit may pass it while the waiting one is younger than the bypass age,
+//      so one large request does not hold back every small one behind it.
+//      Once the oldest waiting request reaches that age, nothing passes it
+//      until it is admitted, so a large request is never starved.  With
+//      caller-managed release (release_after_s < 0) the order is strict by
+//      default: a client that consumes its results in order would otherwise
+//      hold, unreleased, the ranges of the requests that passed the one it
+//      waits for;
 //   3. if an iteration slot is free, pack the next chunk (chunk_elems
 //      variates, up to 64 times more when few requests are active) of every
 //      active request, round-robin, into one work table and launch the
@@ -69,6 +76,8 @@ struct Request {
   double t_arrive = 0, t_admit = 0, t_done = 0;
   TraceSink* sink = nullptr;  // set while a running trace waits for this request
   uint32_t sink_idx = 0;
+  uint32_t readers = 0;         // rng_server_read copies in progress
+  bool release_pending = false; // release asked for while a copy was in progress
 };
 
 // What is kept of a request once its pool range is released (or once it is
@@ -121,9 +130,12 @@ struct bcn_server {
   std::vector<bcn::Slot> slots;
   std::thread worker;
   std::atomic<bool> stop{false};
+  std::atomic<uint64_t> loop_gap_max_us{0};  // scheduler stall diagnostics
+  std::atomic<uint64_t> launch_max_us{0};
   rng_status err = RNG_OK;
   char errmsg[256] = {0};
   uint64_t next_id = 1, rr = 0;
+  double bypass_s = -1.0;     // admission bypass age (negative: strict arrival order)
   rng_server_stats st = {};
   uint64_t lat_hist[RNG_SERVER_HIST_BINS] = {};  // completion latencies, quarter octaves
   bcn_server(uint64_t cap) : pool(cap, 256) {}
@@ -217,39 +229,65 @@ static bool retire(bcn_server* s) {
   return any;
 }
 
+// Free a done request's pool range (mu held).  While rng_server_read is
+// copying the range out, the free is deferred to the end of that copy, so a
+// new request cannot be given the range (and overwrite it) mid-copy.
+static void release_range(bcn_server* s, std::unordered_map<uint64_t, Request>::iterator it) {
+  if (it->second.readers > 0) {
+    it->second.release_pending = true;
+    return;
+  }
+  s->pool.release(it->second.pool_off);
+  it->second.state = RQ_RELEASED;
+  forget(s, it);
+  s->cv_work.notify_one();
+}
+
 // Free pool ranges whose hold time has passed (caller holds mu).
 static void release_due(bcn_server* s, double t) {
   while (!s->to_release.empty() && s->to_release.front().first <= t) {
     const uint64_t id = s->to_release.front().second;
     s->to_release.pop_front();
     auto it = s->reqs.find(id);
-    if (it != s->reqs.end() && it->second.state == RQ_DONE) {
-      s->pool.release(it->second.pool_off);
-      it->second.state = RQ_RELEASED;
-      forget(s, it);
-    }
+    if (it != s->reqs.end() && it->second.state == RQ_DONE) release_range(s, it);
   }
 }
 
-// Admit queued requests in order while slots and pool space allow (mu held).
+// Queued requests looked at per admission pass when earlier ones do not fit.
+constexpr size_t kAdmitScan = 256;
+// How long a waiting request may be passed by later ones that fit, when the
+// server frees results itself and the caller leaves admit_bypass_s at 0.
+constexpr double kDefaultBypassS = 0.05;
+
+// Admit queued requests in arrival order while slots and pool space allow
+// (mu held).  A request that does not fit is passed over while it is younger
+// than the bypass age (s->bypass_s; negative: never), and stops the pass once
+// it is older.
 static bool admit(bcn_server* s, double t) {
   bool any = false;
-  while (!s->queue.empty() && s->active.size() < s->cfg.max_active) {
-    const uint64_t id = s->queue.front();
+  size_t k = 0;
+  while (k < s->queue.size() && k < kAdmitScan && s->active.size() < s->cfg.max_active) {
+    const uint64_t id = s->queue[k];
     auto it = s->reqs.find(id);
     Request& r = it->second;
     if (r.state == RQ_CANCELLED) {
-      s->queue.pop_front();
+      s->queue.erase(s->queue.begin() + (std::ptrdiff_t)k);
       forget(s, it);
       continue;
     }
     uint64_t off = 0;
-    if (!s->pool.alloc(r.bytes, &off)) break;  // memory-based admission
+    if (!s->pool.alloc(r.bytes, &off)) {  // memory-based admission
+      if (s->bypass_s < 0 || t - r.t_arrive >= s->bypass_s) break;
+      ++k;  // later requests may pass this one, for now
+      s->st.bypassed += k == 1 ? 1 : 0;
+      continue;
+    }
     r.pool_off = off;
     r.state = RQ_ACTIVE;
     r.t_admit = t;
     s->active.push_back(id);
-    s->queue.pop_front();
+    s->queue.erase(s->queue.begin() + (std::ptrdiff_t)k);
+    if (k > 0) s->st.admitted_out_of_order += 1;
     any = true;
     if (s->pool.in_use > s->st.peak_pool_bytes) s->st.peak_pool_bytes = s->pool.in_use;
     if (s->active.size() > s->st.peak_active) s->st.peak_active = s->active.size();
@@ -353,7 +391,14 @@ static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units,
 
 static void worker_main(bcn_server* s) {
   cudaSetDevice(s->device);
+  double t_prev = now_s();
   while (!s->stop.load(std::memory_order_relaxed)) {
+    {  // the longest time between two passes of this loop, sleeps excluded
+      const double t = now_s();
+      const uint64_t gap = (uint64_t)((t - t_prev) * 1e6);
+      if (gap > s->loop_gap_max_us.load(std::memory_order_relaxed))
+        s->loop_gap_max_us.store(gap, std::memory_order_relaxed);
+    }
     bool did = retire(s);
     Slot* free_slot = nullptr;
     for (Slot& sl : s->slots)
@@ -387,8 +432,12 @@ static void worker_main(bcn_server* s) {
         }
       }
     }
+    t_prev = now_s();  // a sleep above is not a stall
     if (items > 0) {
       launch_slot(s, *free_slot, items, units, shape);
+      const uint64_t us = (uint64_t)((now_s() - t_prev) * 1e6);
+      if (us > s->launch_max_us.load(std::memory_order_relaxed))
+        s->launch_max_us.store(us, std::memory_order_relaxed);
       did = true;
     }
     if (!did) std::this_thread::yield();  // polling completion events
@@ -473,6 +522,11 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
     s->heavy_elems = shapes[1].grid_full * (w.block / 32) * 2ull * 32ull * w.depth;
   }
   s->device = di.device;
+  // admission bypass: by default a waiting request may be passed for 50 ms
+  // when the server frees results itself, never when the caller does
+  s->bypass_s = cfg.admit_bypass_s > 0 ? cfg.admit_bypass_s
+                : cfg.admit_bypass_s < 0 || cfg.release_after_s < 0 ? -1.0
+                : kDefaultBypassS;
   auto cleanup = [s]() {
     for (Slot& sl : s->slots) {
       if (sl.ev) cudaEventDestroy(sl.ev);
@@ -613,11 +667,19 @@ rng_status rng_server_read(bcn_server* s, uint64_t id, void* dst, uint64_t dst_b
       return set_error(RNG_EINVAL, "unknown request");
     }
     if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done");
+    if (it->second.release_pending) return set_error(RNG_EBUSY, "request released");
     off = it->second.pool_off;
     bytes = it->second.bytes;
+    if (dst_bytes < bytes) return set_error(RNG_EINVAL, "destination smaller than the result");
+    it->second.readers += 1;  // the range stays this request's until the copy ends
   }
-  if (dst_bytes < bytes) return set_error(RNG_EINVAL, "destination smaller than the result");
-  cudaError_t e = cudaMemcpy(dst, s->pool_dev + off, bytes, cudaMemcpyDefault);
+  const cudaError_t e = cudaMemcpy(dst, s->pool_dev + off, bytes, cudaMemcpyDefault);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(id);  // a request with readers is never forgotten
+    it->second.readers -= 1;
+    if (it->second.readers == 0 && it->second.release_pending) release_range(s, it);
+  }
   if (e != cudaSuccess) return cuda_error(e, "reading a result");
   return RNG_OK;
 }
@@ -631,6 +693,7 @@ rng_status rng_server_result_ptr(bcn_server* s, uint64_t id, void** dev_ptr) {
     return set_error(RNG_EINVAL, "unknown request");
   }
   if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done");
+  if (it->second.release_pending) return set_error(RNG_EBUSY, "request released");
   *dev_ptr = s->pool_dev + it->second.pool_off;
   return RNG_OK;
 }
@@ -643,11 +706,10 @@ rng_status rng_server_release(bcn_server* s, uint64_t id) {
     if (s->past.count(id)) return set_error(RNG_EBUSY, "request already released");
     return set_error(RNG_EINVAL, "unknown request");
   }
-  if (it->second.state != RQ_DONE) return set_error(RNG_EBUSY, "request not done");
-  s->pool.release(it->second.pool_off);
-  it->second.state = RQ_RELEASED;
-  forget(s, it);
-  s->cv_work.notify_one();
+  if (it->second.state != RQ_DONE || it->second.release_pending)
+    return set_error(RNG_EBUSY, it->second.state != RQ_DONE ? "request not done"
+                                                            : "request already released");
+  release_range(s, it);
   return RNG_OK;
 }
 
@@ -657,6 +719,8 @@ rng_status rng_server_stats_get(bcn_server* s, rng_server_stats* out) {
   *out = s->st;
   out->pool_in_use = s->pool.in_use;
   out->pool_bytes = s->cfg.pool_bytes;
+  out->loop_gap_max_us = s->loop_gap_max_us.load();
+  out->launch_max_us = s->launch_max_us.load();
   return s->err;
 }
 

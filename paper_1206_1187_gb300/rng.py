@@ -62,14 +62,16 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("pool_bytes", ctypes.c_uint64), ("chunk_elems", ctypes.c_uint64),
                 ("max_active", ctypes.c_uint32), ("max_items", ctypes.c_uint32),
                 ("inflight", ctypes.c_uint32), ("pad", ctypes.c_uint32),
-                ("release_after_s", ctypes.c_double), ("tune", Tune)]
+                ("release_after_s", ctypes.c_double), ("tune", Tune),
+                ("admit_bypass_s", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in
                 ("submitted", "completed", "iterations", "items", "max_items_seen",
                  "peak_active", "peak_pool_bytes", "bytes_done", "pool_in_use", "pool_bytes",
-                 "heavy_iterations")]
+                 "heavy_iterations", "admitted_out_of_order", "bypassed", "loop_gap_max_us",
+                 "launch_max_us")]
 
 
 def _load() -> ctypes.CDLL:
@@ -113,6 +115,8 @@ def _load() -> ctypes.CDLL:
                             ctypes.POINTER(u64), tp], i32),
         "rng_batch_destroy": ([vp], i32),
         "rng_consume_mc": ([u64, u64, u64, u64, vp, vp, vp, vp, vp, tp], i32),
+        "rng_consume_mc_totals": ([u64, u64, u64, u64, vp, vp, vp, vp, vp, vp, tp], i32),
+        "rng_mc_round_totals": ([vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)], i32),
         "rng_batch_generate_noalloc": ([u32, vp, vp, vp, vp, vp, tp, vp], i32),
         "rng_device_api_check": ([u64, u64, u64, vp, vp, u32, vp], i32),
         "rng_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], i32),
@@ -354,6 +358,44 @@ def consume_mc_into(start_index: int, nblocks: int, length: int, total, hits, s1
                               ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
 
 
+MC_TOTAL_WORDS = 10
+
+
+def consume_mc_totals(start_index: int, nblocks: int, length: int, block0: int = 0,
+                      tune=None, stream=None):
+    """consume_mc plus the call's exact totals: returns (hits_total[1],
+    hits[nblocks], sum[nblocks], sumsq[nblocks], totals[10]) as CUDA tensors.
+    totals holds 32-bit pieces of the exact sums over every block of the call
+    (see rng_consume_mc_totals); word arrays of several calls or ranks add
+    element by element, and mc_round_totals rounds the result."""
+    total = torch.empty(1, dtype=torch.uint64, device="cuda")
+    hits = torch.empty(nblocks, dtype=torch.uint64, device="cuda")
+    s1 = torch.empty(nblocks, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(nblocks, dtype=torch.float64, device="cuda")
+    words = torch.empty(MC_TOTAL_WORDS, dtype=torch.uint64, device="cuda")
+    _check(lib.rng_consume_mc_totals(start_index, block0, nblocks, length,
+                                     ctypes.c_void_p(total.data_ptr()),
+                                     ctypes.c_void_p(hits.data_ptr()),
+                                     ctypes.c_void_p(s1.data_ptr()),
+                                     ctypes.c_void_p(s2.data_ptr()),
+                                     ctypes.c_void_p(words.data_ptr()),
+                                     ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
+    return total, hits, s1, s2, words
+
+
+def mc_round_totals(words) -> tuple[float, float]:
+    """(sum, sumsq): the totals word array (host sequence of 10 non-negative
+    integers below 2^64, e.g. several ranks' arrays added) rounded to nearest."""
+    import numpy as np
+    w = np.ascontiguousarray([int(x) for x in words], dtype=np.uint64)
+    if w.size != MC_TOTAL_WORDS:
+        raise ValueError(f"need {MC_TOTAL_WORDS} words, got {w.size}")
+    s1, s2 = ctypes.c_double(), ctypes.c_double()
+    _check(lib.rng_mc_round_totals(ctypes.c_void_p(w.ctypes.data), ctypes.byref(s1),
+                                   ctypes.byref(s2)))
+    return s1.value, s2.value
+
+
 def device_api_check(start_index: int, offset: int, n: int, threads: int = 4096, stream=None):
     """Variates from a kernel written against bcn_device.cuh: (f64, f32) tensors."""
     f64 = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -428,9 +470,9 @@ class Server:
 
     def __init__(self, pool_bytes: int, chunk_elems: int = 0, max_active: int = 0,
                  max_items: int = 0, inflight: int = 0, release_after_s: float = -1.0,
-                 tune=None):
+                 tune=None, admit_bypass_s: float = 0.0):
         cfg = ServerConfig(pool_bytes, chunk_elems, max_active, max_items, inflight, 0,
-                           release_after_s, Tune())
+                           release_after_s, Tune(), admit_bypass_s)
         if tune is not None:
             cfg.tune = tune if isinstance(tune, Tune) else make_tune(**tune)
         h = ctypes.c_void_p()

@@ -408,3 +408,50 @@ def test_paper_strided_layout_at_the_papers_shape(R, oracle_mod):
     with pytest.raises(R.RNGError) as e:
         R.set_auto_tune("f64", R.make_tune(layout="strided"))
     assert e.value.status == 1
+
+
+def test_fp32_near_float_boundaries(R, oracle_mod):
+    """FP32 variates whose quotient floor(2^53 z/m) has all ones (or all ones
+    but the last one or two bits) below its leading 24 bits: the backward FP32
+    step must take its exact path for the first two kinds and may not for the
+    third.  Each chosen state is placed at a known output index of a seed by a
+    discrete logarithm, and windows around it are generated with every FP32
+    tile shape (compile-time and run-time depths, one and two chains) and in a
+    batch."""
+    import sys
+
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from m40_math import dlog2
+    rnd = random.Random(77)
+    a = M + 31337
+    h_inv = pow(M // 2, -1, M)
+    targets = []
+    for tail in (29, 28, 20, 12, 9):
+        for k in (1, 2, 3):
+            for _ in range(40):
+                head = rnd.randrange(1 << 23, 1 << 24)
+                q = (head << tail) | ((1 << tail) - k)
+                z = -(-(q * M) // 2 ** 53)  # the state with this quotient, if any
+                if 0 < z < M and z % 3 and (z << 53) // M == q:
+                    targets.append(z)
+                    break
+    assert len(targets) >= 12
+    shapes = [dict(), dict(depth=31), dict(depth=47, block=768), dict(depth=45, chains=2),
+              dict(depth=63, chains=1), dict(depth=5, block=128)]
+    for z in targets:
+        e = dlog2(z * h_inv % M, 33)
+        i = ((e - (a - M)) * pow(53, -1, P) - 1) % P
+        assert int(oracle_mod.generate(a, i, 1, "u64")[0]) == z
+        off = i - 2000 if i >= 2000 else 0
+        want = oracle_mod.generate(a, off, 4001, "f32")
+        for shape in shapes:
+            t = R.make_tune(step="shared", layout="tiled", **shape)
+            assert_same(R.generate_at(a, off, 4001, "f32", tune=t), want, f"{z} {shape}")
+        outs = [torch.empty(4001, dtype=torch.float32, device="cuda"),
+                torch.empty(3, dtype=torch.float64, device="cuda")]
+        b = R.Batch(np.array([a, a], dtype=np.uint64), np.array([4001, 3], dtype=np.uint64),
+                    ["f32", "f64"], outs=outs, offsets=np.array([off, off], dtype=np.uint64))
+        b.launch()
+        assert_same(outs[0], want, f"batch {z}")
+        b.close()

@@ -102,3 +102,25 @@ def test_2_36_variates_subsample(R, oracle_mod):
     assert np.array_equal(s2[sub].view(np.int64), o2.view(np.int64))
     # pi/4 sanity on 2^35 pairs
     assert abs(total / (nblocks * length / 2) - np.pi / 4) < 1e-4
+
+
+def test_exact_totals_of_one_call(R, oracle_mod):
+    """The call's totals word array rounds to the oracle's exactly rounded sums
+    over all its blocks, for any launch shape; the plain entry point's
+    per-block outputs are unchanged by asking for totals."""
+    import torch
+    a, length, nblocks, block0 = M + 100, 2048, 48, 123457
+    v = oracle_mod.generate(a, block0 * length, nblocks * length, "f64")
+    want = (oracle_mod.exact_sum(v), oracle_mod.exact_sum(v * v))
+    ref = _run(R, a, nblocks, length, block0=block0)
+    for block, conv in ((128, "fp64"), (32, "int"), (256, "fp64")):
+        total, hits, s1, s2, words = R.consume_mc_totals(
+            a, nblocks, length, block0=block0, tune=R.make_tune(block=block, conv=conv))
+        torch.cuda.synchronize()
+        w = [int(x) for x in words.view(torch.int64).cpu().tolist()]
+        assert all(0 <= x < (nblocks << 32) for x in w)
+        assert R.mc_round_totals(w) == want, (block, conv)
+        assert int(total.view(torch.int64).cpu()[0]) == ref[0]
+        assert np.array_equal(hits.view(torch.int64).cpu().numpy(), ref[1])
+        assert np.array_equal(s1.cpu().numpy().view(np.int64), ref[2].view(np.int64))
+        assert np.array_equal(s2.cpu().numpy().view(np.int64), ref[3].view(np.int64))

@@ -438,3 +438,81 @@ def test_fused_chunk_rule_makes_every_square_fast():
     assert kept > 29000
     v21 = 2.0 ** -21
     assert (f64_bits(v21 * v21) >> 52) - 918 == 63
+
+
+MP = (-pow(M, -1, 2 ** 53)) % 2 ** 53  # m' = -m^-1 mod 2^53
+
+
+def back_step_f32_model(y):
+    """The backward FP32 step on 32-bit words: y = z_k - 1 gives y_(k-1), the
+    quotient Q = (u1:u0) of the state z_(k-1), its FP32 bits and the rare-path
+    value v (0: the exact path is needed).  bfind.shiftamt of 0 is 2^32 - 1."""
+    y0, y1 = y & MASK32, y >> 32
+    mp0, mp1 = MP & MASK32, MP >> 32
+    t = (y0 * mp0 + MP) % 2 ** 64
+    u0, th = t & MASK32, t >> 32
+    th = (th + y0 * mp1 + y1 * mp0) & MASK32
+    u1 = th & (2 ** 21 - 1)
+    h0 = (u0 * M0) >> 32
+    lo = u0 * M1 + h0                         # carry chain of 32-bit halves
+    v1 = lo & MASK32
+    x = lo >> 32
+    lo = u1 * M0 + v1
+    v1 = lo & MASK32
+    x += lo >> 32
+    v2 = (u1 * M1 + x) & MASK32
+    v3 = (u1 * M1 + x) >> 32
+    yp = ((funnel_r(v2, v3, 21) << 32) | funnel_r(v1, v2, 21))
+    c = clz32(u1) if u1 else MASK32
+    s = (c - 8) & MASK32
+    mant = ((((u1 << 32) | u0) << s) >> 32) & MASK32 if s < 32 else u0
+    e = (s * 0xFF800000 + 0x40000000) & MASK32
+    bits = (mant + e) & MASK32
+    v = ((~(u0 | 1) & MASK32) << s) & MASK32 if s < 32 else 0
+    return yp, (u1 << 32) | u0, bits, v
+
+
+def test_backward_step_gives_the_previous_state_and_its_quotient():
+    for zk in states(40000, seed=31):
+        yp, q, _, _ = back_step_f32_model(zk - 1)
+        zp = yp + 1
+        assert 0 < zp < M and (zp << 53) % M == zk, zk
+        assert q == (zp << 53) // M, zk
+
+
+def test_backward_f32_from_the_quotient_is_the_truncated_double():
+    """Unflagged steps give RN(z*r3i) toward zero exactly; flags are rare on
+    random states.  Adversarial states: quotients whose bits below the float's
+    24 are all ones, all ones but one or two, at every tail length."""
+    rnd = random.Random(41)
+    flagged = 0
+    zs = states(60000, seed=32)
+    for zk in zs:
+        yp, q, bits, v = back_step_f32_model(zk - 1)
+        if v == 0:
+            flagged += 1
+            continue
+        assert bits == rz_f32_bits(yp + 1), zk
+    assert flagged < 200
+    checked = 0
+    for tail in range(9, 30):
+        for k in range(1, 5):                     # all ones minus 0, 1, 2, 3
+            for _ in range(150):
+                head = rnd.randrange(1 << 23, 1 << 24)
+                qv = (head << tail) | ((1 << tail) - k)
+                zp = -(-(qv * M) // 2 ** 53)     # smallest state with this quotient
+                if not 0 < zp < M or (zp << 53) // M != qv:
+                    continue
+                yp, q, bits, v = back_step_f32_model(((zp << 53) % M) - 1)
+                assert q == qv
+                if k <= 2:
+                    assert v == 0, (tail, k)      # must take the exact path
+                else:
+                    assert v != 0 and bits == rz_f32_bits(zp), (tail, k)
+                    checked += 1
+    assert checked > 3000
+    # variates below 2^-21 (top word of the quotient zero) always take it
+    for qv in list(range(1, 5000)) + [rnd.randrange(1, 2 ** 32) for _ in range(5000)]:
+        zp = -(-(qv * M) // 2 ** 53)
+        if 0 < zp < M and (zp << 53) // M == qv:
+            assert back_step_f32_model(((zp << 53) % M) - 1)[3] == 0

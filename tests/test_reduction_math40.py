@@ -4,6 +4,7 @@ derivations and checked against the definitions (no GPU).
 Models: the quotient floor(2^53 z / 3^40) from the 118-bit reciprocal with
 the carry rule, the remainder in 64-bit wrap-around arithmetic, the
 Montgomery product with its 65-bit sum, the fixed-base skip-ahead table,
+the backward step that yields the previous state with its exact quotient,
 and the variate bits joined from two consecutive quotients (and from the
 next two when the first is 0).  Each is compared with `//`, `%` and exact
 rational truncation on random, edge and adversarial states.
@@ -162,79 +163,69 @@ def test_smallest_variates_take_the_second_window():
     assert index_of_state(M40 + 100, 1) >= 0
 
 
-def test_two_chain_jump_distances():
-    """A chain that has emitted variates [s, s+len) holds the state of
-    variate s+len+1 (one quotient ahead); the jump to a run starting at s'
-    is 2^(53 (s' - s - len - 1)).  Tiles of 32c, a lane's run split into
-    h+1 and h variates (c = 2h+1)."""
+def test_backward_chain_jump_distances():
+    """The tiled kernel's chains run backwards and, for variates, hold the
+    state one above the next element emitted (its digit continues that
+    variate); after a run of c elements at s a single chain holds element s,
+    two chains (b: c-1 .. h+1, a: h .. 0) hold elements s and s+h+1.  The jump
+    to the next tile (s + 32c) must land one above (plus lead) the element
+    each chain emits first."""
     for c in (3, 15, 31, 63):
         h = c // 2
         s = 1000
-        # chain a: variates [s, s+h+1), next run at s + 32c
-        assert (s + 32 * c) - (s + h + 1) - 1 == 32 * c - h - 2
-        # chain b: variates [s+h+1, s+c), next run at s+h+1 + 32c
-        assert (s + h + 1 + 32 * c) - (s + c) - 1 == 31 * c + h
-        # one chain: [s, s+c), next run at s + 32c
-        assert (s + 32 * c) - (s + c) - 1 == 31 * c - 1
+        for lead in (0, 1):
+            assert (s + 32 * c + c + lead) - s == 33 * c + lead           # one chain
+            assert (s + 32 * c + h + 1 + lead) - s == 32 * c + h + 1 + lead  # chain a
+            assert (s + 32 * c + c + lead) - (s + h + 1) == 33 * c - h - 1 + lead  # chain b
 
 
-H0, H1 = RHI & 0xFFFFFFFF, RHI >> 32
-RL1 = RLO >> 32
+MASK32 = 0xFFFFFFFF
+MP40 = (-pow(M40, -1, 2 ** 53)) % 2 ** 53
 
 
-def quot_fast_model(z):
-    """T = z*Rhi + z1*r1 from five 32x32-bit products; returns (floor(T/2^64),
-    high word of T mod 2^64)."""
-    z0, z1 = z & 0xFFFFFFFF, z >> 32
-    p00, p01, p10, p11, b = z0 * H0, z0 * H1, z1 * H0, z1 * H1, z1 * RL1
-    lo = p00 + b
-    c0 = lo >> 64
-    lo &= U64
-    mid = p01 + p10
-    cm = (mid >> 64) << 32
-    mid &= U64
-    f = lo + ((mid << 32) & U64)
-    c1 = f >> 64
-    f &= U64
-    return p11 + (mid >> 32) + cm + c0 + c1, f >> 32
+def back_model(z):
+    """The backward step on 32-bit limbs: Q = z m' mod 2^53 and
+    S = z + Q 3^40 from limb 1 up, limb 0's carry being [low word of z != 0];
+    returns (S >> 53, Q)."""
+    z0, z1 = z & MASK32, z >> 32
+    mp0, mp1 = MP40 & MASK32, MP40 >> 32
+    m0, m1 = M40 & MASK32, M40 >> 32
+    t = z0 * mp0
+    u0, th = t & MASK32, t >> 32
+    u1 = (th + z0 * mp1 + z1 * mp0) & 0x1FFFFF
+    l1 = ((u0 * m0) >> 32) + z1 + (1 if z0 else 0)
+    l1 += (u0 * m1) & MASK32
+    l1 += (u1 * m0) & MASK32
+    l2 = (l1 >> 32) + ((u0 * m1) >> 32) + ((u1 * m0) >> 32) + ((u1 * m1) & MASK32)
+    l3 = (l2 >> 32) + ((u1 * m1) >> 32)
+    s = ((l3 & MASK32) << 64) | ((l2 & MASK32) << 32) | (l1 & MASK32)
+    return s >> 21, (u1 << 32) | u0
+
+
+def test_backward_step_and_its_digit_are_exact():
+    for zk in states(60000, seed=44) + [j << 32 for j in range(1, 400)]:
+        if zk % 3 == 0 or not 0 < zk < M40:
+            continue
+        zp, q = back_model(zk)
+        assert 0 < zp < M40 and (zp << 53) % M40 == zk, zk
+        assert q == (zp << 53) // M40 == quot_model(zp), zk
+
+
+def test_backward_digits_join_into_the_truncated_variate():
+    """Two consecutive digits from two steps back give the variate of the
+    lower state exactly (fast form while its leading digit is >= 2^32)."""
+    for z2 in states(20000, seed=45):
+        z1, q1 = back_model(z2)
+        z0, q0 = back_model(z1)
+        assert q1 == quot_model(z1) and q0 == quot_model(z0)
+        if q0 >> 32:
+            assert f64_from_bits(bits_fast_model(q0, q1)) == trunc_quotient(z0), z2
 
 
 def bits_fast_model(q0, q1):
     t = (32 - (q0 >> 32).bit_length()) - 11
     mant = ((q0 << t) & U64) | ((q1 >> 32) >> (21 - t))
     return (((1021 - t) << 52) + mant) & U64
-
-
-def undecided_states(count):
-    """States whose next remainder is within a few units of 3^40, so that
-    frac(2^53 z / 3^40) is within 2^-60 of 1: the fast quotient's fraction
-    is then in the undecided band."""
-    inv = pow(2 ** 53, -1, M40)
-    out = []
-    for k in range(1, count):
-        if k % 3:
-            out.append((M40 - k) * inv % M40)
-    return out
-
-
-def test_fast_quotient_is_exact_when_decided():
-    zs = states(30000, 5) + undecided_states(300)
-    flagged = 0
-    for z in zs:
-        q_fast, fhi = quot_fast_model(z)
-        exact = (z << 53) // M40
-        # T = z*Rhi + z1*r1 exactly, and it falls short of z*R/2^64 by less than 2^33+2
-        full = z * R >> 64
-        tt = z * RHI + (z >> 32) * RL1
-        assert tt >> 64 == q_fast and 0 <= full - tt < 2 ** 33 + 2
-        if fhi >= 0xFFFFFFFC:
-            flagged += 1
-            assert q_fast in (exact, exact - 1)
-        else:
-            assert q_fast == exact, z
-    assert flagged >= 200
-    for z in undecided_states(300):
-        assert quot_fast_model(z)[1] >= 0xFFFFFFFC
 
 
 def test_fast_conversion_matches_the_exact_one():
@@ -246,47 +237,6 @@ def test_fast_conversion_matches_the_exact_one():
         q1 = (z1 << 53) // M40
         assert bits_fast_model(q0, q1) == bits_model(q0, q1), z
         assert f64_from_bits(bits_fast_model(q0, q1)) == trunc_quotient(z)
-
-
-def quot_fast_chain_model(z):
-    """The same T from the same five products, summed in 32-bit limbs with
-    add-with-carry chains (the kernel's PTX form): limb 0 only feeds its
-    carry, limb 1 is the high word of T mod 2^64, limbs 2-3 the quotient."""
-    m32 = 0xFFFFFFFF
-    a0, a1 = z & m32, z >> 32
-    h0, h1, r1 = H0, H1, RL1
-    w = a0 * h0
-    u = a1 * r1
-    v = a0 * h1
-    x = a1 * h0
-    y = a1 * h1
-    w0, w1, u0, u1 = w & m32, w >> 32, u & m32, u >> 32
-    v0, v1, x0, x1, y0, y1 = v & m32, v >> 32, x & m32, x >> 32, y & m32, y >> 32
-
-    def addc(p, q, cin):  # one 32-bit add with carry in and out
-        s = p + q + cin
-        return s & m32, s >> 32
-
-    _, c = addc(w0, u0, 0)           # chain A: limb 0, limb 1, carry into limb 2
-    s1, c = addc(w1, u1, c)
-    c2, _ = addc(0, 0, c)
-    s1, c = addc(s1, v0, 0)          # chain B: + a0*h1 at limb 1, + a1*h1 at limb 2
-    s2, c = addc(v1, y0, c)
-    s3, _ = addc(y1, 0, c)
-    s1, c = addc(s1, x0, 0)          # chain C: + a1*h0 at limb 1
-    s2, c = addc(s2, x1, c)
-    s3, _ = addc(s3, 0, c)
-    s2, c = addc(s2, c2, 0)          # chain D: chain A's carry into limb 2
-    s3, _ = addc(s3, 0, c)
-    assert s3 < 2 ** 32              # T < 2^118: no carry out of limb 3
-    return (s3 << 32) | s2, s1
-
-
-def test_fast_quotient_carry_chains_match():
-    zs = states(40000, 17) + undecided_states(300) + [2 ** 64 - 1, M40 - 1, 2 ** 63,
-                                                      (2 ** 32 - 1) << 32, 2 ** 32 - 1]
-    for z in zs:
-        assert quot_fast_chain_model(z) == quot_fast_model(z), z
 
 
 def bits_fast_funnel_model(q0, q1):

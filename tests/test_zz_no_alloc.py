@@ -5,10 +5,13 @@ under a framework whose allocator owns all device memory, or latency-critical
 paths that must not allocate -- by keeping the batched kernel's work table in
 a fixed device array inside the library.  This file is collected last so that
 a run stopping at its first failure has already run every other test.  The
-new entry point is called through the C ABI twice in a row, with different
-streams each time, and each call's output must equal, bit for bit, the output
-of the allocating entry point (rng_batch_create + rng_batch_launch) on the
-same inputs -- the exactness every other parity test in this suite uses.
+new entry point is called through the C ABI twice in a row: the first call on
+torch's current stream, the second on a separate CUDA stream created for it
+(started only after the first call has finished, so the two never overlap).
+Every stream of each call must equal, bit for bit, the oracle's variates and
+the output of the allocating entry point (rng_batch_create +
+rng_batch_launch) on the same inputs -- the exactness every other parity test
+in this suite uses.
 """
 import ctypes
 
@@ -30,13 +33,19 @@ def _bits(t):
     return t.view(torch.int64 if t.element_size() == 8 else torch.int32).cpu().numpy()
 
 
-def test_noalloc_batch_equals_the_allocating_batch_twice():
+def _oracle_bits(oracle_mod, start, offset, count, dtype):
+    want = oracle_mod.generate(int(start), int(offset), int(count), dtype)
+    return want.view(np.int64 if want.itemsize == 8 else np.int32)
+
+
+def test_noalloc_batch_equals_the_oracle_and_the_allocating_batch_twice(oracle_mod):
     import torch
     from paper_1206_1187_gb300 import inputs, rng
 
     assert torch.cuda.is_available()
     fn = rng.lib.rng_batch_generate_noalloc
     codes_of = {"f64": 0, "f32": 1, "u64": 2}
+    second = torch.cuda.Stream()  # the second call's own stream
     for call, (nstreams, seed) in enumerate([(150, 21), (600, 22)]):
         starts, offsets, counts, dtypes = inputs.small_batch(nstreams=nstreams, seed=seed,
                                                              max_len=30000)
@@ -44,16 +53,21 @@ def test_noalloc_batch_equals_the_allocating_batch_twice():
         b = rng.Batch(starts, counts, dtypes, outs=ref, offsets=offsets)
         b.launch()
         got = _tensors(counts, dtypes, -2.0)
+        torch.cuda.synchronize()  # nothing earlier overlaps the call
         codes = np.ascontiguousarray([codes_of[d] for d in dtypes], dtype=np.uint8)
         ptrs = (ctypes.c_void_p * nstreams)(*[t.data_ptr() for t in got])
-        stream = torch.cuda.current_stream().cuda_stream
+        cs = torch.cuda.current_stream() if call == 0 else second
         rc = fn(nstreams, ctypes.c_void_p(starts.ctypes.data), ctypes.c_void_p(offsets.ctypes.data),
                 ctypes.c_void_p(counts.ctypes.data), ctypes.c_void_p(codes.ctypes.data), ptrs,
-                None, ctypes.c_void_p(stream))
+                None, ctypes.c_void_p(cs.cuda_stream))
         assert rc == 0, rng.lib.rng_last_error()
+        cs.synchronize()
         torch.cuda.synchronize()
         for s in range(nstreams):
-            assert np.array_equal(_bits(got[s]), _bits(ref[s])), (call, s, dtypes[s])
+            g = _bits(got[s])
+            assert np.array_equal(g, _oracle_bits(oracle_mod, starts[s], offsets[s], counts[s],
+                                                  dtypes[s])), (call, s, dtypes[s])
+            assert np.array_equal(g, _bits(ref[s])), (call, s, dtypes[s])
         b.close()
 
 
