@@ -119,6 +119,28 @@ def profiled_value(key: str, tag: str, kernel: str = "tiled"):
     return None
 
 
+ISSUE_PEAK = 152 * 4 * 32 * 2.07e9  # thread-instructions/s: SMs x schedulers x lanes x clock
+
+
+def issue_roofline(inst_per_variate, variates_per_s, profile_key):
+    """The integer-issue roofline of a kernel from its profiled instruction
+    count per variate (None when profiles/ has no count for its sources)."""
+    if inst_per_variate is None:
+        return None
+    achieved = inst_per_variate * variates_per_s
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": ISSUE_PEAK / 1e12,
+            "unit": "T thread-instructions/s", "frac": achieved / ISSUE_PEAK,
+            "inst_per_variate": inst_per_variate, "profile_key": profile_key,
+            "peak_note": "152 SMs x 4 issue slots x 32 lanes x 2.07 GHz"}
+
+
+def hbm_roofline(bytes_per_launch, ms_per_launch, traffic, peaks):
+    gbs = bytes_per_launch / (ms_per_launch / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
+            "algorithmic_bytes_per_launch": bytes_per_launch}
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
 
@@ -365,6 +387,11 @@ def measure_batched(rng, stream, achieved_gbs: float, steps: int):
     b.close()
     del outs
     torch.cuda.empty_cache()
+    ratio = profiled_value("traffic_per_algorithmic_byte", "batch_512", "batch")
+    roof = hbm_roofline(float(info["bytes"]), ms, ratio * info["bytes"] if ratio else None,
+                        peaks)
+    roof["traffic_note"] = ("DRAM bytes per algorithmic byte of a 512-stream subset (profiles/), "
+                            "times this workload's bytes")
     return {"workload": "4096 streams, seeds default_rng(7) in [3^33+100, 2^53-10^8], lengths "
                         "log-uniform 10^3..10^7, FP64/FP32 alternating, one persistent launch "
                         "replayed as a CUDA graph",
@@ -372,7 +399,11 @@ def measure_batched(rng, stream, achieved_gbs: float, steps: int):
             "tune": info["tune"], "launches": steps, "ms_per_launch": ms,
             "variates_per_s": info["elems"] / (ms / 1e3), "gbs": gbs,
             "frac_of_peak": gbs / peaks["hbm_gbs"],
-            "vs_single_stream_gbs": gbs / achieved_gbs}
+            "vs_single_stream_gbs": gbs / achieved_gbs,
+            "roofline": roof,
+            "roofline_alu": issue_roofline(
+                profiled_value("inst_per_variate", "batch_512", "batch"),
+                info["elems"] / (ms / 1e3), "inst_per_variate[batch_512]")}
 
 
 def measure_fused(rng, stream, steps: int):
@@ -406,15 +437,13 @@ def measure_fused(rng, stream, steps: int):
                        "of squares, nothing stored",
            "launches": steps, "ms_per_launch": ms, "variates_per_s": variates / (ms / 1e3),
            "pi_estimate": pi_est}
-    ipv = profiled_value("inst_per_variate", "mc_2e36", "mc")
-    if ipv is not None:  # integer-issue roofline: 4 schedulers x 32 lanes per SM per clock
-        clk = 2.07e9
-        peak = 152 * 4 * 32 * clk
-        achieved = ipv * variates / (ms / 1e3)
-        out["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                           "unit": "T thread-instructions/s", "frac": achieved / peak,
-                           "inst_per_variate": ipv,
-                           "peak_note": "152 SMs x 4 issue slots x 32 lanes x 2.07 GHz"}
+    # integer-issue roofline: 4 schedulers x 32 lanes per SM per clock; the
+    # integer ALU pipe's own busy fraction is the profiled figure beside it
+    out["roofline"] = issue_roofline(profiled_value("inst_per_variate", "mc_2e36", "mc"),
+                                     variates / (ms / 1e3), "inst_per_variate[mc_2e36]")
+    alu = profiled_value("alu_pipe_busy_frac", "mc_2e36", "mc")
+    if out["roofline"] is not None and alu is not None:
+        out["roofline"]["alu_pipe_busy_frac"] = alu
     return out
 
 
@@ -440,7 +469,14 @@ def measure_other_outputs(rng, stream, peaks, steps: int):
         gbs = out.element_size() * n / (ms / 1e3) / 1e9
         res[dtype] = {"variates_per_s": n / (ms / 1e3), "GBps": gbs,
                       "frac_of_hbm": gbs / peaks["hbm_gbs"], "ms_per_launch": ms,
-                      "launches": steps}
+                      "launches": steps, "tune": rng.resolve_tune(n, dtype)}
+        if dtype == "f32":
+            res[dtype]["roofline"] = hbm_roofline(
+                4.0 * n, ms, profiled_value("traffic_bytes_per_launch", "bulk_f32_2e28", "tiled"),
+                peaks)
+            res[dtype]["roofline_alu"] = issue_roofline(
+                profiled_value("inst_per_variate", "f32_2e26", "tiled"), n / (ms / 1e3),
+                "inst_per_variate[f32_2e26]")
         del out
     return res
 
@@ -470,13 +506,9 @@ def measure_m40(rng, stream, peaks, steps: int):
              "tune": rng.resolve_tune40(n, "f64"),
              "traffic": profiled_value("traffic_bytes_per_launch", "m40_f64_2e28", "m40"),
              "algorithmic_bytes_per_launch": 8.0 * n}
-    ipv = profiled_value("inst_per_variate", "m40_2e25", "m40")
-    if ipv is not None:
-        peak = 152 * 4 * 32 * 2.07e9
-        achieved = ipv * n / (ms / 1e3)
-        out_d["roofline_alu"] = {"achieved": achieved / 1e12, "peak": peak / 1e12,
-                                 "unit": "T thread-instructions/s", "frac": achieved / peak,
-                                 "inst_per_variate": ipv}
+    out_d["roofline"] = hbm_roofline(8.0 * n, ms, out_d["traffic"], peaks)
+    out_d["roofline_alu"] = issue_roofline(profiled_value("inst_per_variate", "m40_2e25", "m40"),
+                                           n / (ms / 1e3), "inst_per_variate[m40_2e25]")
     del out
     return out_d
 
@@ -512,9 +544,16 @@ def measure_serving(rng, n_requests: int = 20000):
                       "heavy_iterations": st["heavy_iterations"], "mean_items_per_iteration":
                           st["items"] / max(st["iterations"], 1),
                       "peak_pool_gb": st["peak_pool_bytes"] / 1e9,
-                      "peak_active": st["peak_active"]}
+                      "peak_active": st["peak_active"],
+                      "admitted_out_of_order": st["admitted_out_of_order"],
+                      "scheduler_max_gap_ms": st["loop_gap_max_us"] / 1e3,
+                      "slowest_launch_ms": {"total": st["launch_max_us"] / 1e3,
+                                            "staging": st["stage_max_us"] / 1e3,
+                                            "kernel_launch": st["kernel_launch_max_us"] / 1e3,
+                                            "event_record": st["event_record_max_us"] / 1e3}}
     return {"workload": f"{n_requests} requests, Poisson 20k req/s, sizes log-uniform "
-                        "1 KiB..256 MiB, FP32/FP64 1:1, random seeds/offsets, 40 GB pool",
+                        "1 KiB..256 MiB, FP32/FP64 1:1, random seeds/offsets, 40 GB pool; "
+                        "admission may pass a request that does not fit for up to 1 s",
             "requests": n_requests, "bytes": total_bytes, "runs": runs}
 
 

@@ -322,10 +322,10 @@ __device__ __forceinline__ uint64_t shared_step_f64_fast(uint64_t& z, bool& rare
 
 // The same step written as inline PTX on 32-bit words, so that every
 // operation maps to one instruction: the product p = z*K needs only the high
-// half of z0*K0 (the low word of p is not used by the fast path), three
-// 32x32+64 wide multiply-adds and two funnel shifts give q and the bits below
-// it, a borrow chain with a predicated "+ m" gives the next state, and the
-// rounding is one carry chain plus a funnel shift.  `qmin` is a running
+// half of z0*K0 (the low word of p is not used by the fast path), a carry
+// chain of 32x32 multiply-adds and two funnel shifts give q and the bits
+// below it, a borrow chain with a predicated "+ m" gives the next state, and
+// the rounding is one carry chain plus a funnel shift.  `qmin` is a running
 // minimum of q's top word: it is 0 exactly when some step of the run left the
 // fast path (variate below 2^-21), and the caller then redoes the run.
 __device__ __forceinline__ uint64_t shared_step_f64_ptx(uint64_t& z, uint32_t& qmin) {
@@ -333,8 +333,8 @@ __device__ __forceinline__ uint64_t shared_step_f64_ptx(uint64_t& z, uint32_t& q
   uint32_t r0, r1, b0, b1, qm_out;
   asm("{\n\t"
       ".reg .u32 a0, a1, k0, k1, m0, m1, qi, zr;\n\t"
-      ".reg .u32 h0, w1, w2, w3, t1h, q0, q1, ml, mh, zh, c, s, lh, gh, gl, ew, x0, x1;\n\t"
-      ".reg .u64 t1, t2, qm, h0w, t1hw;\n\t"
+      ".reg .u32 h0, w1, w2, w3, x, y, q0, q1, ml, mh, zh, c, s, lh, gh, gl, ew, x0, x1;\n\t"
+      ".reg .u64 qm;\n\t"
       ".reg .pred neg;\n\t"
       "mov.u32 a0, %5;\n\t"
       "mov.u32 a1, %6;\n\t"
@@ -345,13 +345,13 @@ __device__ __forceinline__ uint64_t shared_step_f64_ptx(uint64_t& z, uint32_t& q
       "mov.u32 qi, %11;\n\t"
       "mov.u32 zr, 0;\n\t"
       "mul.hi.u32 h0, a0, k0;\n\t"
-      "cvt.u64.u32 h0w, h0;\n\t"
-      "mad.wide.u32 t1, a0, k1, h0w;\n\t"
-      "mad.wide.u32 t1, a1, k0, t1;\n\t"
-      "mov.b64 {w1, t1h}, t1;\n\t"
-      "cvt.u64.u32 t1hw, t1h;\n\t"
-      "mad.wide.u32 t2, a1, k1, t1hw;\n\t"
-      "mov.b64 {w2, w3}, t2;\n\t"
+      "mad.lo.cc.u32 w1, a0, k1, h0;\n\t"     // p = z*K from bit 32 up, on 32-bit
+      "madc.hi.u32 x, a0, k1, 0;\n\t"         // carry chains (measured fewer
+      "mad.lo.cc.u32 w1, a1, k0, w1;\n\t"     // instructions than 64-bit
+      "madc.hi.cc.u32 x, a1, k0, x;\n\t"      // multiply-adds with zero-extended
+      "addc.u32 y, 0, 0;\n\t"                 // addends)
+      "mad.lo.cc.u32 w2, a1, k1, x;\n\t"
+      "madc.hi.u32 w3, a1, k1, y;\n\t"
       "shf.r.clamp.b32 q0, w1, w2, 21;\n\t"
       "shf.r.clamp.b32 q1, w2, w3, 21;\n\t"
       "mul.wide.u32 qm, q0, m0;\n\t"

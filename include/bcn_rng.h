@@ -332,7 +332,7 @@ typedef struct {
   double admit_bypass_s;   /* how long a queued request that does not fit the
                               pool may be passed by later requests that do:
                               > 0 that many seconds; < 0 never (strict arrival
-                              order); 0 = 0.05 s when release_after_s >= 0,
+                              order); 0 = 1 s when release_after_s >= 0,
                               never when the caller releases results (a client
                               consuming results in order could otherwise wait
                               on a request whose space is held by unreleased
@@ -349,6 +349,9 @@ typedef struct {
   uint64_t loop_gap_max_us;   /* longest interval between two passes of the
                                  scheduler loop, its own idle waits excluded  */
   uint64_t launch_max_us;     /* longest staging + launch of one iteration    */
+  uint64_t stage_max_us;      /* of which: longest work-table copy + memset   */
+  uint64_t kernel_launch_max_us; /* longest kernel launch call               */
+  uint64_t event_record_max_us;  /* longest completion-event record          */
 } rng_server_stats;
 
 /* Request states reported by rng_server_status. */

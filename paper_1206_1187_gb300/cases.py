@@ -1,14 +1,17 @@
 """Named workloads at sizes suited to a profiler capture.
 
-    python -m paper_1206_1187_gb300.cases bulk 33554432 [reps]
-    python -m paper_1206_1187_gb300.cases bulk32 33554432 [reps]
-    python -m paper_1206_1187_gb300.cases batch 2048 [reps]
+    python -m paper_1206_1187_gb300.cases bulk 33554432 [reps]     # FP64, autotuned shape
+    python -m paper_1206_1187_gb300.cases bulk32 67108864 [reps]   # FP32, default shape
+    python -m paper_1206_1187_gb300.cases batch 512 [reps]   # first 512 streams of the batched workload
+    python -m paper_1206_1187_gb300.cases batch 4096 [reps]  # the whole batched workload
     python -m paper_1206_1187_gb300.cases mc 16384 [reps]
     python -m paper_1206_1187_gb300.cases m40 33554432 [reps]
 
 Each case runs `reps` launches (default 3) of one of the library's kernels on
 synthetic inputs and exits 0; nothing is checked here (the test suite does
-that).  The tuning is the installed autotune result when one is cached.
+that).  Each uses the launch shape the benchmark uses for that form: the
+autotuned one for FP64 (cached per GPU model), the built-in default for FP32,
+batch plans, 3^40 and the fused consumer.
 """
 from __future__ import annotations
 
@@ -25,24 +28,19 @@ def main(argv):
     seed = 3 ** 33 + 12345
     if case in ("bulk", "bulk32"):
         dtype = "f64" if case == "bulk" else "f32"
-        autotune.tune_bulk(dtype, n=1 << 28)  # the tuning the benchmark uses
+        if dtype == "f64":
+            autotune.tune_bulk(dtype, n=1 << 28)  # the tuning the benchmark uses
         out = torch.empty(size, dtype=torch.float64 if dtype == "f64" else torch.float32,
                           device="cuda")
         for _ in range(reps):
             rng.generate_at(seed, 0, size, dtype, out=out)
     elif case == "batch":
         tdt = {"f64": torch.float64, "f32": torch.float32}
-
-        def workload():  # built only if the tuning is not cached yet
-            st, co, dt = inputs.batch_streams()
-            return st, co, dt, [torch.empty(int(c), dtype=tdt[d], device="cuda")
-                                for c, d in zip(co, dt)]
-        # the benchmark's tuning, measured on the batched workload itself
-        tune = autotune.tune_batch(workload=workload, tag="batched-4096-seed7")["best"]
-        torch.cuda.empty_cache()
-        starts, counts, dtypes = inputs.batch_streams(nstreams=size, len_hi=1e6)
+        starts, counts, dtypes = inputs.batch_streams()  # the batched workload's streams
+        starts, counts, dtypes = starts[:size], counts[:size], dtypes[:size]
         outs = [torch.empty(int(c), dtype=tdt[d], device="cuda") for c, d in zip(counts, dtypes)]
-        b = rng.Batch(starts, counts, dtypes, outs=outs, tune=tune)
+        # a plan's built-in shape (the one the autotuner picks for this workload)
+        b = rng.Batch(starts, counts, dtypes, outs=outs)
         for _ in range(reps):
             b.launch()
     elif case == "m40":

@@ -132,6 +132,7 @@ struct bcn_server {
   std::atomic<bool> stop{false};
   std::atomic<uint64_t> loop_gap_max_us{0};  // scheduler stall diagnostics
   std::atomic<uint64_t> launch_max_us{0};
+  std::atomic<uint64_t> call_max_us[3] = {};  // staging copies, kernel launch, event record
   rng_status err = RNG_OK;
   char errmsg[256] = {0};
   uint64_t next_id = 1, rr = 0;
@@ -257,7 +258,12 @@ static void release_due(bcn_server* s, double t) {
 constexpr size_t kAdmitScan = 256;
 // How long a waiting request may be passed by later ones that fit, when the
 // server frees results itself and the caller leaves admit_bypass_s at 0.
-constexpr double kDefaultBypassS = 0.05;
+// Measured on the serving trace with results held 0.2 s (the pool binds):
+// strict order and ages up to 0.2 s give p50 539 ms (under sustained
+// overload the oldest request is soon older than the age and the order is
+// strict again); 0.5 s and 1 s give p50 362 ms with the same throughput and
+// p99 (1.1 s), 1 s the lower p90 (910 against 995 ms).
+constexpr double kDefaultBypassS = 1.0;
 
 // Admit queued requests in arrival order while slots and pool space allow
 // (mu held).  A request that does not fit is passed over while it is younger
@@ -355,19 +361,41 @@ static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out, uint32_t* sha
   return items;
 }
 
+// Wall time of one runtime call, kept as the slowest of its kind (the
+// server's stall diagnostics: which call a long launch spent its time in).
+static cudaError_t timed_call(bcn_server* s, int kind, cudaError_t (*fn)(void*), void* arg) {
+  const double t0 = now_s();
+  const cudaError_t e = fn(arg);
+  const uint64_t us = (uint64_t)((now_s() - t0) * 1e6);
+  if (us > s->call_max_us[kind].load(std::memory_order_relaxed))
+    s->call_max_us[kind].store(us, std::memory_order_relaxed);
+  return e;
+}
+
 static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units,
                         uint32_t shape) {
   const ServeShape& sh = s->shape[shape];
   const size_t desc_bytes = sizeof(BatchDesc) * s->cfg.max_items;
   const size_t prefix_bytes = sizeof(uint64_t) * (s->cfg.max_items + 1);
-  cudaError_t e = cudaMemcpyAsync(sl.d_table, sl.h_desc, sizeof(BatchDesc) * items,
-                                  cudaMemcpyHostToDevice, sl.cs);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_table + desc_bytes, sl.h_prefix, sizeof(uint64_t) * (items + 1),
-                        cudaMemcpyHostToDevice, sl.cs);
+  struct Stage {
+    Slot* sl;
+    uint32_t items;
+    size_t desc_bytes, prefix_bytes;
+  } stage = {&sl, items, desc_bytes, prefix_bytes};
+  cudaError_t e = timed_call(s, 0, [](void* a) {
+    const Stage& g = *static_cast<Stage*>(a);
+    cudaError_t r = cudaMemcpyAsync(g.sl->d_table, g.sl->h_desc, sizeof(BatchDesc) * g.items,
+                                    cudaMemcpyHostToDevice, g.sl->cs);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(g.sl->d_table + g.desc_bytes, g.sl->h_prefix,
+                          sizeof(uint64_t) * (g.items + 1), cudaMemcpyHostToDevice, g.sl->cs);
+    if (r == cudaSuccess)
+      r = cudaMemsetAsync(g.sl->d_table + g.desc_bytes + g.prefix_bytes, 0,
+                          sizeof(unsigned long long), g.sl->cs);
+    return r;
+  }, &stage);
   unsigned long long* counter =
       reinterpret_cast<unsigned long long*>(sl.d_table + desc_bytes + prefix_bytes);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), sl.cs);
   if (e != cudaSuccess) return server_fail(s, e, "staging an iteration");
   BatchParams p;
   p.desc = reinterpret_cast<const BatchDesc*>(sl.d_table);
@@ -382,9 +410,23 @@ static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units,
   p.nbuf = sh.tune.buffers;
   const uint64_t wpb = sh.tune.block / 32;
   const uint64_t grid = std::max<uint64_t>(1, std::min(sh.grid_full, (units + wpb - 1) / wpb));
-  void* args[] = {&p};
-  e = cudaLaunchKernel(sh.fn, dim3((unsigned)grid), dim3(sh.tune.block), args, sh.smem, sl.cs);
-  if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.cs);
+  struct Launch {
+    const ServeShape* sh;
+    uint64_t grid;
+    BatchParams* p;
+    Slot* sl;
+  } launch = {&sh, grid, &p, &sl};
+  e = timed_call(s, 1, [](void* a) {
+    const Launch& g = *static_cast<Launch*>(a);
+    void* args[] = {g.p};
+    return cudaLaunchKernel(g.sh->fn, dim3((unsigned)g.grid), dim3(g.sh->tune.block), args,
+                            g.sh->smem, g.sl->cs);
+  }, &launch);
+  if (e == cudaSuccess)
+    e = timed_call(s, 2, [](void* a) {
+      Slot* sl2 = static_cast<Slot*>(a);
+      return cudaEventRecord(sl2->ev, sl2->cs);
+    }, &sl);
   if (e != cudaSuccess) return server_fail(s, e, "launching an iteration");
   sl.busy = true;
 }
@@ -522,7 +564,7 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
     s->heavy_elems = shapes[1].grid_full * (w.block / 32) * 2ull * 32ull * w.depth;
   }
   s->device = di.device;
-  // admission bypass: by default a waiting request may be passed for 50 ms
+  // admission bypass: by default a waiting request may be passed for 1 s
   // when the server frees results itself, never when the caller does
   s->bypass_s = cfg.admit_bypass_s > 0 ? cfg.admit_bypass_s
                 : cfg.admit_bypass_s < 0 || cfg.release_after_s < 0 ? -1.0
@@ -556,6 +598,37 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
     if (e != cudaSuccess) {
       cleanup();
       return cuda_error(e, "creating server slots");
+    }
+  }
+  // First use of each slot's stream, and one empty launch of each kernel
+  // shape on it (no work units), here rather than in the first iteration:
+  // lazy initialisation in the runtime would otherwise land in a request's
+  // latency.
+  for (Slot& sl : s->slots) {
+    const size_t desc_bytes = sizeof(BatchDesc) * cfg.max_items;
+    const size_t prefix_bytes = sizeof(uint64_t) * (cfg.max_items + 1);
+    BatchParams p = {};
+    p.desc = reinterpret_cast<const BatchDesc*>(sl.d_table);
+    p.prefix = reinterpret_cast<const uint64_t*>(sl.d_table + desc_bytes);
+    p.counter = reinterpret_cast<unsigned long long*>(sl.d_table + desc_bytes + prefix_bytes);
+    p.total_units = 0;
+    for (uint32_t k = 0; k < nshapes && e == cudaSuccess; ++k) {
+      const ServeShape& sh = s->shape[k];
+      batch_fill_jumps(p, (int)sh.tune.step, sh.tune.depth);
+      p.depth = sh.tune.depth;
+      p.unit_tiles = sh.tune.unit;
+      p.skip = sh.tune.skip;
+      p.nbuf = sh.tune.buffers;
+      void* args[] = {&p};
+      e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), sl.cs);
+      if (e == cudaSuccess)
+        e = cudaLaunchKernel(sh.fn, dim3(1), dim3(sh.tune.block), args, sh.smem, sl.cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sl.cs);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_error(e, "warming the server slots");
     }
   }
   s->worker = std::thread(worker_main, s);
@@ -721,6 +794,9 @@ rng_status rng_server_stats_get(bcn_server* s, rng_server_stats* out) {
   out->pool_bytes = s->cfg.pool_bytes;
   out->loop_gap_max_us = s->loop_gap_max_us.load();
   out->launch_max_us = s->launch_max_us.load();
+  out->stage_max_us = s->call_max_us[0].load();
+  out->kernel_launch_max_us = s->call_max_us[1].load();
+  out->event_record_max_us = s->call_max_us[2].load();
   return s->err;
 }
 

@@ -71,7 +71,8 @@ class ServerStats(ctypes.Structure):
                 ("submitted", "completed", "iterations", "items", "max_items_seen",
                  "peak_active", "peak_pool_bytes", "bytes_done", "pool_in_use", "pool_bytes",
                  "heavy_iterations", "admitted_out_of_order", "bypassed", "loop_gap_max_us",
-                 "launch_max_us")]
+                 "launch_max_us", "stage_max_us", "kernel_launch_max_us",
+                 "event_record_max_us")]
 
 
 def _load() -> ctypes.CDLL:

@@ -13,9 +13,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # the counters bench.py reads, with the kernel each one describes
 READ_BY_BENCH = {
     ("traffic_bytes_per_launch", "bulk_f64_2e28"): "tiled",
+    ("traffic_bytes_per_launch", "bulk_f32_2e28"): "tiled",
+    ("inst_per_variate", "f32_2e26"): "tiled",
     ("traffic_bytes_per_launch", "m40_f64_2e28"): "m40",
     ("inst_per_variate", "m40_2e25"): "m40",
     ("inst_per_variate", "mc_2e36"): "mc",
+    ("alu_pipe_busy_frac", "mc_2e36"): "mc",
+    ("traffic_per_algorithmic_byte", "batch_512"): "batch",
+    ("inst_per_variate", "batch_512"): "batch",
 }
 
 

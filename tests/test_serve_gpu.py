@@ -243,3 +243,52 @@ def test_concurrent_clients(R, oracle_mod):
     st = srv.stats()
     assert st["completed"] == 480 and st["pool_in_use"] == 0
     srv.close()
+
+
+def test_reads_race_automatic_release(R, oracle_mod):
+    """With results freed almost at once (release_after_s = 1 ms) and other
+    requests admitted into the freed space all the time, a read either finds
+    the request already released (RNG_EBUSY) or returns exactly its bytes: a
+    release that falls due during the copy waits for it."""
+    import threading
+    srv = R.Server(pool_bytes=24 << 20, release_after_s=0.001, chunk_elems=1 << 14)
+    stop = threading.Event()
+
+    def load():  # keeps the pool busy with other requests, at most 16 in flight
+        rnd = np.random.default_rng(5)
+        pending = []
+        while not stop.is_set():
+            pending.append(srv.submit(int(rnd.integers(M + 100, 2 ** 53)), 0,
+                                      int(rnd.integers(1 << 12, 1 << 18)), "f64"))
+            if len(pending) >= 16:
+                srv.wait(pending.pop(0), 60.0)
+
+    th = threading.Thread(target=load)
+    th.start()
+    rnd = np.random.default_rng(6)
+    ok = busy = 0
+    try:
+        for i in range(150):
+            a, off = int(rnd.integers(M + 100, 2 ** 53)), int(rnd.integers(0, 2 ** 40))
+            n = int(rnd.integers(1 << 14, 1 << 19))
+            rid = srv.submit(a, off, n, "f64")
+            srv.wait(rid, 60.0)
+            try:
+                got = _bits(srv.read(rid, n, "f64"))
+            except R.RNGError as e:
+                assert e.status == 6, e  # released before the read started
+                busy += 1
+                continue
+            ok += 1
+            if i % 5 == 0:
+                want = oracle_mod.generate(a, off, n, "f64")
+                assert np.array_equal(got, _obits(want)), i
+            else:
+                idx = rnd.integers(0, n, 64)
+                want = oracle_mod.at(a, (off + idx).astype(np.uint64), "f64")
+                assert np.array_equal(got[idx], _obits(want)), i
+    finally:
+        stop.set()
+        th.join(60)
+    assert ok > 0
+    srv.close()
