@@ -56,7 +56,9 @@ def parse_args():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--n", "--variates", dest="n", type=int, default=N_DEFAULT,
+                   help="variates per GPU per step (--variates under torchrun, whose own "
+                        "options --n would abbreviate)")
     p.add_argument("--e2e-steps", type=int, default=7)
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="target CPU time of the oracle baseline sample")
@@ -666,15 +668,22 @@ def run_ours(args):
     from paper_1206_1187_gb300 import rng
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
+    # one rank per GPU; BCN_BENCH_BACKEND=gloo runs the multi-rank path with
+    # ranks sharing the visible GPUs (no kernel of one rank waits on another's)
+    backend = os.environ.get("BCN_BENCH_BACKEND", "nccl")
+    gpu = local % max(torch.cuda.device_count(), 1)
+    torch.cuda.set_device(gpu)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", gpu))
+        else:
+            dist.init_process_group(backend)
     from paper_1206_1187_gb300 import shard
     n = args.n
     offset, _ = shard.shard_range(rank, world, n)  # skip-ahead shard, no data exchange
-    dev = torch.device("cuda", local)
+    dev = torch.device("cuda", gpu)
     tuned = None
     if not args.no_autotune:  # measured choice of step, conversion and tile shape
         from paper_1206_1187_gb300 import autotune

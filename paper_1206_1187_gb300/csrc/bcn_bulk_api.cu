@@ -1,6 +1,7 @@
 // bcn_bulk_api.cu -- host side of single-stream generation: the launch
 // shape a call resolves to (tile depth, block, chains, buffers, grid) and the
 // launch itself.  The kernels are in bcn_bulk.cu.
+#include <algorithm>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -47,6 +48,8 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
                         bool constant) {
   rng_tune t = {};
   if (tune) t = *tune;
+  // a block the caller (or BCN_RNG_TUNE) chose, before installed defaults fill it
+  const bool caller_block = t.block != 0 || (!constant && env_tune_sets_block());
   if (!constant) {  // zero fields take the installed (measured) defaults
     const rng_status env = env_tune_check();
     if (env != RNG_OK) return env;
@@ -147,6 +150,20 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
     if (L.smem_bytes > di.smem_optin)
       return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
                        L.smem_bytes, di.smem_optin);
+    // A call with too few tiles to give every SM a full block takes blocks
+    // just large enough to spread its tiles over all SMs (whole groups of four
+    // warps from four warps up), unless the caller chose the block or the
+    // grid: 10^6 FP64 variates ran 14.8 us in 896-thread blocks on 36 SMs and
+    // 9.2 us in 256-thread blocks on 126.
+    if (!caller_block && !t.grid) {
+      const uint64_t per_sm = (tile_count(n, 0, L.depth) + di.sms - 1) / di.sms;
+      uint64_t b = std::max<uint64_t>(per_sm, 1) * 32;
+      if (b >= 128) b = (b + 127) / 128 * 128;
+      if (b < L.block) {
+        L.block = (uint32_t)b;
+        L.smem_bytes = (size_t)(L.block / 32) * warp_bytes;
+      }
+    }
     if (t.grid) {
       L.grid = t.grid;
     } else {

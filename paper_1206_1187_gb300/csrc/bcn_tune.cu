@@ -120,6 +120,11 @@ rng_tune auto_defaults(int dt) {
   return g_auto[dt];
 }
 
+bool env_tune_sets_block() {
+  std::call_once(g_env_once, load_env_tune);
+  return g_env_set && !g_env_err[0] && g_env.block != 0;
+}
+
 rng_status env_tune_check() {
   std::call_once(g_env_once, load_env_tune);
   if (g_env_set && g_env_err[0]) return set_error(RNG_EINVAL, "BCN_RNG_TUNE: %s", g_env_err);

@@ -455,3 +455,21 @@ def test_fp32_near_float_boundaries(R, oracle_mod):
         b.launch()
         assert_same(outs[0], want, f"batch {z}")
         b.close()
+
+
+def test_small_calls_spread_their_tiles_over_every_sm(R, oracle_mod):
+    """A call with too few tiles to give every SM a full block takes smaller
+    blocks (unless the caller names the block or the grid); the output does
+    not change."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for dtype, n in (("f64", 10 ** 6), ("f32", 10 ** 6), ("f64", 3 * 10 ** 5)):
+        auto = R.resolve_tune(n, dtype)
+        tiles = n // (32 * auto["depth"])
+        assert auto["block"] < 896 and auto["block"] % 32 == 0, (dtype, n, auto)
+        assert auto["grid"] * auto["block"] // 32 >= min(tiles, sms), (dtype, n, auto)
+        assert R.resolve_tune(n, dtype, R.make_tune(block=896))["block"] == 896
+        assert R.resolve_tune(n, dtype, R.make_tune(grid=16))["block"] == 896
+        a = M + 1618
+        assert_same(R.generate_at(a, 99, n, dtype), oracle_mod.generate(a, 99, n, dtype), dtype)
+    assert R.resolve_tune(1 << 28, "f64")["block"] == 896
