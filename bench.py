@@ -121,7 +121,11 @@ def profiled_value(key: str, tag: str, kernel: str = "tiled"):
     return None
 
 
-ISSUE_PEAK = 152 * 4 * 32 * 2.07e9  # thread-instructions/s: SMs x schedulers x lanes x clock
+SMS, SM_MAX_GHZ = 152, 2.07
+ISSUE_PEAK = SMS * 4 * 32 * SM_MAX_GHZ * 1e9  # thread-instructions/s: SMs x schedulers x lanes x clock
+# FP64 operations per SM per clock: 1.25 TFLOP/s of FP64 FMA on 152 SMs at 2.07 GHz;
+# the fused kernel's profile (one multiply per variate, pipe 74% busy) agrees
+FP64_OPS_PER_SM_CLK = 2
 
 
 def issue_roofline(inst_per_variate, variates_per_s, profile_key):
@@ -446,6 +450,14 @@ def measure_fused(rng, stream, steps: int):
     alu = profiled_value("alu_pipe_busy_frac", "mc_2e36", "mc")
     if out["roofline"] is not None and alu is not None:
         out["roofline"]["alu_pipe_busy_frac"] = alu
+    # every variate's RN(v*v) is one FP64 multiply; the FP64 pipe retires
+    # about 2 operations per SM per clock, a ceiling on this form's rate
+    fp64 = profiled_value("fp64_pipe_busy_frac", "mc_2e36", "mc")
+    if out["roofline"] is not None and fp64 is not None:
+        ceiling = FP64_OPS_PER_SM_CLK * SMS * SM_MAX_GHZ * 1e9
+        out["roofline"]["fp64_pipe_busy_frac"] = fp64
+        out["roofline"]["fp64_ceiling_variates_per_s"] = ceiling
+        out["roofline"]["frac_of_fp64_ceiling"] = out["variates_per_s"] / ceiling
     return out
 
 

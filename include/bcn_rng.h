@@ -254,7 +254,7 @@ rng_status rng_batch_destroy(bcn_batch *b);
  *   - The first call on a device, with that device current, looks up the
  *     array's device address, and the first call with each kernel shape
  *     (step, conversion, chains, depth) sets that kernel's shared-memory
- *     limit; make those calls before any stream capture on the device.
+ *     limit.
  *   - Every call rewrites the one shared table and clears its work counter:
  *     calls whose work overlaps on the GPU (on different streams, or from
  *     different host threads' streams) race and must be serialised by the
@@ -462,15 +462,16 @@ rng_status rng_consume_mc(uint64_t start_index, uint64_t block0, uint64_t nblock
  * order-free) and round once with rng_mc_round_totals.
  *   totals: caller-owned device array of RNG_MC_TOTAL_WORDS uint64 words,
  *   8-byte aligned (NULL: plain rng_consume_mc), zeroed by the call.  For
- *   k < 4, word k is the sum over the call's blocks of bits 32k..32k+31 of
- *   the block's exact sum of v * 2^105; for k < 6, word 4+k the same of the
- *   block's exact sum of RN(v*v) * 2^157.  So the words T stand for
- *     sum of v      = (T[0] + T[1] 2^32 + T[2] 2^64 + T[3] 2^96) * 2^-105,
- *     sum of RN(v^2) = (T[4] + T[5] 2^32 + ... + T[9] 2^160) * 2^-157.
+ *   k < 5, word k is the sum over the call's blocks of bits 32k..32k+31 of
+ *   the block's exact sum of v * 2^105 (below 2^138); for k < 6, word 5+k
+ *   the same of the block's exact sum of RN(v*v) * 2^157 (below 2^190).  So
+ *   the words T stand for
+ *     sum of v      = (T[0] + T[1] 2^32 + ... + T[4] 2^128) * 2^-105,
+ *     sum of RN(v^2) = (T[5] + T[6] 2^32 + ... + T[10] 2^160) * 2^-157.
  *   Each word gains less than 2^32 per block, so word arrays stay exact for
  *   up to 2^32 blocks in all (a call of more blocks is RNG_ERANGE).
  * Other arguments, outputs and errors as rng_consume_mc. */
-#define RNG_MC_TOTAL_WORDS 10
+#define RNG_MC_TOTAL_WORDS 11
 rng_status rng_consume_mc_totals(uint64_t start_index, uint64_t block0, uint64_t nblocks,
                                  uint64_t len, uint64_t *hits_total, uint64_t *hits, double *sum,
                                  double *sumsq, uint64_t *totals, void *cuda_stream,

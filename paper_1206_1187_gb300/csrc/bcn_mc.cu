@@ -9,14 +9,17 @@
 //   sum   = RN(exact sum of v),   sumsq = RN(exact sum of RN(v*v)),
 // with RN round-to-nearest-even.  Everything is decided in integers:
 //   * every variate is a multiple of 2^-105 below 1, so v*2^105 is an integer
-//     below 2^105 and a lane's sum fits 128 bits;
+//     below 2^105 and a block's sum (len <= 2^33) fits 138 bits, kept in
+//     three 64-bit words;
 //   * every RN(v*v) is a multiple of 2^-157 (the smallest variate is about
 //     1.62*2^-53, so the smallest square has exponent -105), so RN(v*v)*2^157
 //     is an integer below 2^157.  For every variate above about 2^-20 its low
 //     64 bits are zero, so those squares are summed exactly as 128-bit
 //     integers on the 2^-93 grid; the rare smaller ones (below 2^117 on the
 //     2^-157 grid) go to a second 128-bit sum, and the two are joined into one
-//     192-bit integer per block;
+//     192-bit integer per block.  Chunks whose variates are all at least
+//     2^-16 (nearly all) take their squares on the coarser 2^-84 grid, where
+//     every such square is an integer below 2^84, and fold them in;
 //   * RN(X + Y) <= 1 exactly when X + Y <= 1 + 2^-53 (the tie rounds to the
 //     even 1.0), i.e. when the two grid integers sum to at most 2^157 + 2^104.
 //     That bound is a multiple of 2^64, so the test can be made on the 2^-93
@@ -97,17 +100,6 @@ __device__ __forceinline__ Terms variate_terms_fp64(uint64_t bits) {
   return t;
 }
 
-// The fast-grid image of RN(v*v) for a variate v >= 2^-20, as every variate
-// of a kept chunk is: RN(v*v) >= 2^-40, so its image on the 2^-157 grid is
-// M2 << k with k = e2 - 918 >= 65, and RN(v*v) * 2^93 = M2 << (e2 - 982)
-// exactly, with no branch on the square's size.
-__device__ __forceinline__ void square_fast_fp64(uint64_t bits, uint64_t& q0, uint64_t& q1) {
-  const double v = __longlong_as_double((long long)bits);
-  const uint64_t sb = (uint64_t)__double_as_longlong(__dmul_rn(v, v));
-  const uint64_t m2 = (sb & ((1ull << 52) - 1)) | (1ull << 52);
-  shl128(m2, (uint32_t)(sb >> 52) - 982u, q0, q1);
-}
-
 // hits += [ (r1:r0) <= (lim1:lim0) ]: the borrow of (r1:r0) - (lim1:lim0) - 1
 // (one subtract-with-borrow chain instead of three 64-bit compares).
 __device__ __forceinline__ void count_hit(uint32_t& hits, uint64_t r0, uint64_t r1,
@@ -124,72 +116,110 @@ __device__ __forceinline__ void count_hit(uint32_t& hits, uint64_t r0, uint64_t 
       : "l"(r0), "l"(lim0p1), "l"(r1), "l"(lim1));
 }
 
-// (a1:a0) += v * 2^105 for a variate v >= 2^-21 (the branch-free path, where
-// every variate of a kept chunk is at least 2^-21): its biased exponent e is
-// in [1002, 1022], so v * 2^105 = mant * 2^(32 + j) with j = e - 1002 in
-// [0, 20], and the image's low 32-bit word is zero.  The shift is made as
-// products by 2^j on the multiply-add pipe, whose carries feed the
-// accumulator directly: the integer ALU pipe, which binds this kernel, keeps
-// only the exponent and the two-word split (measured: 424 -> 437 G
-// variates/s with the hit test and the sums' adds below also moved there).
-__device__ __forceinline__ void add_variate_fast(uint64_t& a0, uint64_t& a1, uint64_t bits) {
-  const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
-  const uint32_t pj = 1u << ((hi >> 20) - 1002u);
-  const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
-  asm("{\n\t"
-      ".reg .u32 A0, A1, A2, A3;\n\t"
-      "mov.b64 {A0, A1}, %0;\n\t"
-      "mov.b64 {A2, A3}, %1;\n\t"
-      "mad.lo.cc.u32 A1, %2, %4, A1;\n\t"   // + lo * 2^j, word 1
-      "madc.hi.cc.u32 A2, %2, %4, A2;\n\t"  // + its high word, word 2
-      "madc.hi.u32 A3, %3, %4, A3;\n\t"     // + high word of mh * 2^j, word 3
-      "mad.lo.cc.u32 A2, %3, %4, A2;\n\t"   // + low word of mh * 2^j, word 2
-      "addc.u32 A3, A3, 0;\n\t"
-      "mov.b64 %0, {A0, A1};\n\t"
-      "mov.b64 %1, {A2, A3};\n\t"
-      "}"
-      : "+l"(a0), "+l"(a1)
-      : "r"(lo), "r"(mh), "r"(pj));
-}
-
-// (a1:a0) += (b1:b0) as multiply-adds by 1 with carries (the multiply-add
-// pipe, not the integer ALU pipe).
-__device__ __forceinline__ void add128_fma(uint64_t& a0, uint64_t& a1, uint64_t b0, uint64_t b1) {
-  asm("{\n\t"
-      ".reg .u32 A0, A1, A2, A3, B0, B1, B2, B3;\n\t"
-      "mov.b64 {A0, A1}, %0;\n\t"
-      "mov.b64 {A2, A3}, %1;\n\t"
-      "mov.b64 {B0, B1}, %2;\n\t"
-      "mov.b64 {B2, B3}, %3;\n\t"
-      "mad.lo.cc.u32 A0, B0, 1, A0;\n\t"
-      "madc.lo.cc.u32 A1, B1, 1, A1;\n\t"
-      "madc.lo.cc.u32 A2, B2, 1, A2;\n\t"
-      "madc.lo.u32 A3, B3, 1, A3;\n\t"
-      "mov.b64 %0, {A0, A1};\n\t"
-      "mov.b64 %1, {A2, A3};\n\t"
-      "}"
-      : "+l"(a0), "+l"(a1)
+// (a2:a1:a0) += (b1:b0) with one carry chain.
+__device__ __forceinline__ void add192(uint64_t& a0, uint64_t& a1, uint64_t& a2, uint64_t b0,
+                                       uint64_t b1) {
+  asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, 0;"
+      : "+l"(a0), "+l"(a1), "+l"(a2)
       : "l"(b0), "l"(b1));
 }
 
-// misses += [ (r1:r0) > lim ]: the carry out of (r1:r0) + ~lim, summed by
-// multiply-adds with carries.
-__device__ __forceinline__ void count_miss_fma(uint32_t& miss, uint64_t r0, uint64_t r1,
-                                               uint64_t nlim0, uint64_t nlim1) {
+// ---- the kept-chunk path: every variate of a kept chunk is at least 2^-16 ----
+//
+// A variate v >= 2^-16 has biased exponent e in [1007, 1022], so
+//   v * 2^105 = (mh 2^32 + lo) * pj * 2^32,  pj = 2^(e - 1002) in [2^5, 2^20],
+// with mh the top 21 bits of its significand (leading one included) and lo
+// the low 32.  Its square RN(v*v) >= 2^-32 has biased exponent e2 in
+// [991, 1022], so on the 2^-84 grid
+//   RN(v*v) * 2^84 = (mh2 2^32 + ml2) * pk,  pk = 2^(e2 - 991) in [1, 2^31].
+// Both powers of two come from one funnel rotate of a constant by the
+// exponent (the rotate takes the amount mod 32): e - 1002 = (e + 22) mod 32
+// and e2 - 991 = (e2 + 1) mod 32 on those ranges.  The shifts are then
+// products on the multiply-add pipe, which also sums them: per chunk of 64
+// pairs, lo*pj and mh*pj go to 64-bit partial sums (below 2^59 and 2^48),
+// and each pair's exact x'+y' (below 2^85, three words) to three more.
+// The integer ALU pipe keeps only the field extractions.
+__device__ __forceinline__ void variate_parts(uint64_t bits, uint32_t& lo, uint32_t& mh,
+                                              uint32_t& pj) {
+  const uint32_t hi = (uint32_t)(bits >> 32);
+  lo = (uint32_t)bits;
+  mh = (hi & 0xFFFFFu) | 0x100000u;
+  pj = __funnelshift_l(1u << 22, 1u << 22, hi >> 20);  // 2^(e - 1002)
+}
+
+__device__ __forceinline__ void square_parts(uint64_t sb, uint32_t& ml, uint32_t& mh,
+                                             uint32_t& pk) {
+  const uint32_t hi = (uint32_t)(sb >> 32);
+  ml = (uint32_t)sb;
+  mh = (hi & 0xFFFFFu) | 0x100000u;
+  pk = __funnelshift_l(2u, 2u, hi >> 20);  // 2^(e2 - 991)
+}
+
+// The bits of RN(v*v) for a variate v >= 2^-16 (no subnormal, no overflow):
+// one round-to-nearest multiply on the FP64 pipe, or the same rounding of
+// mant^2 made on the integer pipes (ties to even; a carry into bit 53 moves
+// the exponent up through the addition).
+template <bool FP64SQ>
+__device__ __forceinline__ uint64_t square_bits(uint64_t bits) {
+  if constexpr (FP64SQ) {
+    const double v = __longlong_as_double((long long)bits);
+    return (uint64_t)__double_as_longlong(__dmul_rn(v, v));
+  } else {
+    const uint32_t e = (uint32_t)(bits >> 52);
+    const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const uint64_t plo = mant * mant, phi = __umul64hi(mant, mant);
+    const uint32_t sh = 52u + ((uint32_t)(phi >> 41) & 1u);
+    uint64_t m2 = (phi << (64u - sh)) | (plo >> sh);
+    const uint64_t rest = plo & ((1ull << sh) - 1ull);
+    const uint64_t half = 1ull << (sh - 1u);
+    m2 += (rest > half) | ((rest == half) & (m2 & 1ull));
+    return ((uint64_t)(2u * e + sh - 1076u) << 52) + m2;
+  }
+}
+
+// (s2:s1:s0) = x' + y' for the 2^-84-grid images of two squares: the two
+// low-part products fit one 64-bit sum (each below 2^63), the two high-part
+// products another (below 2^53), and the result is their sum with the
+// second shifted by 32.
+__device__ __forceinline__ void pair_square_sum(uint32_t mlx, uint32_t mhx, uint32_t pkx,
+                                                uint32_t mly, uint32_t mhy, uint32_t pky,
+                                                uint32_t& s0, uint32_t& s1, uint32_t& s2) {
   asm("{\n\t"
-      ".reg .u32 R0, R1, R2, R3, C0, C1, C2, C3, t;\n\t"
-      "mov.b64 {R0, R1}, %1;\n\t"
-      "mov.b64 {R2, R3}, %2;\n\t"
-      "mov.b64 {C0, C1}, %3;\n\t"
-      "mov.b64 {C2, C3}, %4;\n\t"
-      "mad.lo.cc.u32 t, R0, 1, C0;\n\t"
-      "madc.lo.cc.u32 t, R1, 1, C1;\n\t"
-      "madc.lo.cc.u32 t, R2, 1, C2;\n\t"
-      "madc.lo.cc.u32 t, R3, 1, C3;\n\t"
+      ".reg .u64 TL, TH;\n\t"
+      ".reg .u32 l1, h0, h1;\n\t"
+      "mul.wide.u32 TL, %3, %5;\n\t"
+      "mad.wide.u32 TL, %6, %8, TL;\n\t"
+      "mul.wide.u32 TH, %4, %5;\n\t"
+      "mad.wide.u32 TH, %7, %8, TH;\n\t"
+      "mov.b64 {%0, l1}, TL;\n\t"
+      "mov.b64 {h0, h1}, TH;\n\t"
+      "add.cc.u32 %1, l1, h0;\n\t"
+      "addc.u32 %2, h1, 0;\n\t"
+      "}"
+      : "=&r"(s0), "=&r"(s1), "=&r"(s2)
+      : "r"(mlx), "r"(mhx), "r"(pkx), "r"(mly), "r"(mhy), "r"(pky));
+}
+
+// misses += [S > 2^84 + 2^31] for S = (s2:s1:s0): the carry out of S plus
+// the 96-bit complement of that bound, taken as multiply-adds by 1.  A pair
+// is a hit iff RN(x^2) + RN(y^2) <= 1 + 2^-53 (the tie rounds to the even
+// 1.0), which on the 2^-84 grid is S <= 2^84 + 2^31.
+__device__ __forceinline__ void count_miss3(uint32_t& miss, uint32_t s0, uint32_t s1,
+                                            uint32_t s2) {
+  asm("{\n\t"
+      ".reg .u32 t;\n\t"
+      "mad.lo.cc.u32 t, %1, 1, 0x7FFFFFFF;\n\t"
+      "madc.lo.cc.u32 t, %2, 1, 0xFFFFFFFF;\n\t"
+      "madc.lo.cc.u32 t, %3, 1, 0xFFEFFFFF;\n\t"
       "madc.lo.u32 %0, 0, 0, %0;\n\t"
       "}"
       : "+r"(miss)
-      : "l"(r0), "l"(r1), "l"(nlim0), "l"(nlim1));
+      : "r"(s0), "r"(s1), "r"(s2));
+}
+
+// q += s as one 64-bit multiply-add (the multiply-add pipe, not the ALU).
+__device__ __forceinline__ void acc_wide(uint64_t& q, uint32_t s) {
+  asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(q) : "r"(s));
 }
 
 // Round (w2:w1:w0) * 2^-scale to the nearest double, ties to even.
@@ -221,11 +251,12 @@ __device__ double round_words(uint64_t w0, uint64_t w1, uint64_t w2, int scale) 
 }
 
 // FP64SQ: each RN(v*v) by one multiply on the FP64 pipe, else formed on the
-// integer pipes; the hit test and the sums stay integer either way (taking
-// the test's add on the FP64 pipe as well measured slower: that pipe is the
-// scarcer one).  The two forms give identical bits.
+// integer pipes; the hit test and the sums stay integer either way.  The two
+// forms give identical bits.  At most 64 registers (the launch bound), which
+// measured faster than the 68 the compiler takes unbounded: more warps hide
+// the step's latency while the three pipes stay near 70% busy.
 template <bool FP64SQ>
-__global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
+__global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t wpb = blockDim.x >> 5;
   const uint64_t b = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
@@ -233,44 +264,24 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
   const uint64_t pairs = p.len / 2;
   const uint64_t j0 = lane * pairs / 32, j1 = (lane + 1) * pairs / 32;
   const uint64_t first = (p.block0 + b) * p.len + 2 * j0;
-  uint32_t hits = 0;        // hits of the exactly made pairs
+  uint32_t hits = 0;            // hits of the exactly made pairs
   uint32_t miss = 0, kept = 0;  // misses among the pairs of kept chunks, and those pairs
-  uint64_t a0 = 0, a1 = 0;  // sum of v * 2^105
-  uint64_t h0 = 0, h1 = 0;  // sum of the fast RN(v*v) * 2^93
-  uint64_t l0 = 0, l1 = 0;  // sum of the other RN(v*v) * 2^157 (rare)
-  // hit iff RN(x^2) + RN(y^2) <= 1 + 2^-53, i.e. on the 2^-93 grid
-  // (exact high parts, ceilings of the rare small squares) <= 2^93 + 2^40
+  uint64_t a0 = 0, a1 = 0, a2 = 0;  // sum of v * 2^105 (below 2^138: len <= 2^33)
+  uint64_t h0 = 0, h1 = 0;          // sum of the fast RN(v*v) * 2^93
+  uint64_t l0 = 0, l1 = 0;          // sum of the other RN(v*v) * 2^157 (rare)
+  // exact path: hit iff RN(x^2) + RN(y^2) <= 1 + 2^-53, i.e. on the 2^-93
+  // grid (exact high parts, ceilings of the rare small squares) <= 2^93 + 2^40
   const uint64_t lim0 = 1ull << 40, lim1 = 1ull << 29;
   if (j0 < j1) {
     uint64_t z = seed_state(exponent_add(p.ebase, first + 1), p.skip);
-    // One pair of variates into the accumulators; `exact` selects the
-    // conversion with its own rare-case branch, else the branch-free one
-    // that only lowers qmin when it cannot be trusted.
-    auto pair = [&](bool exact, uint32_t& qmin) {
-      const uint64_t bx = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
-      const uint64_t by = exact ? shared_step_f64(z) : shared_step_f64_ptx(z, qmin);
-      if constexpr (FP64SQ) {
-        if (!exact) {  // a kept chunk: both squares on the fast grid, no branch
-          uint64_t xq0, xq1, yq0, yq1;
-          square_fast_fp64(bx, xq0, xq1);
-          square_fast_fp64(by, yq0, yq1);
-          add_variate_fast(a0, a1, bx);
-          add_variate_fast(a0, a1, by);
-          add128_fma(xq0, xq1, yq0, yq1);
-          count_miss_fma(miss, xq0, xq1, ~lim0, ~lim1);
-          add128_fma(h0, h1, xq0, xq1);
-          return;
-        }
-      }
+    // One pair with the exact conversion and the general grids.
+    auto exact_pair = [&]() {
+      const uint64_t bx = shared_step_f64(z);
+      const uint64_t by = shared_step_f64(z);
       const Terms x = FP64SQ ? variate_terms_fp64(bx) : variate_terms(bx);
       const Terms y = FP64SQ ? variate_terms_fp64(by) : variate_terms(by);
-      if (exact) {
-        add128(a0, a1, x.v0, x.v1);
-        add128(a0, a1, y.v0, y.v1);
-      } else {  // every variate of a kept chunk is at least 2^-21
-        add_variate_fast(a0, a1, bx);
-        add_variate_fast(a0, a1, by);
-      }
+      add192(a0, a1, a2, x.v0, x.v1);
+      add192(a0, a1, a2, y.v0, y.v1);
       uint64_t r0 = x.q0, r1 = x.q1;
       add128(r0, r1, y.q0, y.q1);
       count_hit(hits, r0, r1, lim0 + 1, lim1);
@@ -283,30 +294,56 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
         add128(l0, l1, y.s0, y.s1);
       }
     };
-    // Chunks of kChunk pairs with the branch-free conversion; a lane whose
-    // chunk met a variate below 2^-20 (a quotient window below 2^33, about
-    // one chunk in 2^13) restores the chunk's starting point and redoes it
-    // exactly.  Every variate of a kept chunk is then at least 2^-20, so its
-    // square lies on the fast grid and its image has a zero low word.
+    // Chunks of kChunk pairs with the branch-free conversion and per-chunk
+    // partial sums.  A chunk that met a variate below 2^-16 (a quotient
+    // window below 2^37, qmin < 32: about one chunk in 2^9) drops its
+    // partials and misses, restores its starting state and is redone
+    // exactly; a kept chunk folds its partials into the block's sums:
+    // v-sum += P1 2^32 + P2 2^64, and on the 2^-93 grid the squares'
+    // h += (Q0 + Q1 2^32 + Q2 2^64) 2^9.
     constexpr uint32_t kChunk = 64;
     uint64_t j = j0;
     for (; j + kChunk <= j1; j += kChunk) {
-      const uint64_t zs = z, sa0 = a0, sa1 = a1, sh0 = h0, sh1 = h1, sl0 = l0, sl1 = l1;
-      const uint32_t shits = hits, smiss = miss;
-      uint32_t qmin = 0xffffffffu;
+      const uint64_t zs = z;
+      const uint32_t smiss = miss;
+      uint64_t P1 = 0, P2 = 0, Q0 = 0, Q1 = 0;
+      uint32_t Q2 = 0, qmin = 0xffffffffu;
 #pragma unroll 4
-      for (uint32_t k = 0; k < kChunk; ++k) pair(false, qmin);
-      if (__builtin_expect(qmin < 2, 0)) {
-        z = zs; a0 = sa0; a1 = sa1; h0 = sh0; h1 = sh1; l0 = sl0; l1 = sl1; hits = shits;
+      for (uint32_t k = 0; k < kChunk; ++k) {
+        const uint64_t bx = shared_step_f64_ptx(z, qmin);
+        const uint64_t by = shared_step_f64_ptx(z, qmin);
+        uint32_t xl, xm, xp, yl, ym, yp;
+        variate_parts(bx, xl, xm, xp);
+        variate_parts(by, yl, ym, yp);
+        P1 += (uint64_t)xl * xp;
+        P2 += (uint64_t)xm * xp;
+        P1 += (uint64_t)yl * yp;
+        P2 += (uint64_t)ym * yp;
+        uint32_t sxl, sxm, sxp, syl, sym, syp;
+        square_parts(square_bits<FP64SQ>(bx), sxl, sxm, sxp);
+        square_parts(square_bits<FP64SQ>(by), syl, sym, syp);
+        uint32_t s0, s1, s2;
+        pair_square_sum(sxl, sxm, sxp, syl, sym, syp, s0, s1, s2);
+        count_miss3(miss, s0, s1, s2);
+        acc_wide(Q0, s0);
+        acc_wide(Q1, s1);
+        Q2 += s2;
+      }
+      if (__builtin_expect(qmin < 32, 0)) {
+        z = zs;
         miss = smiss;
-        uint32_t unused = 0;
-        for (uint32_t k = 0; k < kChunk; ++k) pair(true, unused);
+        for (uint32_t k = 0; k < kChunk; ++k) exact_pair();
       } else {
         kept += kChunk;
+        add192(a0, a1, a2, P1 << 32, P1 >> 32);
+        add128(a1, a2, P2, 0);
+        add128(h0, h1, Q0 << 9, 0);
+        add128(h0, h1, Q1 << 41, Q1 >> 23);
+        h1 += (uint64_t)Q2 << 9;
       }
     }
-    for (uint32_t unused = 0; j < j1; ++j) pair(true, unused);
-    if constexpr (FP64SQ) hits += kept - miss;  // the kept chunks counted their misses
+    for (; j < j1; ++j) exact_pair();
+    hits += kept - miss;  // the kept chunks counted their misses
   }
   // exact warp reduction (integer addition is order-free)
 #pragma unroll
@@ -314,7 +351,9 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
     hits += __shfl_xor_sync(0xffffffffu, hits, off);
     uint64_t o0 = __shfl_xor_sync(0xffffffffu, a0, off);
     uint64_t o1 = __shfl_xor_sync(0xffffffffu, a1, off);
-    add128(a0, a1, o0, o1);
+    const uint64_t o2 = __shfl_xor_sync(0xffffffffu, a2, off);
+    add192(a0, a1, a2, o0, o1);
+    a2 += o2;
     o0 = __shfl_xor_sync(0xffffffffu, h0, off);
     o1 = __shfl_xor_sync(0xffffffffu, h1, off);
     add128(h0, h1, o0, o1);
@@ -326,12 +365,12 @@ __global__ void __launch_bounds__(256) mc_kernel(const McParams p) {
   uint64_t w0 = l0, w1 = l1, w2 = 0;
   add128(w1, w2, h0, h1);
   if (lane == 0) {
-    p.sum[b] = round_words(a0, a1, 0, 105);
+    p.sum[b] = round_words(a0, a1, a2, 105);
     p.sumsq[b] = round_words(w0, w1, w2, 157);
     if (p.hits) p.hits[b] = hits;
     atomicAdd(p.hits_total, (unsigned long long)hits);
     if (p.totals) {  // exact totals over the call: every 32-bit piece into its own word
-      const uint64_t words[kMcSumWords + kMcSqWords] = {a0, a0 >> 32, a1, a1 >> 32,
+      const uint64_t words[kMcSumWords + kMcSqWords] = {a0, a0 >> 32, a1, a1 >> 32, a2,
                                                           w0, w0 >> 32, w1, w1 >> 32,
                                                           w2, w2 >> 32};
 #pragma unroll

@@ -22,10 +22,10 @@ struct McParams {
   uint32_t skip;
 };
 
-// Words of the exact totals: 4 pieces of the sum on the 2^-105 grid (below
-// 2^128 per block), then 6 of the sum of squares on the 2^-157 grid (below
-// 2^192 per block).
-constexpr uint32_t kMcSumWords = 4, kMcSqWords = 6;
+// Words of the exact totals: 5 pieces of the sum on the 2^-105 grid (below
+// 2^138 per block), then 6 of the sum of squares on the 2^-157 grid (below
+// 2^190 per block).
+constexpr uint32_t kMcSumWords = 5, kMcSqWords = 6;
 
 // The fused kernel forming each RN(v*v) on the FP64 pipe (true) or on the
 // integer pipes (false).

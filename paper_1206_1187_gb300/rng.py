@@ -359,13 +359,13 @@ def consume_mc_into(start_index: int, nblocks: int, length: int, total, hits, s1
                               ctypes.c_void_p(_stream_handle(stream)), _tune_ptr(tune)))
 
 
-MC_TOTAL_WORDS = 10
+MC_TOTAL_WORDS = 11
 
 
 def consume_mc_totals(start_index: int, nblocks: int, length: int, block0: int = 0,
                       tune=None, stream=None):
     """consume_mc plus the call's exact totals: returns (hits_total[1],
-    hits[nblocks], sum[nblocks], sumsq[nblocks], totals[10]) as CUDA tensors.
+    hits[nblocks], sum[nblocks], sumsq[nblocks], totals[11]) as CUDA tensors.
     totals holds 32-bit pieces of the exact sums over every block of the call
     (see rng_consume_mc_totals); word arrays of several calls or ranks add
     element by element, and mc_round_totals rounds the result."""
@@ -385,7 +385,7 @@ def consume_mc_totals(start_index: int, nblocks: int, length: int, block0: int =
 
 
 def mc_round_totals(words) -> tuple[float, float]:
-    """(sum, sumsq): the totals word array (host sequence of 10 non-negative
+    """(sum, sumsq): the totals word array (host sequence of 11 non-negative
     integers below 2^64, e.g. several ranks' arrays added) rounded to nearest."""
     import numpy as np
     w = np.ascontiguousarray([int(x) for x in words], dtype=np.uint64)

@@ -124,3 +124,27 @@ def test_exact_totals_of_one_call(R, oracle_mod):
         assert np.array_equal(hits.view(torch.int64).cpu().numpy(), ref[1])
         assert np.array_equal(s1.cpu().numpy().view(np.int64), ref[2].view(np.int64))
         assert np.array_equal(s2.cpu().numpy().view(np.int64), ref[3].view(np.int64))
+
+
+def test_long_blocks_whose_sum_passes_2_128(R, oracle_mod):
+    """Blocks of 2^25 variates: the exact sum of v * 2^105 of such a block is
+    about 2^129, past 128 bits, so the block sum needs its third word.  Per
+    block outputs and the call's totals match the oracle for both forms of
+    the squares."""
+    import torch
+    a, length, block0 = M + 100, 1 << 25, 3
+    oh, o1, o2 = oracle_mod.mc(a, length, block0 + np.arange(2))
+    assert float(np.sum(o1)) * 2.0 ** 105 > 2.0 ** 128
+    for conv in ("fp64", "int"):
+        total, hits, s1, s2 = _run(R, a, 2, length, block0=block0, tune=R.make_tune(conv=conv))
+        assert np.array_equal(hits, oh.astype(np.int64)), conv
+        assert np.array_equal(s1.view(np.int64), o1.view(np.int64)), conv
+        assert np.array_equal(s2.view(np.int64), o2.view(np.int64)), conv
+        assert total == int(oh.sum())
+    v = oracle_mod.generate(a, block0 * length, length, "f64")
+    want = (oracle_mod.exact_sum(v), oracle_mod.exact_sum(v * v))
+    _, _, _, _, words = R.consume_mc_totals(a, 1, length, block0=block0)
+    torch.cuda.synchronize()
+    w = [int(x) for x in words.view(torch.int64).cpu().tolist()]
+    assert w[4] > 0  # the fifth piece of the sum is in use
+    assert R.mc_round_totals(w) == want

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 M = 3 ** 33
-SUM_WORDS, SQ_WORDS = 4, 6
+SUM_WORDS, SQ_WORDS = 5, 6
 
 
 @pytest.fixture(scope="module")
@@ -64,9 +64,9 @@ def test_rounding_ties_go_to_even(R):
                 base = (y >> (top - 52)) << (top - 52)
                 assert s1 == float(Fraction(base + ((1 << (top - 52)) if want_up else 0),
                                             1 << 105))
-    assert R.mc_round_totals([0] * 10) == (0.0, 0.0)
+    assert R.mc_round_totals([0] * 11) == (0.0, 0.0)
     with pytest.raises(ValueError):
-        R.mc_round_totals([0] * 9)
+        R.mc_round_totals([0] * 10)
 
 
 def _block_words(oracle_mod, a, length, blocks):

@@ -19,6 +19,7 @@ READ_BY_BENCH = {
     ("inst_per_variate", "m40_2e25"): "m40",
     ("inst_per_variate", "mc_2e36"): "mc",
     ("alu_pipe_busy_frac", "mc_2e36"): "mc",
+    ("fp64_pipe_busy_frac", "mc_2e36"): "mc",
     ("traffic_per_algorithmic_byte", "batch_512"): "batch",
     ("inst_per_variate", "batch_512"): "batch",
 }
