@@ -464,64 +464,65 @@ static_assert((136u << 21) == 0x11000000u, "exponent constant of the FP32 PTX st
 // B - 1.38 * 2^-53; nor can it go below Q 2^-53, a double.  So every value it
 // can take truncates to W.
 //
-// Q = (u1:u0) on 32-bit words.  With c = leading zeros of u1 and s = c - 8,
-// the high word of (u1:u0) << s is W with its leading one at bit 23, and the
-// float's bits are W + (128 - s) 2^23 (biased exponent 137 - c, the leading
-// one adding its 1).  The bits of Q below W are the low 32 - s bits of u0, so
-// v = ~(u0 | 1) << s is zero exactly when they are all ones but perhaps the
-// last.  u1 = 0 (variate below 2^-21) makes bfind.shiftamt return 2^32 - 1,
-// s >= 32 and v = 0 as well.  `qmin` keeps the running minimum of v: it is 0
-// exactly when some step of the run needs the exact path, and the caller
-// redoes the run.  The product Q m is formed with 32-bit carry chains, which
-// measured fewer instructions than 64-bit multiply-adds with zero-extended
-// addends.
+// The step is computed on X = Q 2^11, which is what a multiplier of
+// m' 2^11 mod 2^64 gives directly: X = (y + 1)(m' 2^11) mod 2^64 (a 64-bit
+// product needs no mask), and y_(k-1) = floor(Q m / 2^53) = floor(X m / 2^64)
+// is the high word of X m with no final shift.  X = (u1:u0) on 32-bit words,
+// Q's leading one at bit 63 - c with c = leading zeros of u1.  The high word
+// of (u1:u0) << c, shifted right by 8, is W with its leading one at bit 23,
+// and the float's bits are W + (125 - c) 2^23 (biased exponent 126 - c, the
+// leading one adding its 1).  The flag is v = ~(u0 | 0xFFF) << c, zero when
+// Q's bits 1 .. 20 - c are all ones: a superset of the cases above, since
+// Q's bits below W are bits 0 .. 28 - c (it also flags a one-in-2^(20-c)
+// share of the other steps, about one step in 2^16 overall).  Q below 2^33
+// (variate below 2^-20) gives c >= 20 and v = 0, and u1 = 0 makes
+// bfind.shiftamt return 2^32 - 1 and v = 0 as well.  `qmin` keeps the
+// running minimum of v: it is 0 when some step of the run needs the exact
+// path, and the caller redoes the run.  The product X m is formed with
+// 32-bit carry chains (measured fewer instructions than 64-bit multiply-adds
+// with zero-extended addends), and the whole step takes 24.1 instructions per
+// variate in the tiled kernel against 28.2 for the same step on Q itself.
 constexpr uint64_t kMp = kNegMinv53;  // m' = -m^-1 mod 2^53
-constexpr uint32_t kMp0 = (uint32_t)kMp, kMp1 = (uint32_t)(kMp >> 32);
-static_assert(kMp1 < (1u << 21), "m' < 2^53");
+static_assert((kMp >> 53) == 0, "m' < 2^53");
 static_assert((kM >> 32) < (1u << 21), "m < 2^53");
+constexpr uint64_t kMpX = kMp << 11;  // m' 2^11 mod 2^64
+constexpr uint32_t kMpX0 = (uint32_t)kMpX, kMpX1 = (uint32_t)(kMpX >> 32);
 __device__ __forceinline__ uint32_t back_step_f32_ptx(uint64_t& y, uint32_t& qmin) {
   const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
   uint32_t r0, r1, b, qo;
-  // inputs are copied first and outputs written last, so that no output
-  // register can overlap an input still to be read
+  // outputs are early-clobber: none shares a register with an input
   asm("{\n\t"
-      ".reg .u32 a0, a1, qi, u0, u1, th, h0, v1, v2, v3, x, w, c, s, mant, e, nv;\n\t"
+      ".reg .u32 u0, u1, th, h0, w1, x, w, c, mant, e, nv;\n\t"
       ".reg .u64 t;\n\t"
-      "mov.u32 a0, %4;\n\t"
-      "mov.u32 a1, %5;\n\t"
-      "mov.u32 qi, %11;\n\t"
-      "mad.wide.u32 t, a0, %6, %8;\n\t"        // y0 m'0 + m'
+      "mad.wide.u32 t, %4, %6, %8;\n\t"         // X = (y + 1) m' 2^11 mod 2^64
       "mov.b64 {u0, th}, t;\n\t"
-      "mad.lo.u32 th, a0, %7, th;\n\t"         // + (y0 m'1 + y1 m'0) 2^32
-      "mad.lo.u32 th, a1, %6, th;\n\t"
-      "and.b32 u1, th, 0x1FFFFF;\n\t"          // Q = (u1:u0) = z m' mod 2^53
-      "mul.hi.u32 h0, u0, %9;\n\t"             // Q m from bit 32 up: v1, v2, v3
-      "mad.lo.cc.u32 v1, u0, %10, h0;\n\t"
+      "mad.lo.u32 th, %4, %7, th;\n\t"
+      "mad.lo.u32 u1, %5, %6, th;\n\t"
+      "mul.hi.u32 h0, u0, %9;\n\t"              // high word of X m:
+      "mad.lo.cc.u32 w1, u0, %10, h0;\n\t"      // y_(k-1) = floor(X m / 2^64)
       "madc.hi.u32 x, u0, %10, 0;\n\t"
-      "mad.lo.cc.u32 v1, u1, %9, v1;\n\t"
+      "mad.lo.cc.u32 w1, u1, %9, w1;\n\t"
       "madc.hi.cc.u32 x, u1, %9, x;\n\t"
       "addc.u32 w, 0, 0;\n\t"
-      "mad.lo.cc.u32 v2, u1, %10, x;\n\t"
-      "madc.hi.u32 v3, u1, %10, w;\n\t"
-      "bfind.shiftamt.u32 c, u1;\n\t"          // leading zeros of u1; 2^32-1 if u1 = 0
-      "add.u32 s, c, -8;\n\t"
-      "shf.l.clamp.b32 mant, u0, u1, s;\n\t"   // W, leading one at bit 23
-      "mad.lo.u32 e, s, 0xFF800000, 0x40000000;\n\t"  // (128 - s) << 23
-      "or.b32 nv, u0, 1;\n\t"
+      "mad.lo.cc.u32 %0, u1, %10, x;\n\t"
+      "madc.hi.u32 %1, u1, %10, w;\n\t"
+      "bfind.shiftamt.u32 c, u1;\n\t"           // leading zeros of u1; 2^32-1 if u1 = 0
+      "shf.l.clamp.b32 mant, u0, u1, c;\n\t"
+      "shr.b32 mant, mant, 8;\n\t"              // W, leading one at bit 23
+      "mad.lo.u32 e, c, 0xFF800000, 0x3E800000;\n\t"  // (125 - c) << 23
+      "or.b32 nv, u0, 0xFFF;\n\t"
       "not.b32 nv, nv;\n\t"
-      "shl.b32 nv, nv, s;\n\t"                 // 0: the exact path is needed
-      "shf.r.clamp.b32 %0, v1, v2, 21;\n\t"   // y_(k-1) = floor(Q m / 2^53)
-      "shf.r.clamp.b32 %1, v2, v3, 21;\n\t"
+      "shl.b32 nv, nv, c;\n\t"                  // 0: the exact path is needed
       "add.u32 %2, mant, e;\n\t"
-      "min.u32 %3, qi, nv;\n\t"
+      "min.u32 %3, %11, nv;\n\t"
       "}"
-      : "=r"(r0), "=r"(r1), "=r"(b), "=r"(qo)
-      : "r"(y0), "r"(y1), "n"(kMp0), "n"(kMp1), "l"(kMp), "n"(kM0), "n"(kM1), "r"(qmin));
+      : "=&r"(r0), "=&r"(r1), "=&r"(b), "=&r"(qo)
+      : "r"(y0), "r"(y1), "n"(kMpX0), "n"(kMpX1), "l"(kMpX), "n"(kM0), "n"(kM1), "r"(qmin));
   y = ((uint64_t)r1 << 32) | r0;
   qmin = qo;
   return b;
 }
-static_assert((128u << 23) == 0x40000000u && (0u - (1u << 23)) == 0xFF800000u,
+static_assert((125u << 23) == 0x3E800000u && (0u - (1u << 23)) == 0xFF800000u,
               "exponent field of the backward FP32 step");
 
 // The state advance of shared_step_f64 alone (raw-state output).

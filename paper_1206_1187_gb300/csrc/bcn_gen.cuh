@@ -304,12 +304,11 @@ __device__ __forceinline__ void shared_run_fast2(typename Word<DT>::type* mine, 
 // FP32 output by the backward step with its exact quotient (two chains on
 // y = z - 1): chain b starts one past the run and emits elements c-1 .. h+1,
 // chain a starts at element h+1 and emits h .. 0, so afterwards chain a holds
-// element 0 and chain b element h+1.  Every K-th iteration of chain b takes
-// its conversion on the otherwise idle FP64 pipe (int->double and one
-// round-to-nearest multiply, then truncation to float), the step's own
-// conversion being dropped by the compiler.  A lane whose run needs the exact
-// path (see back_step_f32_ptx) redoes it forward from element 0.
-constexpr uint32_t kBackFp64Every = 6;
+// element 0 and chain b element h+1.  Every conversion stays on the integer
+// pipes (taking one in six or twelve on the FP64 pipe, as the forward FP64
+// kernel does, measured 1% slower or no faster with this step).  A lane
+// whose run needs the exact path (see back_step_f32_ptx) redoes it forward
+// from element 0.
 template <int CDEPTH>
 __device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_t& ya,
                                              uint64_t& yb) {
@@ -318,13 +317,7 @@ __device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_
   const uint32_t last = CDEPTH > 0 ? (uint32_t)CDEPTH - 1 : c - 1;
 #pragma unroll
   for (uint32_t i = 0; i < h; ++i) {
-    if (CDEPTH > 0 && i % kBackFp64Every == kBackFp64Every / 2) {
-      uint32_t unused = 0;
-      back_step_f32_ptx(yb, unused);
-      mine[last - i] = f32_bits_from_f64_bits(f64_bits_fp64(yb + 1));
-    } else {
-      mine[last - i] = back_step_f32_ptx(yb, qmin);
-    }
+    mine[last - i] = back_step_f32_ptx(yb, qmin);
     mine[h - i] = back_step_f32_ptx(ya, qmin);
   }
   mine[0] = back_step_f32_ptx(ya, qmin);
