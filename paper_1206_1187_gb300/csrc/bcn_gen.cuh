@@ -240,62 +240,49 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
 // stride c (odd), so they stay bank-conflict free.  Between tiles chain a
 // jumps by 32c-h-1 steps and chain b by 31c+h+1.  Forward steps only.
 
-// Every second iteration of the two-chain loop (compile-time depths) takes
+// The FP64 output chains of the two-chain loop hold Z = z 2^10 (see
+// shared_step_f64_ptx).  Every fourth iteration (compile-time depths) takes
 // one conversion on the FP64 pipe, alternating between chain a (iterations
-// 0, 4, 8, ...) and chain b (2, 6, 10, ...): int->double and one
+// 0, 8, 16, ...) and chain b (4, 12, ...): int->double and one
 // round-to-nearest multiply, the definition itself, instead of the integer
-// rounding.  The FP64 pipe is otherwise idle here; a quarter of the
-// conversions spread evenly this way measured 3% faster than none for FP64
-// output (a sixth, or uneven spacings such as every third step of each chain:
-// 1-2%).  FP32 output, whose integer conversion is cheaper, does best with
-// one conversion in six (every third iteration).  Same bits either way.
-template <int DT>
-constexpr uint32_t kFp64ConvEvery = DT == DT_F32 ? 6 : 4;
-__device__ __forceinline__ uint64_t fp64_conv_step(uint64_t& z) {
-  const uint64_t bits = f64_bits_fp64(z);
-  z = shared_advance(z);
+// rounding.  The FP64 pipe is otherwise idle here; with the scaled step an
+// eighth of the conversions measured as fast as a sixth and faster than a
+// quarter (787, 787, 785 G variates/s) or a third (771).  Same bits either way.
+constexpr uint32_t kFp64ConvEvery = 8;
+__device__ __forceinline__ uint64_t fp64_conv_step_scaled(uint64_t& Z) {
+  const uint64_t bits = f64_bits_fp64_scaled(Z);
+  Z = shared_advance_scaled(Z);
   return bits;
 }
 
-// One fast step's output word: FP64 bits, or the FP32 bits made directly by
-// the FP32 form of the step; `fp64` takes the conversion on the FP64 pipe.
-template <int DT>
-__device__ __forceinline__ typename Word<DT>::type fast_word(uint64_t& z, uint32_t& qmin,
-                                                             bool fp64) {
-  if (fp64) {
-    const uint64_t bits = fp64_conv_step(z);
-    if constexpr (DT == DT_F64) return bits;
-    else return f32_bits_from_f64_bits(bits);
-  }
-  if constexpr (DT == DT_F64) return shared_step_f64_ptx(z, qmin);
-  else return shared_step_f32_ptx(z, qmin);
+// One fast step's FP64 bits from a scaled chain; `fp64` takes the conversion
+// on the FP64 pipe.
+__device__ __forceinline__ uint64_t fast_word(uint64_t& Z, uint32_t& qmin, bool fp64) {
+  if (fp64) return fp64_conv_step_scaled(Z);
+  return shared_step_f64_ptx(Z, qmin);
 }
 
-// The two interleaved chains of the branch-free shared-quotient step over one
-// run; a lane that left the fast path redoes its run with one exact chain.
-template <int DT, int CDEPTH>
-__device__ __forceinline__ void shared_run_fast2(typename Word<DT>::type* mine, uint32_t c,
-                                                 uint64_t& za, uint64_t& zb) {
-  typedef typename Word<DT>::type W;
+// The two interleaved scaled chains of the branch-free shared-quotient step
+// over one run of FP64 output; a lane that left the fast path redoes its run
+// with one exact chain on z.
+template <int CDEPTH>
+__device__ __forceinline__ void shared_run_fast2(uint64_t* mine, uint32_t c, uint64_t& za,
+                                                 uint64_t& zb) {
   const uint64_t a_start = za;
   uint32_t qmin = 0xffffffffu;
   const uint32_t h = CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : c / 2;
 #pragma unroll
   for (uint32_t i = 0; i < h; ++i) {
-    constexpr uint32_t K = kFp64ConvEvery<DT>;
-    mine[i] = fast_word<DT>(za, qmin, CDEPTH > 0 && i % K == 0);
-    mine[h + 1 + i] = fast_word<DT>(zb, qmin, CDEPTH > 0 && i % K == K / 2);
+    constexpr uint32_t K = kFp64ConvEvery;
+    mine[i] = fast_word(za, qmin, CDEPTH > 0 && i % K == 0);
+    mine[h + 1 + i] = fast_word(zb, qmin, CDEPTH > 0 && i % K == K / 2);
   }
-  mine[h] = fast_word<DT>(za, qmin, false);
+  mine[h] = fast_word(za, qmin, false);
   const bool rare = qmin == 0;
   if (__any_sync(0xffffffffu, rare)) {
     if (rare) {
-      uint64_t y = a_start;
-      for (uint32_t i = 0; i < c; ++i) {
-        const uint64_t bits = shared_step_f64(y);
-        if constexpr (DT == DT_F64) mine[i] = (W)bits;
-        else mine[i] = (W)f32_bits_from_f64_bits(bits);
-      }
+      uint64_t y = a_start >> kZShift;
+      for (uint32_t i = 0; i < c; ++i) mine[i] = shared_step_f64(y);
     }
     __syncwarp();
   }
@@ -333,6 +320,9 @@ __device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_
 // Whether a two-chain tile loop of this kind runs the backward FP32 step.
 template <int DT, int STEP, int CONV>
 constexpr bool kBackF32 = DT == DT_F32 && STEP == ST_SHARED && CONV == CV_INT;
+// Whether it runs the forward FP64 step on chains scaled by 2^10.
+template <int DT, int STEP, int CONV>
+constexpr bool kScaledF64 = DT == DT_F64 && STEP == ST_SHARED && CONV == CV_INT;
 
 template <int DT, int STEP, int CONV, int CDEPTH = 0>
 __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict__ out,
@@ -353,8 +343,8 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
     W* const mine = buf + lane * c;
     if constexpr (kBackF32<DT, STEP, CONV>) {
       back_run_f32<CDEPTH>(reinterpret_cast<uint32_t*>(mine), c, a.z, b.z);
-    } else if constexpr (STEP == ST_SHARED && CONV == CV_INT && DT != DT_U64) {
-      shared_run_fast2<DT, CDEPTH>(mine, c, a.z, b.z);
+    } else if constexpr (kScaledF64<DT, STEP, CONV>) {
+      shared_run_fast2<CDEPTH>(reinterpret_cast<uint64_t*>(mine), c, a.z, b.z);
     } else {
 #pragma unroll 4
       for (uint32_t i = 0; i < h; ++i) {
@@ -374,6 +364,9 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
       if constexpr (kBackF32<DT, STEP, CONV>) {  // the chains hold z - 1
         a.z = mulmod_pre(a.z + 1, jump_a, jump_aq) - 1;
         b.z = mulmod_pre(b.z + 1, jump_b, jump_bq) - 1;
+      } else if constexpr (kScaledF64<DT, STEP, CONV>) {  // the chains hold z 2^10
+        a.z = mulmod_pre(a.z >> kZShift, jump_a, jump_aq) << kZShift;
+        b.z = mulmod_pre(b.z >> kZShift, jump_b, jump_bq) << kZShift;
       } else {
         a.z = mulmod_pre(a.z, jump_a, jump_aq);
         b.z = mulmod_pre(b.z, jump_b, jump_bq);
@@ -383,8 +376,9 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
 }
 
 // Initial states of the two chains of a lane whose first run starts at
-// element `first`: forward chains at elements first and first + h + 1; the
-// backward FP32 chains one past elements h and c - 1, as z - 1.
+// element `first`: forward chains at elements first and first + h + 1 (the
+// FP64 output chains as z 2^10); the backward FP32 chains one past elements
+// h and c - 1, as z - 1.
 template <int DT, int STEP, int CONV>
 __device__ __forceinline__ void lane_chains2(uint64_t ebase, uint64_t first, uint32_t c,
                                              uint32_t skip, Gen<DT, STEP, CONV>& a,
@@ -393,6 +387,9 @@ __device__ __forceinline__ void lane_chains2(uint64_t ebase, uint64_t first, uin
   if constexpr (kBackF32<DT, STEP, CONV>) {
     a.z = state_of(ebase, first + h + 1, skip) - 1;
     b.z = state_of(ebase, first + c, skip) - 1;
+  } else if constexpr (kScaledF64<DT, STEP, CONV>) {
+    a.z = state_of(ebase, first, skip) << kZShift;
+    b.z = state_of(ebase, first + h + 1, skip) << kZShift;
   } else {
     a.z = state_of(ebase, first, skip);
     b.z = state_of(ebase, first + h + 1, skip);

@@ -273,7 +273,10 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
   // grid (exact high parts, ceilings of the rare small squares) <= 2^93 + 2^40
   const uint64_t lim0 = 1ull << 40, lim1 = 1ull << 29;
   if (j0 < j1) {
+    // the kept chunks step a chain scaled by 2^10 (see shared_step_f64_ptx),
+    // the exact pairs the plain state
     uint64_t z = seed_state(exponent_add(p.ebase, first + 1), p.skip);
+    uint64_t Z = z << kZShift;
     // One pair with the exact conversion and the general grids.
     auto exact_pair = [&]() {
       const uint64_t bx = shared_step_f64(z);
@@ -304,14 +307,14 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
     constexpr uint32_t kChunk = 64;
     uint64_t j = j0;
     for (; j + kChunk <= j1; j += kChunk) {
-      const uint64_t zs = z;
+      const uint64_t zs = Z;
       const uint32_t smiss = miss;
       uint64_t P1 = 0, P2 = 0, Q0 = 0, Q1 = 0;
       uint32_t Q2 = 0, qmin = 0xffffffffu;
 #pragma unroll 4
       for (uint32_t k = 0; k < kChunk; ++k) {
-        const uint64_t bx = shared_step_f64_ptx(z, qmin);
-        const uint64_t by = shared_step_f64_ptx(z, qmin);
+        const uint64_t bx = shared_step_f64_ptx(Z, qmin);
+        const uint64_t by = shared_step_f64_ptx(Z, qmin);
         uint32_t xl, xm, xp, yl, ym, yp;
         variate_parts(bx, xl, xm, xp);
         variate_parts(by, yl, ym, yp);
@@ -330,9 +333,10 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
         Q2 += s2;
       }
       if (__builtin_expect(qmin < 32, 0)) {
-        z = zs;
+        z = zs >> kZShift;
         miss = smiss;
         for (uint32_t k = 0; k < kChunk; ++k) exact_pair();
+        Z = z << kZShift;
       } else {
         kept += kChunk;
         add192(a0, a1, a2, P1 << 32, P1 >> 32);
@@ -342,6 +346,7 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
         h1 += (uint64_t)Q2 << 9;
       }
     }
+    z = Z >> kZShift;
     for (; j < j1; ++j) exact_pair();
     hits += kept - miss;  // the kept chunks counted their misses
   }

@@ -159,6 +159,59 @@ def test_shared_step_model_matches_definitions():
     assert slow > 0  # the rare path is exercised by the edge states
 
 
+KB, MS = K << 1, M << 10  # the scaled chain's constants: Z = z 2^10
+
+
+def shared_step_scaled_model(zz):
+    """Word-level model of the PTX step on a chain holding Z = z 2^10:
+    returns (next Z, FP64 bits or None for the rare path, q's top word)."""
+    z0, z1 = zz & MASK32, zz >> 32
+    kb0, kb1, ms0, ms1 = KB & MASK32, KB >> 32, MS & MASK32, MS >> 32
+    h0 = (z0 * kb0) >> 32
+    t = z0 * kb1 + h0
+    w1, x = t & MASK32, t >> 32
+    t = z1 * kb0 + w1
+    w1, x = t & MASK32, x + (t >> 32)
+    t = z1 * kb1 + x
+    q0, q1 = t & MASK32, t >> 32
+    assert q1 < 2 ** 32
+    qm = (q0 * ms0 + (((q0 * ms1 + q1 * ms0) & MASK32) << 32)) % 2 ** 64
+    r = ((((z0 << 21) & MASK32) << 32) - qm) % 2 ** 64
+    if r >= 2 ** 63:
+        r = (r + MS) % 2 ** 64
+    if q1 == 0:
+        return r, None, q1
+    c = clz32(q1)
+    s = c - 10
+    g_hi, g_lo = funnel_l(q0, q1, s), funnel_l(w1, q0, s)
+    xx = ((g_hi << 32) | g_lo) + (((1032 - c) << 53) | 1)
+    return r, xx >> 1, q1
+
+
+def test_scaled_step_model_matches_the_unscaled_step():
+    """On Z = z 2^10 with 2K and m 2^10: the same quotient window, the next
+    state scaled, the same FP64 bits, and the remainder's sign from its top
+    bit (|2^53 z - q m| 2^10 < 2^63)."""
+    assert KB < 2 ** 55 and 2 ** 62 <= MS < 2 ** 63
+    edge = [1, 2, 3, M - 1, M - 2, ((2 ** 32) * M) >> 53, (((2 ** 32) * M) >> 53) + 1]
+    slow = 0
+    for z in states(60000, seed=22) + edge:
+        zz = z << 10
+        assert ((zz * KB) >> 64) == (z * K) >> 53
+        r, bits, q1 = shared_step_scaled_model(zz)
+        assert r == ((z << 53) % M) << 10, z
+        assert (r, bits) == ((shared_step_model(z)[0]) << 10, shared_step_model(z)[1]), z
+        if bits is None:
+            slow += 1
+            continue
+        assert bits == rn_bits(z), z
+    assert slow > 0
+    # the FP64-pipe conversion from Z: exact int->double, then r3i 2^-10
+    for z in states(5000, seed=24) + edge:
+        assert float(z << 10) == float(z) * 1024.0
+        assert f64_bits(float(z << 10) * (R3I * 2.0 ** -10)) == rn_bits(z), z
+
+
 def general_conversion_model(p):
     """The general integer rounding of p * 2^-106 (any leading-zero count)."""
     q = p >> 53
@@ -304,29 +357,6 @@ def test_precomputed_quotient_mulmod():
             assert r == (z * j) % M
 
 
-def f32_step_model(z):
-    """The FP32-output step: the FP64 path's rounding add with the FP32
-    exponent (136 - c) pre-shifted into the high word, then >> 30."""
-    z0, z1 = z & MASK32, z >> 32
-    t0 = z0 * K0
-    t1 = z0 * K1 + (t0 >> 32)
-    t1 = z1 * K0 + t1
-    t2 = z1 * K1 + (t1 >> 32)
-    w1, w2, w3 = t1 & MASK32, t2 & MASK32, t2 >> 32
-    q0, q1 = funnel_r(w1, w2, 21), funnel_r(w2, w3, 21)
-    if q1 == 0:
-        return None
-    c = clz32(q1)
-    s = c - 10
-    lh = (w1 << 11) & MASK32
-    g_hi, g_lo = funnel_l(q0, q1, s), funnel_l(lh, q0, s)
-    ew = (0x11000000 - c * 0x200000) & MASK32
-    x0 = g_lo + 1
-    x1 = (g_hi + ew + (x0 >> 32)) & MASK32
-    x0 &= MASK32
-    return (((x1 << 32) | x0) >> 30) & MASK32
-
-
 def rz_f32_bits(z: int) -> int:
     """Bits of the FP32 variate: RN(z * r3i) as a double, then toward zero."""
     import numpy as np
@@ -337,58 +367,58 @@ def rz_f32_bits(z: int) -> int:
     return int(np.array([f], dtype=np.float32).view(np.uint32)[0])
 
 
-def test_f32_step_model_is_the_truncated_double():
-    n_fast = 0
-    for z in states(60000, seed=12):
-        bits = f32_step_model(z)
-        if bits is None:
-            continue
-        n_fast += 1
-        b64 = rn_bits(z)
-        assert bits == ((b64 >> 29) - (896 << 23)) & MASK32, z  # the FP64 path's truncation
-        assert bits == rz_f32_bits(z), z
-    assert n_fast > 50000
-    # states whose double lands on a float value (low 29 significand bits zero),
-    # among them those rounded up across the float boundary: the rounding
-    # carry must reach the float bits.  For random floats f, the states next to
-    # f / r3i give products within a few ulps of f.
-    rnd = random.Random(13)
-    hits = 0
-    for _ in range(20000):
-        f = struct.unpack("<f", struct.pack("<f", rnd.uniform(2.0 ** -20, 1.0)))[0]
-        zc = int(f / R3I)
-        for z in range(zc - 3, zc + 4):
-            if not 0 < z < M:
-                continue
-            b64 = f64_bits(float(z) * R3I)  # one round-to-nearest multiply
-            if (b64 & (2 ** 29 - 1)) == 0:
-                bits = f32_step_model(z)
-                if bits is not None:
-                    hits += 1
-                    assert bits == ((b64 >> 29) - (896 << 23)) & MASK32, z
-    assert hits > 1000
+def rotl32(x, n):
+    n &= 31
+    return ((x << n) | (x >> (32 - n))) & MASK32 if n else x
 
 
-def test_fused_fast_variate_image():
-    """The fused kernel's fast accumulation of v * 2^105 for v >= 2^-21: the
-    three upper 32-bit words of mant << (32 + j), j = e - 1002, from three
-    shifts (funnel shifts clamp a zero shift to the high operand)."""
+def test_fused_kept_chunk_parts():
+    """The fused kernel's kept-chunk arithmetic for variates v >= 2^-16:
+    v * 2^105 = (mh 2^32 + lo) pj 2^32 with pj = rotl(2^22, e) = 2^(e-1002),
+    RN(v*v) * 2^84 = (mh2 2^32 + ml2) pk with pk = rotl(2, e2) = 2^(e2-991),
+    both powers of two below 2^32, and the pair's hit rule on the 2^-84 grid
+    (S <= 2^84 + 2^31 iff RN(RN(x^2) + RN(y^2)) <= 1) with S below 2^85."""
+    import math
     rnd = random.Random(14)
     vals = [float(Fraction(z) * Fraction(R3I)) for z in states(20000, seed=15)]
-    vals += [2.0 ** -21, math.nextafter(1.0, 0.0), 0.5, math.nextafter(0.5, 0.0)]
-    for v in vals:
-        if v < 2.0 ** -21:
-            continue
+    vals += [2.0 ** -16, math.nextafter(1.0, 0.0), 0.5, math.nextafter(0.5, 0.0),
+             math.nextafter(2.0 ** -16, 1.0)]
+    vals = [v for v in vals if v >= 2.0 ** -16]
+
+    def parts(v):
         b = f64_bits(v)
         hi, lo = b >> 32, b & MASK32
-        j = (hi >> 20) - 1002
-        assert 0 <= j <= 20
         mh = (hi & 0xFFFFF) | 0x100000
-        w1 = (lo << j) & MASK32
-        w2 = funnel_l(lo, mh, j)
-        w3 = funnel_l(mh, 0, j)
-        image = (w3 << 96) | (w2 << 64) | (w1 << 32)
-        assert Fraction(image, 2 ** 105) == Fraction(v), v
+        pj = rotl32(1 << 22, hi >> 20)
+        assert pj == 2 ** ((hi >> 20) - 1002) and 2 ** 5 <= pj <= 2 ** 20
+        assert Fraction((mh << 32 | lo) * pj << 32, 2 ** 105) == Fraction(v), v
+        sb = f64_bits(v * v)                        # one round-to-nearest multiply
+        shi, slo = sb >> 32, sb & MASK32
+        mh2 = (shi & 0xFFFFF) | 0x100000
+        pk = rotl32(2, shi >> 20)
+        assert pk == 2 ** ((shi >> 20) - 991) and 1 <= pk <= 2 ** 31
+        img = (mh2 << 32 | slo) * pk
+        assert Fraction(img, 2 ** 84) == Fraction(v * v) and img < 2 ** 84
+        return img, slo * pk, mh2 * pk
+
+    for v in vals:
+        parts(v)
+    pairs = [(rnd.choice(vals), rnd.choice(vals)) for _ in range(8000)]
+    for _ in range(4000):  # pairs on the unit circle to within a few ulps
+        x = rnd.uniform(2.0 ** -16, 1.0)
+        y = math.sqrt(max(0.0, 1 - x * x))
+        for d in (-2, -1, 0, 1, 2):
+            if 2.0 ** -16 <= y + d * 2 ** -53 < 1:
+                pairs.append((x, y + d * 2 ** -53))
+    lim = 2 ** 84 + 2 ** 31
+    for x, y in pairs:
+        ix, lx, hx = parts(x)
+        iy, ly, hy = parts(y)
+        tl, th = lx + ly, hx + hy                   # the two 64-bit partial sums
+        assert tl < 2 ** 64 and th < 2 ** 53
+        S = tl + (th << 32)
+        assert S == ix + iy and S < 2 ** 85
+        assert (S <= lim) == (x * x + y * y <= 1.0), (x, y)
 
 
 def f64_of_bits(b: int) -> float:
@@ -416,14 +446,13 @@ def test_fp64_pipe_conversion_by_one_fused_multiply_add():
         assert f64_bits(float(exact)) == rn_bits(z)  # one rounding of the same value
 
 
-def test_fused_chunk_rule_makes_every_square_fast():
+def test_fused_chunk_rule_puts_every_variate_above_2_16():
     """A fused-consumer chunk is kept when the top word of every step's 53-bit
-    quotient window is at least 2 (q >= 2^33): then z*r3i >= 2^-20, so
-    v = RN(z*r3i) >= 2^-20 and RN(v*v) >= 2^-40, whose exponent puts its
-    2^-157-grid image at least 2^64 up (k = e2 - 918 >= 65): every square of
-    a kept chunk takes the fast (exact 2^-93 grid) form.  At 2^-21 that
-    would fail (k = 63 occurs)."""
-    edge = ((2 ** 33) * M) >> 53  # states around the 2^-20 boundary
+    quotient window is at least 32 (q >= 2^37): then z*r3i >= 2^-16, so
+    v = RN(z*r3i) >= 2^-16 and RN(v*v) >= 2^-32 (exponent e2 >= 991), as the
+    kept-chunk parts need.  Such a variate's square is also on the fast
+    2^-93 grid of the exact path (k = e2 - 918 >= 73)."""
+    edge = ((2 ** 37) * M) >> 53  # states around the 2^-16 boundary
     kept = 0
     for z in states(30000, 23) + [edge + d for d in range(-3, 4)]:
         if not 0 < z < M:
@@ -431,13 +460,13 @@ def test_fused_chunk_rule_makes_every_square_fast():
         q = (z * K) >> 53  # the step's 53-bit quotient window, floor(z*K / 2^53)
         v = float(Fraction(z) * Fraction(R3I))
         e2 = f64_bits(v * v) >> 52
-        if q >> 32 >= 2:
+        if q >> 32 >= 32:
             kept += 1
-            assert Fraction(z) * Fraction(R3I) >= Fraction(1, 2 ** 20)
-            assert v >= 2.0 ** -20 and e2 - 918 >= 65
+            assert Fraction(z) * Fraction(R3I) >= Fraction(1, 2 ** 16)
+            assert v >= 2.0 ** -16 and e2 >= 991
+        elif q >> 32 < 32 and 0 < z < edge - 3:
+            assert v < 2.0 ** -16 + 2.0 ** -60
     assert kept > 29000
-    v21 = 2.0 ** -21
-    assert (f64_bits(v21 * v21) >> 52) - 918 == 63
 
 
 MP = (-pow(M, -1, 2 ** 53)) % 2 ** 53  # m' = -m^-1 mod 2^53
