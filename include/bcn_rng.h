@@ -123,7 +123,9 @@ typedef struct {
   uint32_t conv;    /* rng_conv                                              */
   uint32_t layout;  /* rng_layout                                            */
   uint32_t skip;    /* rng_skip_method                                       */
-  uint32_t depth;   /* TILED: variates per lane per tile, odd, 1..255;
+  uint32_t depth;   /* TILED: variates per lane per tile, odd, 1..255 (FP32
+                       with the shared step on two chains also 4 mod 8:
+                       four variates per shared-memory store);
                        STRIDED: variates per thread                          */
   uint32_t block;   /* threads per block (TILED: multiple of 32, <= 1024)    */
   uint32_t grid;    /* blocks                                                */

@@ -1,7 +1,8 @@
 // bcn_bulk.cu -- bulk generation kernels for one stream (sm_103a).
 //
 // TILED layout (the fast path).  Output elements [head, head + ntiles*32*c)
-// are cut into tiles of 32*c elements (c = depth, odd).  Each warp owns a
+// are cut into tiles of 32*c elements (c = depth: odd, or 4 mod 8 for the
+// backward FP32 runs, which store four variates at a time).  Each warp owns a
 // contiguous range of tiles; in a tile, lane l owns elements [l*c, (l+1)*c)
 // and produces them with c consecutive steps of Eq. 3 from one state, so the
 // per-variate work is one reduction and one conversion.  Lanes write their
@@ -95,6 +96,7 @@ static const void* pick_ilp(int layout, int ilp, uint32_t depth) {
       if (depth == 15) return (const void*)tiled_kernel<DT, ST, CV, 2, 15>;
       if (depth == 31) return (const void*)tiled_kernel<DT, ST, CV, 2, 31>;
       if constexpr (DT == DT_F32) {  // FP32 tiles are half the bytes: deeper ones fit
+        if (depth == 44) return (const void*)tiled_kernel<DT, ST, CV, 2, 44>;
         if (depth == 47) return (const void*)tiled_kernel<DT, ST, CV, 2, 47>;
         if (depth == 63) return (const void*)tiled_kernel<DT, ST, CV, 2, 63>;
       }

@@ -38,11 +38,18 @@ static uint64_t tile_count(uint64_t n, uint64_t head, uint32_t depth) {
 // shape the autotuner picks on GB300 for 2^28 variates of every output type
 // (FP64 756, raw states 821 G/s there, against 573 and 704 with 15-deep tiles
 // in 256-thread blocks).  FP32 tiles are half the bytes, so FP32 can take
-// deeper tiles in the same shared memory: 47-deep measured 1% faster than
-// 63-deep with the backward FP32 step.
+// deeper tiles in the same shared memory.  With the backward FP32 step,
+// 44-deep tiles stored four variates at a time measured 1.5% faster than
+// 47-deep ones stored one at a time, and those 1% faster than 63-deep.
 constexpr uint32_t kDefDepth = 31, kDefBlock = 896, kDefChains = 2, kDefBuffers = 1;
-constexpr uint32_t kDefDepthF32 = 47;
-inline uint32_t def_depth(int dt) { return dt == DT_F32 ? kDefDepthF32 : kDefDepth; }
+constexpr uint32_t kDefDepthF32 = 44, kDefBlockF32 = 1024;
+// Its 44-deep tiles fit 32 warps per SM: 1024-thread blocks (999 against 995
+// G variates/s with 896).  Other FP32 launches (forward steps, one chain)
+// need odd depths: 47.
+constexpr uint32_t kDefDepthF32Odd = 47;
+inline uint32_t def_depth(int dt, bool back32) {
+  return dt == DT_F32 ? (back32 ? kDefDepthF32 : kDefDepthF32Odd) : kDefDepth;
+}
 
 rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* out,
                         bool constant) {
@@ -64,7 +71,11 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
     if (!t.skip) t.skip = d.skip;
     if (same_layout) {
       if (!t.layout) t.layout = d.layout;
-      if (!t.depth) t.depth = d.depth;
+      // an even default depth (the backward FP32 runs' four-variate stores)
+      // goes only to calls that run that same kernel kind
+      const bool same_kind = t.step == d.step && t.conv == d.conv &&
+                             (!t.chains || !d.chains || t.chains == d.chains);
+      if (!t.depth && (d.depth % 2 == 1 || same_kind)) t.depth = d.depth;
       if (!t.block) t.block = d.block;
       if (!t.chains) t.chains = d.chains;
       if (!t.buffers) t.buffers = d.buffers;
@@ -123,17 +134,23 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   L.chains = 1;
   const uint32_t want_chains = t.chains ? t.chains : kDefChains;
   if (L.layout == RNG_LAYOUT_TILED && (L.step == ST_SHARED || L.step == ST_BARRETT) &&
-      want_chains == 2 && (t.depth ? t.depth : def_depth(dt)) >= 3)
+      want_chains == 2 && (t.depth ? t.depth : def_depth(dt, false)) >= 3)
     L.chains = 2;
-  const uint32_t depth0 = L.layout == RNG_LAYOUT_TILED ? (t.depth ? t.depth : def_depth(dt)) : 0;
+  // FP32 with the shared step on two chains runs the backward step
+  const bool back32 = dt == DT_F32 && L.step == ST_SHARED && L.conv == CV_INT && L.chains == 2;
+  const uint32_t depth0 =
+      L.layout == RNG_LAYOUT_TILED ? (t.depth ? t.depth : def_depth(dt, back32)) : 0;
   const void* fn = pick_kernel(L.layout, dt, L.step, L.conv, (int)L.chains, depth0);
   if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   if (L.layout == RNG_LAYOUT_TILED) {
-    L.depth = t.depth ? t.depth : def_depth(dt);
-    L.block = t.block ? t.block : kDefBlock;
-    if (L.depth % 2 == 0 || L.depth > kMaxDepth)
-      return set_error(RNG_EINVAL, "tune.depth %u must be odd and at most %u", L.depth,
-                       kMaxDepth);
+    L.depth = t.depth ? t.depth : def_depth(dt, back32);
+    L.block = t.block ? t.block : (back32 ? kDefBlockF32 : kDefBlock);
+    // odd depths keep the one-variate shared-memory stores bank-conflict free;
+    // the backward FP32 runs also take depths of 4 mod 8 (four-variate stores)
+    if ((L.depth % 2 == 0 && !(back32 && vec4_depth(L.depth))) || L.depth > kMaxDepth)
+      return set_error(RNG_EINVAL,
+                       "tune.depth %u must be odd (FP32 on two chains: or 4 mod 8) and at "
+                       "most %u", L.depth, kMaxDepth);
     if (L.block % 32 != 0 || L.block == 0 || L.block > 1024)
       return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024",
                        L.block);

@@ -289,29 +289,53 @@ __device__ __forceinline__ void shared_run_fast2(uint64_t* mine, uint32_t c, uin
 }
 
 // FP32 output by the backward step with its exact quotient (two chains on
-// y = z - 1): chain b starts one past the run and emits elements c-1 .. h+1,
-// chain a starts at element h+1 and emits h .. 0, so afterwards chain a holds
-// element 0 and chain b element h+1.  Every conversion stays on the integer
-// pipes (taking one in six or twelve on the FP64 pipe, as the forward FP64
-// kernel does, measured 1% slower or no faster with this step).  A lane
-// whose run needs the exact path (see back_step_f32_ptx) redoes it forward
-// from element 0.
+// y = z - 1): with s = chain_split(c), chain b starts one past the run and
+// emits elements c-1 .. s, chain a starts at element s and emits s-1 .. 0, so
+// afterwards chain a holds element 0 and chain b element s.  Every conversion
+// stays on the integer pipes (taking one in six or twelve on the FP64 pipe, as
+// the forward FP64 kernel does, measured 1% slower or no faster with this
+// step).  Depths of 4 mod 8 (compile-time) store four variates at a time:
+// each lane's run then starts 16-byte aligned, and the eight lanes of each
+// 16-byte store phase hit distinct bank groups (c/4 odd); the two chains hold
+// whole groups of four (for c = 44: 24 and 20 elements).  A lane whose run
+// needs the exact path (see back_step_f32_ptx) redoes it forward from
+// element 0.
 template <int CDEPTH>
 __device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_t& ya,
                                              uint64_t& yb) {
   uint32_t qmin = 0xffffffffu;
-  const uint32_t h = CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : c / 2;
-  const uint32_t last = CDEPTH > 0 ? (uint32_t)CDEPTH - 1 : c - 1;
+  if constexpr (CDEPTH > 0 && vec4_depth(CDEPTH)) {
+    constexpr int S = (int)chain_split(CDEPTH), GA = S / 4, GB = (CDEPTH - S) / 4;
+    constexpr int G = GA > GB ? GA : GB;
 #pragma unroll
-  for (uint32_t i = 0; i < h; ++i) {
-    mine[last - i] = back_step_f32_ptx(yb, qmin);
-    mine[h - i] = back_step_f32_ptx(ya, qmin);
+    for (int g = 0; g < G; ++g) {
+      uint32_t va[4], vb[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (g < GB) vb[k] = back_step_f32_ptx(yb, qmin);
+        if (g < GA) va[k] = back_step_f32_ptx(ya, qmin);
+      }
+      if (g < GB)
+        *reinterpret_cast<uint4*>(mine + CDEPTH - 4 * (g + 1)) =
+            make_uint4(vb[3], vb[2], vb[1], vb[0]);
+      if (g < GA)
+        *reinterpret_cast<uint4*>(mine + S - 4 * (g + 1)) = make_uint4(va[3], va[2], va[1], va[0]);
+    }
+  } else {
+    const uint32_t cc = CDEPTH > 0 ? (uint32_t)CDEPTH : c;
+    const uint32_t s = chain_split(cc), nb = cc - s;  // nb <= s
+#pragma unroll
+    for (uint32_t i = 0; i < nb; ++i) {
+      mine[cc - 1 - i] = back_step_f32_ptx(yb, qmin);
+      mine[s - 1 - i] = back_step_f32_ptx(ya, qmin);
+    }
+    for (uint32_t i = nb; i < s; ++i) mine[s - 1 - i] = back_step_f32_ptx(ya, qmin);
   }
-  mine[0] = back_step_f32_ptx(ya, qmin);
   if (__any_sync(0xffffffffu, qmin == 0)) {
     if (qmin == 0) {
+      const uint32_t cc = CDEPTH > 0 ? (uint32_t)CDEPTH : c;
       uint64_t z = ya + 1;  // element 0, forward
-      for (uint32_t i = 0; i <= last; ++i) mine[i] = f32_bits_from_f64_bits(shared_step_f64(z));
+      for (uint32_t i = 0; i < cc; ++i) mine[i] = f32_bits_from_f64_bits(shared_step_f64(z));
     }
     __syncwarp();
   }
@@ -378,14 +402,14 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
 // Initial states of the two chains of a lane whose first run starts at
 // element `first`: forward chains at elements first and first + h + 1 (the
 // FP64 output chains as z 2^10); the backward FP32 chains one past elements
-// h and c - 1, as z - 1.
+// s - 1 and c - 1 (s = chain_split(c)), as z - 1.
 template <int DT, int STEP, int CONV>
 __device__ __forceinline__ void lane_chains2(uint64_t ebase, uint64_t first, uint32_t c,
                                              uint32_t skip, Gen<DT, STEP, CONV>& a,
                                              Gen<DT, STEP, CONV>& b) {
   const uint32_t h = c / 2;
   if constexpr (kBackF32<DT, STEP, CONV>) {
-    a.z = state_of(ebase, first + h + 1, skip) - 1;
+    a.z = state_of(ebase, first + chain_split(c), skip) - 1;
     b.z = state_of(ebase, first + c, skip) - 1;
   } else if constexpr (kScaledF64<DT, STEP, CONV>) {
     a.z = state_of(ebase, first, skip) << kZShift;

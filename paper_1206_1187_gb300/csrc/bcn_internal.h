@@ -27,16 +27,26 @@ struct BulkLaunch {
   size_t smem_bytes;  // TILED only
 };
 
+// Where a lane's run of c elements is split between its two chains: chain a
+// takes elements [0, s), chain b [s, c).  Odd c: s = c/2 + 1.  The backward
+// FP32 runs also take c = 4 mod 8, stored four variates at a time, where s
+// is the larger half in whole groups of four (c = 44: s = 24).
+__host__ __device__ constexpr uint32_t chain_split(uint64_t c) {
+  return (uint32_t)(c % 2 ? c / 2 + 1 : 4 * ((c / 4 + 1) / 2));
+}
+// Whether a backward FP32 run of this depth takes the four-variate stores.
+__host__ __device__ constexpr bool vec4_depth(uint64_t c) { return c % 8 == 4; }
+
 // The tile-to-tile jumps (in steps) of a lane's two chains over tiles of
-// 32*c elements (h = c/2): forward chains move from elements h + 1 and c of
-// the lane's run to elements 0 and h + 1 of its run in the next tile,
+// 32*c elements (s = chain_split(c)): forward chains move from elements s and
+// c of the lane's run to elements 0 and s of its run in the next tile,
 // backward ones (the FP32 step that runs Eq. 3 backwards) from elements 0 and
-// h + 1 to h + 1 and c.
+// s to s and c.
 inline uint64_t chain_jump_a(bool backward, uint64_t c) {
-  return backward ? 32 * c + c / 2 + 1 : 32 * c - c / 2 - 1;
+  return backward ? 32 * c + chain_split(c) : 32 * c - chain_split(c);
 }
 inline uint64_t chain_jump_b(bool backward, uint64_t c) {
-  return backward ? 33 * c - c / 2 - 1 : 31 * c + c / 2 + 1;
+  return backward ? 33 * c - chain_split(c) : 31 * c + chain_split(c);
 }
 
 // Element size in bytes of an rng_dtype.

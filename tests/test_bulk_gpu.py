@@ -108,6 +108,14 @@ def test_two_chains_per_lane(R, oracle_mod, step):
                             chains=2)
             out = R.generate_at(a, off, n, dtype, tune=t)
             assert_same(out, want, f"{step}/{dtype}/{depth}/{block}/{grid}")
+    if step == "shared":  # FP32 runs of 4 mod 8: four variates per shared-memory store
+        want = oracle_mod.generate(a, off, n, "f32")
+        for depth, block, grid in [(4, 32, 1), (12, 96, 0), (44, 896, 0), (44, 1024, 7),
+                                   (252, 32, 0)]:
+            t = R.make_tune(step=step, layout="tiled", depth=depth, block=block, grid=grid,
+                            chains=2)
+            assert_same(R.generate_at(a, off, n, "f32", tune=t), want,
+                        f"{step}/f32/{depth}/{block}/{grid}")
 
 
 def test_windows_around_tiny_variates(R, oracle_mod):
@@ -125,6 +133,9 @@ def test_windows_around_tiny_variates(R, oracle_mod):
         for depth in (5, 9, 15, 31, 63):
             t = R.make_tune(step="shared", layout="tiled", depth=depth)
             assert_same(R.generate_at(a, off, 6001, "f64", tune=t), want64, f"f64 {i} {depth}")
+            assert_same(R.generate_at(a, off, 6001, "f32", tune=t), want32, f"f32 {i} {depth}")
+        for depth in (12, 44):
+            t = R.make_tune(step="shared", layout="tiled", depth=depth)
             assert_same(R.generate_at(a, off, 6001, "f32", tune=t), want32, f"f32 {i} {depth}")
 
 
@@ -222,9 +233,16 @@ def test_seed_bounds_on_device(R, oracle_mod):
 
 def test_bad_tuning_is_rejected(R):
     for kw in ({"depth": 16, "layout": "tiled"}, {"block": 48, "layout": "tiled"},
-               {"block": 2048}, {"step": 9}, {"conv": 5}, {"skip": 4}):
+               {"block": 2048}, {"step": 9}, {"conv": 5}, {"skip": 4},
+               {"depth": 12, "layout": "tiled"}):
         with pytest.raises(R.RNGError) as e:
             R.generate_at(M + 100, 0, 1000, "f64", tune=R.make_tune(**kw))
+        assert e.value.status == 1
+    # even depths: FP32 on two chains takes 4 mod 8 only
+    for kw in ({"depth": 16}, {"depth": 6}, {"depth": 12, "chains": 1},
+               {"depth": 12, "step": "barrett"}):
+        with pytest.raises(R.RNGError) as e:
+            R.generate_at(M + 100, 0, 1000, "f32", tune=R.make_tune(layout="tiled", **kw))
         assert e.value.status == 1
 
 
@@ -438,7 +456,8 @@ def test_fp32_near_float_boundaries(R, oracle_mod):
                     break
     assert len(targets) >= 12
     shapes = [dict(), dict(depth=31), dict(depth=47, block=768), dict(depth=45, chains=2),
-              dict(depth=63, chains=1), dict(depth=5, block=128)]
+              dict(depth=63, chains=1), dict(depth=5, block=128), dict(depth=44, block=1024),
+              dict(depth=12, block=96)]
     for z in targets:
         e = dlog2(z * h_inv % M, 33)
         i = ((e - (a - M)) * pow(53, -1, P) - 1) % P
@@ -464,12 +483,14 @@ def test_small_calls_spread_their_tiles_over_every_sm(R, oracle_mod):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     for dtype, n in (("f64", 10 ** 6), ("f32", 10 ** 6), ("f64", 3 * 10 ** 5)):
+        full = 1024 if dtype == "f32" else 896  # the default block of a large call
         auto = R.resolve_tune(n, dtype)
         tiles = n // (32 * auto["depth"])
-        assert auto["block"] < 896 and auto["block"] % 32 == 0, (dtype, n, auto)
+        assert auto["block"] < full and auto["block"] % 32 == 0, (dtype, n, auto)
         assert auto["grid"] * auto["block"] // 32 >= min(tiles, sms), (dtype, n, auto)
         assert R.resolve_tune(n, dtype, R.make_tune(block=896))["block"] == 896
-        assert R.resolve_tune(n, dtype, R.make_tune(grid=16))["block"] == 896
+        assert R.resolve_tune(n, dtype, R.make_tune(grid=16))["block"] == full
         a = M + 1618
         assert_same(R.generate_at(a, 99, n, dtype), oracle_mod.generate(a, 99, n, dtype), dtype)
     assert R.resolve_tune(1 << 28, "f64")["block"] == 896
+    assert R.resolve_tune(1 << 28, "f32")["block"] == 1024
