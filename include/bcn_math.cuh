@@ -492,15 +492,11 @@ __device__ __forceinline__ uint64_t shared_advance(uint64_t z) {
   return r;
 }
 
-// FP64-pipe conversion: exact int->double, then one RN multiply (no FMA).
-// Both operations run on the FP64 pipe and none on the integer pipes, which
-// is what a kernel bound by its integer work wants from it.
-__device__ __forceinline__ uint64_t f64_bits_fp64(uint64_t z) {
-  double v = __dmul_rn(__ull2double_rn(z), kR3i);
-  return (uint64_t)__double_as_longlong(v);
-}
-// The same from a scaled chain value Z = z 2^10: Z converts exactly (53
-// significant bits) and Z (r3i 2^-10) = z r3i, so the rounding is the same.
+// FP64-pipe conversion from a scaled chain value Z = z 2^10: exact
+// int->double (Z has 53 significant bits), then one RN multiply by r3i 2^-10
+// (no FMA): Z (r3i 2^-10) = z r3i, so the rounding is RN(z r3i) itself.  Both
+// operations run on the FP64 pipe and none on the integer pipes, which is what
+// a kernel bound by its integer work wants from it.
 constexpr double kR3iScaled = kR3i * 0x1p-10;
 __device__ __forceinline__ uint64_t f64_bits_fp64_scaled(uint64_t Z) {
   double v = __dmul_rn(__ull2double_rn(Z), kR3iScaled);
