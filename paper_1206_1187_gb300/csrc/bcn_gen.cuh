@@ -233,12 +233,13 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
   }
 }
 
-// Two independent chains per lane: the lane's run of c = 2h+1 elements is
-// split into its first h+1 elements (chain a) and its last h (chain b), and
+// Two independent chains per lane: the lane's run of c elements is split at
+// s = chain_split(c) into elements [0, s) (chain a) and [s, c) (chain b), and
 // the two chains step alternately, so each step's latency is hidden behind
-// the other chain's work.  Stores to mine[i] and mine[h+1+i] keep lane
-// stride c (odd), so they stay bank-conflict free.  Between tiles chain a
-// jumps by 32c-h-1 steps and chain b by 31c+h+1.  Forward steps only.
+// the other chain's work.  With odd c (s = h+1, h = c/2) the stores to mine[i]
+// and mine[h+1+i] keep lane stride c, so they stay bank-conflict free.
+// Between tiles the forward chains jump by 32c-s and 31c+s steps, the
+// backward FP32 chains by 32c+s and 33c-s (chain_jump_a / chain_jump_b).
 
 // The FP64 output chains of the two-chain loop hold Z = z 2^10 (see
 // shared_step_f64_ptx).  Every fourth iteration (compile-time depths) takes
