@@ -42,6 +42,8 @@ def bulk_candidates(dtype: str) -> list[dict]:
     # share an SM's shared memory
     if dtype != "u64":
         wide = [(15, (768, 1024)), (31, (640, 768, 896))]
+        if dtype == "f64":  # 30: 2 mod 4, two variates per shared-memory store
+            wide += [(30, (640, 768, 896))]
         if dtype == "f32":  # FP32 tiles are half the bytes: deeper ones fit (44: 4 mod 8,
             # four variates per shared-memory store)
             wide += [(44, (768, 896, 1024)), (47, (768, 896, 1024)), (63, (512, 640, 768, 896))]

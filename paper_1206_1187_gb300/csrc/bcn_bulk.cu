@@ -2,7 +2,8 @@
 //
 // TILED layout (the fast path).  Output elements [head, head + ntiles*32*c)
 // are cut into tiles of 32*c elements (c = depth: odd, or 4 mod 8 for the
-// backward FP32 runs, which store four variates at a time).  Each warp owns a
+// backward FP32 runs, which store four variates at a time, or 2 mod 4 for the
+// forward FP64 runs on two chains, which store two).  Each warp owns a
 // contiguous range of tiles; in a tile, lane l owns elements [l*c, (l+1)*c)
 // and produces them with c consecutive steps of Eq. 3 from one state, so the
 // per-variate work is one reduction and one conversion.  Lanes write their
@@ -22,8 +23,8 @@
 // counts (down to one thread) and is the uncoalesced baseline.
 //
 // The head (elements before the first 16-byte boundary) and the tail (fewer
-// than one tile) are produced by the last warp of the grid with direct
-// stores.  Every element's value depends only on its index, so the result is
+// than one tile) are produced with direct stores by the grid's last warps.
+// Every element's value depends only on its index, so the result is
 // identical for every layout, depth, block and grid.
 #include "bcn_bulk.cuh"
 #include "bcn_gen.cuh"
@@ -65,14 +66,22 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
     __syncwarp();
   }
 
-  if (gw == nw - 1) {  // head and tail, split contiguously over the lanes
-    const uint64_t tail0 = p.head + p.ntiles * tile_elems;
-    const uint64_t tl = p.n - tail0;
+  // The tail (less than one tile) is spread over the grid's last warps, at
+  // most four elements per lane, so that no warp's exact single-chain steps
+  // outlast the tiles (a 640-element tail on one warp added about a microsecond
+  // to a 10^6-variate call); the head (under 16 bytes) goes to the last warp.
+  const uint64_t tail0 = p.head + p.ntiles * tile_elems;
+  const uint64_t tl = p.n - tail0;
+  const uint64_t wt = min(nw, (tl + 127) / 128);
+  if (gw + wt >= nw) {
+    const uint64_t k = gw - (nw - wt);
+    const uint64_t lo = tail0 + k * tl / wt, len = tail0 + (k + 1) * tl / wt - lo;
+    run_direct<DT, STEP, CONV>(out, p.ebase, p.skip, lo + lane * len / 32,
+                               lo + (lane + 1) * len / 32, p.cbits);
+  }
+  if (gw == nw - 1)
     run_direct<DT, STEP, CONV>(out, p.ebase, p.skip, lane * p.head / 32,
                                (lane + 1) * p.head / 32, p.cbits);
-    run_direct<DT, STEP, CONV>(out, p.ebase, p.skip, tail0 + lane * tl / 32,
-                               tail0 + (lane + 1) * tl / 32, p.cbits);
-  }
 }
 
 template <int DT, int STEP, int CONV>
@@ -95,6 +104,9 @@ static const void* pick_ilp(int layout, int ilp, uint32_t depth) {
       if (depth == 9) return (const void*)tiled_kernel<DT, ST, CV, 2, 9>;
       if (depth == 15) return (const void*)tiled_kernel<DT, ST, CV, 2, 15>;
       if (depth == 31) return (const void*)tiled_kernel<DT, ST, CV, 2, 31>;
+      if constexpr (DT == DT_F64) {  // two variates per shared-memory store
+        if (depth == 30) return (const void*)tiled_kernel<DT, ST, CV, 2, 30>;
+      }
       if constexpr (DT == DT_F32) {  // FP32 tiles are half the bytes: deeper ones fit
         if (depth == 44) return (const void*)tiled_kernel<DT, ST, CV, 2, 44>;
         if (depth == 47) return (const void*)tiled_kernel<DT, ST, CV, 2, 47>;

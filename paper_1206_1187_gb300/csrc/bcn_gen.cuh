@@ -242,14 +242,16 @@ __device__ __forceinline__ void warp_tiles(typename Word<DT>::type* __restrict__
 // backward FP32 chains by 32c+s and 33c-s (chain_jump_a / chain_jump_b).
 
 // The FP64 output chains of the two-chain loop hold Z = z 2^10 (see
-// shared_step_f64_ptx).  Every fourth iteration (compile-time depths) takes
-// one conversion on the FP64 pipe, alternating between chain a (iterations
-// 0, 8, 16, ...) and chain b (4, 12, ...): int->double and one
+// shared_step_f64_ptx).  In runs of compile-time depth some iterations take
+// their conversion on the FP64 pipe, alternating between chain a (iteration
+// 0 of every K) and chain b (iteration K/2): int->double and one
 // round-to-nearest multiply, the definition itself, instead of the integer
-// rounding.  The FP64 pipe is otherwise idle here; with the scaled step an
-// eighth of the conversions measured as fast as a sixth and faster than a
-// quarter (787, 787, 785 G variates/s) or a third (771).  Same bits either way.
-constexpr uint32_t kFp64ConvEvery = 8;
+// rounding.  The FP64 pipe is otherwise idle here.  One-variate runs (odd
+// depths) take K = 8, an eighth of the conversions (787 G variates/s in a
+// test kernel against 787 for a sixth, 785 for a quarter and 771 for a
+// third); two-variate runs (depths of 2 mod 4) take K = 6 (812 against 808
+// for an eighth).  Same bits either way.
+constexpr uint32_t kFp64ConvEvery = 8, kFp64ConvEveryVec2 = 6;
 __device__ __forceinline__ uint64_t fp64_conv_step_scaled(uint64_t& Z) {
   const uint64_t bits = f64_bits_fp64_scaled(Z);
   Z = shared_advance_scaled(Z);
@@ -264,26 +266,56 @@ __device__ __forceinline__ uint64_t fast_word(uint64_t& Z, uint32_t& qmin, bool 
 }
 
 // The two interleaved scaled chains of the branch-free shared-quotient step
-// over one run of FP64 output; a lane that left the fast path redoes its run
-// with one exact chain on z.
+// over one run of FP64 output, split at s = chain_split(c); a lane that left
+// the fast path redoes its run with one exact chain on z.  Depths of 2 mod 4
+// (compile-time) store two variates at a time: each lane's run then starts
+// 16-byte aligned and the eight lanes of each 16-byte store phase hit
+// distinct bank groups (c/2 odd); 30-deep runs split 16/14 this way measured
+// 808 against 789 G variates/s for 31-deep one-variate runs in a test kernel.
 template <int CDEPTH>
 __device__ __forceinline__ void shared_run_fast2(uint64_t* mine, uint32_t c, uint64_t& za,
                                                  uint64_t& zb) {
   const uint64_t a_start = za;
   uint32_t qmin = 0xffffffffu;
-  const uint32_t h = CDEPTH > 0 ? (uint32_t)CDEPTH / 2 : c / 2;
+  if constexpr (CDEPTH > 0 && vec2_depth(CDEPTH)) {
+    constexpr int S = (int)chain_split(CDEPTH), GA = S / 2, GB = (CDEPTH - S) / 2;
+    constexpr int G = GA > GB ? GA : GB;
+    constexpr int K = (int)kFp64ConvEveryVec2;
 #pragma unroll
-  for (uint32_t i = 0; i < h; ++i) {
+    for (int g = 0; g < G; ++g) {
+      uint64_t va[2], vb[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int i = 2 * g + k;
+        if (g < GA) va[k] = fast_word(za, qmin, i % K == 0);
+        if (g < GB) vb[k] = fast_word(zb, qmin, i % K == K / 2);
+      }
+      if (g < GA)
+        *reinterpret_cast<uint4*>(mine + 2 * g) =
+            make_uint4((uint32_t)va[0], (uint32_t)(va[0] >> 32), (uint32_t)va[1],
+                       (uint32_t)(va[1] >> 32));
+      if (g < GB)
+        *reinterpret_cast<uint4*>(mine + S + 2 * g) =
+            make_uint4((uint32_t)vb[0], (uint32_t)(vb[0] >> 32), (uint32_t)vb[1],
+                       (uint32_t)(vb[1] >> 32));
+    }
+  } else {
+    const uint32_t cc = CDEPTH > 0 ? (uint32_t)CDEPTH : c;
+    const uint32_t s = chain_split(cc), nb = cc - s;  // nb <= s
     constexpr uint32_t K = kFp64ConvEvery;
-    mine[i] = fast_word(za, qmin, CDEPTH > 0 && i % K == 0);
-    mine[h + 1 + i] = fast_word(zb, qmin, CDEPTH > 0 && i % K == K / 2);
+#pragma unroll
+    for (uint32_t i = 0; i < nb; ++i) {
+      mine[i] = fast_word(za, qmin, CDEPTH > 0 && i % K == 0);
+      mine[s + i] = fast_word(zb, qmin, CDEPTH > 0 && i % K == K / 2);
+    }
+    for (uint32_t i = nb; i < s; ++i) mine[i] = fast_word(za, qmin, false);
   }
-  mine[h] = fast_word(za, qmin, false);
   const bool rare = qmin == 0;
   if (__any_sync(0xffffffffu, rare)) {
     if (rare) {
+      const uint32_t cc = CDEPTH > 0 ? (uint32_t)CDEPTH : c;
       uint64_t y = a_start >> kZShift;
-      for (uint32_t i = 0; i < c; ++i) mine[i] = shared_step_f64(y);
+      for (uint32_t i = 0; i < cc; ++i) mine[i] = shared_step_f64(y);
     }
     __syncwarp();
   }
@@ -401,9 +433,9 @@ __device__ __forceinline__ void warp_tiles2(typename Word<DT>::type* __restrict_
 }
 
 // Initial states of the two chains of a lane whose first run starts at
-// element `first`: forward chains at elements first and first + h + 1 (the
-// FP64 output chains as z 2^10); the backward FP32 chains one past elements
-// s - 1 and c - 1 (s = chain_split(c)), as z - 1.
+// element `first` (s = chain_split(c)): forward chains at elements first and
+// first + s (the FP64 output chains as z 2^10); the backward FP32 chains one
+// past elements s - 1 and c - 1, as z - 1.
 template <int DT, int STEP, int CONV>
 __device__ __forceinline__ void lane_chains2(uint64_t ebase, uint64_t first, uint32_t c,
                                              uint32_t skip, Gen<DT, STEP, CONV>& a,
@@ -414,7 +446,7 @@ __device__ __forceinline__ void lane_chains2(uint64_t ebase, uint64_t first, uin
     b.z = state_of(ebase, first + c, skip) - 1;
   } else if constexpr (kScaledF64<DT, STEP, CONV>) {
     a.z = state_of(ebase, first, skip) << kZShift;
-    b.z = state_of(ebase, first + h + 1, skip) << kZShift;
+    b.z = state_of(ebase, first + chain_split(c), skip) << kZShift;
   } else {
     a.z = state_of(ebase, first, skip);
     b.z = state_of(ebase, first + h + 1, skip);

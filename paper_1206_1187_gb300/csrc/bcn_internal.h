@@ -30,12 +30,17 @@ struct BulkLaunch {
 // Where a lane's run of c elements is split between its two chains: chain a
 // takes elements [0, s), chain b [s, c).  Odd c: s = c/2 + 1.  The backward
 // FP32 runs also take c = 4 mod 8, stored four variates at a time, where s
-// is the larger half in whole groups of four (c = 44: s = 24).
+// is the larger half in whole groups of four (c = 44: s = 24); the forward
+// FP64 runs c = 2 mod 4, stored two variates at a time, where s is the larger
+// half in whole pairs (c = 30: s = 16).
 __host__ __device__ constexpr uint32_t chain_split(uint64_t c) {
-  return (uint32_t)(c % 2 ? c / 2 + 1 : 4 * ((c / 4 + 1) / 2));
+  return (uint32_t)(c % 2 ? c / 2 + 1
+                          : c % 4 == 2 ? 2 * ((c / 2 + 1) / 2) : 4 * ((c / 4 + 1) / 2));
 }
 // Whether a backward FP32 run of this depth takes the four-variate stores.
 __host__ __device__ constexpr bool vec4_depth(uint64_t c) { return c % 8 == 4; }
+// Whether a forward FP64 run of this depth takes the two-variate stores.
+__host__ __device__ constexpr bool vec2_depth(uint64_t c) { return c % 4 == 2; }
 
 // The tile-to-tile jumps (in steps) of a lane's two chains over tiles of
 // 32*c elements (s = chain_split(c)): forward chains move from elements s and

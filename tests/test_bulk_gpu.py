@@ -108,6 +108,14 @@ def test_two_chains_per_lane(R, oracle_mod, step):
                             chains=2)
             out = R.generate_at(a, off, n, dtype, tune=t)
             assert_same(out, want, f"{step}/{dtype}/{depth}/{block}/{grid}")
+    if step == "shared":  # FP64 runs of 2 mod 4: two variates per shared-memory store
+        want = oracle_mod.generate(a, off, n, "f64")
+        for depth, block, grid in [(10, 32, 1), (6, 96, 0), (30, 896, 0), (30, 640, 7),
+                                   (254, 32, 0)]:
+            t = R.make_tune(step=step, layout="tiled", depth=depth, block=block, grid=grid,
+                            chains=2)
+            assert_same(R.generate_at(a, off, n, "f64", tune=t), want,
+                        f"{step}/f64/{depth}/{block}/{grid}")
     if step == "shared":  # FP32 runs of 4 mod 8: four variates per shared-memory store
         want = oracle_mod.generate(a, off, n, "f32")
         for depth, block, grid in [(4, 32, 1), (12, 96, 0), (44, 896, 0), (44, 1024, 7),
@@ -137,6 +145,9 @@ def test_windows_around_tiny_variates(R, oracle_mod):
         for depth in (12, 44):
             t = R.make_tune(step="shared", layout="tiled", depth=depth)
             assert_same(R.generate_at(a, off, 6001, "f32", tune=t), want32, f"f32 {i} {depth}")
+        for depth in (6, 30):
+            t = R.make_tune(step="shared", layout="tiled", depth=depth)
+            assert_same(R.generate_at(a, off, 6001, "f64", tune=t), want64, f"f64 {i} {depth}")
 
 
 def test_device_side_api_matches_the_oracle(R, oracle_mod):
@@ -238,12 +249,16 @@ def test_bad_tuning_is_rejected(R):
         with pytest.raises(R.RNGError) as e:
             R.generate_at(M + 100, 0, 1000, "f64", tune=R.make_tune(**kw))
         assert e.value.status == 1
-    # even depths: FP32 on two chains takes 4 mod 8 only
-    for kw in ({"depth": 16}, {"depth": 6}, {"depth": 12, "chains": 1},
-               {"depth": 12, "step": "barrett"}):
+    # even depths: on two chains with the shared step FP32 takes 4 mod 8 only,
+    # FP64 2 mod 4 only, raw states none
+    for dtype, kw in (("f32", {"depth": 16}), ("f32", {"depth": 6}), ("f32", {"depth": 30}),
+                      ("f32", {"depth": 12, "chains": 1}), ("f32", {"depth": 12, "step": "barrett"}),
+                      ("f64", {"depth": 44}), ("f64", {"depth": 30, "chains": 1}),
+                      ("f64", {"depth": 30, "step": "barrett"}), ("f64", {"depth": 30, "conv": "fp64"}),
+                      ("u64", {"depth": 30}), ("u64", {"depth": 44})):
         with pytest.raises(R.RNGError) as e:
-            R.generate_at(M + 100, 0, 1000, "f32", tune=R.make_tune(layout="tiled", **kw))
-        assert e.value.status == 1
+            R.generate_at(M + 100, 0, 1000, dtype, tune=R.make_tune(layout="tiled", **kw))
+        assert e.value.status == 1, (dtype, kw)
 
 
 def test_oversized_tiles_shrink_the_block_by_whole_warps(R, oracle_mod):
