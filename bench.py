@@ -364,9 +364,11 @@ def cpu_baseline_config1():
                               "sample": f"the whole workload; {dt1:.3f} s"}}
 
 
-def measure_batched(rng, stream, achieved_gbs: float, steps: int):
+def measure_batched(rng, stream, achieved_gbs: float, steps: int, rates=None):
     """The batched form: 4096 streams of log-uniform length 10^3..10^7, FP64
-    and FP32 alternating, one persistent launch replayed as a CUDA graph."""
+    and FP32 alternating, one persistent launch replayed as a CUDA graph.
+    `rates` ({"f64": variates/s, "f32": variates/s}, this run's single-stream
+    kernels) gives the time those kernels would take for the same mix."""
     import torch
     from paper_1206_1187_gb300 import inputs
     from paper_1206_1187_gb300 import autotune
@@ -398,6 +400,11 @@ def measure_batched(rng, stream, achieved_gbs: float, steps: int):
                         peaks)
     roof["traffic_note"] = ("DRAM bytes per algorithmic byte of a 512-stream subset (profiles/), "
                             "times this workload's bytes")
+    mix = None
+    if rates and rates.get("f64") and rates.get("f32"):
+        # the single-stream kernels' time for the same FP64/FP32 variates, over this time
+        mix_s = sum(int(c) / rates[d] for c, d in zip(counts, dtypes))
+        mix = mix_s / (ms / 1e3)
     return {"workload": "4096 streams, seeds default_rng(7) in [3^33+100, 2^53-10^8], lengths "
                         "log-uniform 10^3..10^7, FP64/FP32 alternating, one persistent launch "
                         "replayed as a CUDA graph",
@@ -406,6 +413,7 @@ def measure_batched(rng, stream, achieved_gbs: float, steps: int):
             "variates_per_s": info["elems"] / (ms / 1e3), "gbs": gbs,
             "frac_of_peak": gbs / peaks["hbm_gbs"],
             "vs_single_stream_gbs": gbs / achieved_gbs,
+            "vs_single_stream_mix": mix,
             "roofline": roof,
             "roofline_alu": issue_roofline(
                 profiled_value("inst_per_variate", "batch_512", "batch"),
@@ -816,8 +824,10 @@ def run_ours(args):
         serving = measure_serving(rng)
     batched = None
     if not args.no_batch and rank == 0:
+        rates = {"f64": n / (ms / 1e3),
+                 "f32": (others or {}).get("f32", {}).get("variates_per_s")}
         batched = measure_batched(rng, stream, achieved_gbs=8.0 * n / (ms / 1e3) / 1e9,
-                                  steps=max(min(args.steps // 20, 50), 5))
+                                  steps=max(min(args.steps // 20, 50), 5), rates=rates)
 
 
     config1 = None

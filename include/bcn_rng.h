@@ -114,8 +114,10 @@ typedef enum {
 
 /* Launch tuning.  Zero in any field means "choose": the tuning installed by
  * rng_set_auto_tune for the output type if any, else the shape measured best
- * on GB300 (tiles 31 deep, 896-thread blocks, two chains per lane, one tile
- * buffer per warp; batch plans also 64-tile work units).  Results never
+ * on GB300: two chains per lane, one tile buffer per warp, and tiles 30 deep
+ * in 896-thread blocks for FP64, 44 deep in 1024-thread blocks for FP32, 31
+ * deep in 896-thread blocks for raw states (batch plans: 896-thread blocks,
+ * each stream's tiles of its type's depth, 64-tile work units).  Results never
  * depend on these fields, only speed does -- except layout =
  * RNG_LAYOUT_STRIDED, which writes the paper's permuted order. */
 typedef struct {
@@ -123,9 +125,10 @@ typedef struct {
   uint32_t conv;    /* rng_conv                                              */
   uint32_t layout;  /* rng_layout                                            */
   uint32_t skip;    /* rng_skip_method                                       */
-  uint32_t depth;   /* TILED: variates per lane per tile, odd, 1..255 (FP32
-                       with the shared step on two chains also 4 mod 8:
-                       four variates per shared-memory store);
+  uint32_t depth;   /* TILED: variates per lane per tile, odd, 1..255; with
+                       the shared step on two chains also FP32 depths of
+                       4 mod 8 (four variates per shared-memory store) and
+                       FP64 depths of 2 mod 4 (two per store);
                        STRIDED: variates per thread                          */
   uint32_t block;   /* threads per block (TILED: multiple of 32, <= 1024)    */
   uint32_t grid;    /* blocks                                                */
@@ -233,7 +236,9 @@ rng_status rng_batch_launch(bcn_batch *b, void *cuda_stream);
  * cudaGraphLaunch per call on `cuda_stream`). */
 rng_status rng_batch_graph_launch(bcn_batch *b, void *cuda_stream);
 
-/* Totals of the plan and its resolved tuning (each pointer nullable). */
+/* Totals of the plan and its resolved tuning (each pointer nullable); a
+ * resolved depth of 0 means each stream's tiles take its type's built-in depth
+ * (FP64 30, FP32 44, raw states 31). */
 rng_status rng_batch_info(const bcn_batch *b, uint64_t *total_elems, uint64_t *total_bytes,
                           uint64_t *units, rng_tune *resolved);
 
@@ -251,8 +256,9 @@ rng_status rng_batch_destroy(bcn_batch *b);
  * instead of a cudaMalloc'd plan, and it allocates no device or host memory.
  *   - At most 1024 streams per call; more is RNG_ERANGE.  The array (about
  *     49 KB) is held by every device that loads the library until exit.
- *   - Zero tuning fields take a batch plan's shape (31-deep tiles,
- *     896-thread blocks, one buffer per warp, 64-tile work units).
+ *   - Zero tuning fields take a batch plan's shape (tiles 30 deep for FP64
+ *     streams, 44 for FP32, 31 for raw states; 896-thread blocks, one buffer
+ *     per warp, 64-tile work units).
  *   - The first call on a device, with that device current, looks up the
  *     array's device address, and the first call with each kernel shape
  *     (step, conversion, chains, depth) sets that kernel's shared-memory

@@ -111,6 +111,9 @@ def batch_candidates() -> list[dict]:
     cands += [dict(step="shared", conv="int", depth=d, block=b, chains=2, unit=u, buffers=1)
               for d, blocks in ((15, (512, 768, 1024)), (31, (512, 640, 768, 896)))
               for b in blocks for u in BATCH_UNITS]
+    # the built-in per-type depths (FP64 30, FP32 44, raw states 31)
+    cands += [dict(step="shared", conv="int", depth=0, block=b, chains=2, unit=u, buffers=1)
+              for b in (640, 768, 896) for u in BATCH_UNITS]
     return cands
 
 

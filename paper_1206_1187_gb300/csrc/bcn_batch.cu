@@ -29,7 +29,7 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const
                                            uint32_t lane) {
   typedef typename Word<DT>::type W;
   W* const out = reinterpret_cast<W*>(d.out);
-  const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : p.depth;
+  const uint32_t c = CDEPTH > 0 ? (uint32_t)CDEPTH : p.depth[DT];
   const uint64_t tile_elems = 32ull * c;
   const uint64_t unit_elems = tile_elems * p.unit_tiles;
   const uint64_t s0 = d.head + k * unit_elems;
@@ -44,13 +44,9 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const
     if constexpr (ILP == 2) {
       Gen<DT, STEP, CONV> a{0}, b{0};
       lane_chains2<DT, STEP, CONV>(d.ebase, first, c, p.skip, a, b);
-      constexpr bool back = kBackF32<DT, STEP, CONV>;
-      warp_tiles2<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, back ? p.back_a : p.jump_a,
-                                          back ? p.back_aq : p.jump_aq,
-                                          back ? p.back_b : p.jump_b,
-                                          back ? p.back_bq : p.jump_bq, a, b,
-                                          reinterpret_cast<W*>(buf0_bytes), issued, lane,
-                                          p.nbuf);
+      warp_tiles2<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.ja[DT], p.jaq[DT], p.jb[DT],
+                                          p.jbq[DT], a, b, reinterpret_cast<W*>(buf0_bytes),
+                                          issued, lane, p.nbuf);
     } else {
       Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(d.ebase, first, c, p.skip);
       warp_tiles<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.jump, p.jump_q, g,
@@ -63,13 +59,15 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const
                              0);
 }
 
-template <int STEP, int CONV, int ILP, int CDEPTH>
+// C64, C32: compile-time tile depths of the FP64 and FP32 streams (0: the
+// run-time depths); raw states always take their run-time depth.
+template <int STEP, int CONV, int ILP, int C64, int C32>
 __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
-  // p.nbuf tile buffers per warp, sized for 8-byte elements
-  unsigned char* const buf0 = smem + (size_t)warp * p.nbuf * 32u * p.depth * 8u;
+  // p.nbuf tile buffers per warp, each sized for the largest type's tile
+  unsigned char* const buf0 = smem + (size_t)warp * p.nbuf * p.warp_bytes;
   uint32_t issued = 0;
   for (;;) {
     unsigned long long u = 0;
@@ -85,40 +83,43 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams p) {
     }
     const BatchDesc d = p.desc[lo];
     const uint64_t k = u - d.unit0;
-    if (d.dt == DT_F64) batch_unit<DT_F64, STEP, CONV, ILP, CDEPTH>(d, k, p, buf0, issued, lane);
-    else if (d.dt == DT_F32) batch_unit<DT_F32, STEP, CONV, ILP, CDEPTH>(d, k, p, buf0, issued, lane);
+    if (d.dt == DT_F64) batch_unit<DT_F64, STEP, CONV, ILP, C64>(d, k, p, buf0, issued, lane);
+    else if (d.dt == DT_F32) batch_unit<DT_F32, STEP, CONV, ILP, C32>(d, k, p, buf0, issued, lane);
     else batch_unit<DT_U64, STEP, CONV, ILP, 0>(d, k, p, buf0, issued, lane);
   }
   if (lane == 0) bulk_wait_all();
   __syncwarp();
 }
 
-static const void* pick_batch(int st, int cv, int ilp, uint32_t depth) {
+static const void* pick_batch(int st, int cv, int ilp, const uint32_t d[3]) {
+  const bool same = d[DT_F64] == d[DT_F32] && d[DT_F64] == d[DT_U64];
   if (st == ST_SHARED && cv == CV_INT) {  // the production path: fixed depths
     if (ilp == 2) {
-      if (depth == 15) return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 15>;
-      if (depth == 31) return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 31>;
-      return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 0>;
+      if (d[DT_F64] == kBatchDepthF64 && d[DT_F32] == kBatchDepthF32)
+        return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, kBatchDepthF64, kBatchDepthF32>;
+      if (same && d[0] == 15) return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 15, 15>;
+      if (same && d[0] == 31) return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 31, 31>;
+      return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 0, 0>;
     }
-    if (depth == 15) return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 15>;
-    if (depth == 31) return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 31>;
-    return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 0>;
+    if (same && d[0] == 15) return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 15, 15>;
+    if (same && d[0] == 31) return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 31, 31>;
+    return (const void*)batch_kernel<ST_SHARED, CV_INT, 1, 0, 0>;
   }
   switch (st) {
-    case ST_SHARED: return (const void*)batch_kernel<ST_SHARED, CV_FP64, 1, 0>;
+    case ST_SHARED: return (const void*)batch_kernel<ST_SHARED, CV_FP64, 1, 0, 0>;
     case ST_BARRETT:
-      if (ilp == 2) return cv == CV_FP64 ? (const void*)batch_kernel<ST_BARRETT, CV_FP64, 2, 0>
-                                         : (const void*)batch_kernel<ST_BARRETT, CV_INT, 2, 0>;
-      return cv == CV_FP64 ? (const void*)batch_kernel<ST_BARRETT, CV_FP64, 1, 0>
-                           : (const void*)batch_kernel<ST_BARRETT, CV_INT, 1, 0>;
-    case ST_MONT: return cv == CV_FP64 ? (const void*)batch_kernel<ST_MONT, CV_FP64, 1, 0>
-                                       : (const void*)batch_kernel<ST_MONT, CV_INT, 1, 0>;
+      if (ilp == 2) return cv == CV_FP64 ? (const void*)batch_kernel<ST_BARRETT, CV_FP64, 2, 0, 0>
+                                         : (const void*)batch_kernel<ST_BARRETT, CV_INT, 2, 0, 0>;
+      return cv == CV_FP64 ? (const void*)batch_kernel<ST_BARRETT, CV_FP64, 1, 0, 0>
+                           : (const void*)batch_kernel<ST_BARRETT, CV_INT, 1, 0, 0>;
+    case ST_MONT: return cv == CV_FP64 ? (const void*)batch_kernel<ST_MONT, CV_FP64, 1, 0, 0>
+                                       : (const void*)batch_kernel<ST_MONT, CV_INT, 1, 0, 0>;
     default: return nullptr;
   }
 }
 
-const void* batch_kernel_fn(int step, int conv, int chains, uint32_t depth) {
-  return pick_batch(step, conv, chains, depth);
+const void* batch_kernel_fn(int step, int conv, int chains, const uint32_t d[3]) {
+  return pick_batch(step, conv, chains, d);
 }
 
 }  // namespace bcn

@@ -15,8 +15,7 @@ struct bcn_batch {
   uint64_t total_units;
   uint64_t total_elems;
   uint64_t total_bytes;
-  rng_tune tune;       // resolved
-  uint32_t unit_elems;
+  rng_tune tune;       // resolved (depth 0: the built-in per-type depths)
   void* dev;           // descriptors | prefix | counter (one allocation)
   size_t dev_bytes;
   cudaGraph_t graph;
@@ -37,23 +36,28 @@ static void longest_first(uint32_t* order, uint32_t nstreams, const uint64_t* co
   });
 }
 
-void batch_fill_jumps(BatchParams& p, int step, uint32_t depth) {
+// The tile-jump multipliers of every element type; with two chains, FP32
+// runs the backward step when the step is the shared one with the integer
+// conversion.  One chain per lane only occurs with one depth for every type.
+void batch_fill_jumps(BatchParams& p, int step, int conv, const uint32_t d[3]) {
   const uint64_t stride = (step == ST_MONT) ? 33ull : 31ull;
-  p.jump = host_pow2((53ull * stride * depth) % kP);
+  p.jump = host_pow2((53ull * stride * d[DT_F64]) % kP);
   p.jump_q = host_mulmod_quotient(p.jump);
-  p.jump_a = host_pow2((53ull * chain_jump_a(false, depth)) % kP);
-  p.jump_aq = host_mulmod_quotient(p.jump_a);
-  p.jump_b = host_pow2((53ull * chain_jump_b(false, depth)) % kP);
-  p.jump_bq = host_mulmod_quotient(p.jump_b);
-  p.back_a = host_pow2((53ull * chain_jump_a(true, depth)) % kP);
-  p.back_aq = host_mulmod_quotient(p.back_a);
-  p.back_b = host_pow2((53ull * chain_jump_b(true, depth)) % kP);
-  p.back_bq = host_mulmod_quotient(p.back_b);
+  for (int dt = 0; dt < 3; ++dt) {
+    const bool back = dt == DT_F32 && step == ST_SHARED && conv == CV_INT;
+    p.ja[dt] = host_pow2((53ull * chain_jump_a(back, d[dt])) % kP);
+    p.jaq[dt] = host_mulmod_quotient(p.ja[dt]);
+    p.jb[dt] = host_pow2((53ull * chain_jump_b(back, d[dt])) % kP);
+    p.jbq[dt] = host_mulmod_quotient(p.jb[dt]);
+    p.depth[dt] = d[dt];
+  }
+  p.warp_bytes = batch_warp_bytes(d);
 }
 
 static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
-  const void* fn = batch_kernel_fn((int)b->tune.step, (int)b->tune.conv, (int)b->tune.chains,
-                                   b->tune.depth);
+  uint32_t dd[3];
+  batch_depths(b->tune, dd);
+  const void* fn = batch_kernel_fn((int)b->tune.step, (int)b->tune.conv, (int)b->tune.chains, dd);
   if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
   unsigned char* base = static_cast<unsigned char*>(b->dev);
   BatchParams p;
@@ -62,15 +66,14 @@ static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
   p.counter = reinterpret_cast<unsigned long long*>(base + sizeof(BatchDesc) * b->nstreams +
                                                     sizeof(uint64_t) * (b->nstreams + 1));
   p.total_units = b->total_units;
-  batch_fill_jumps(p, (int)b->tune.step, b->tune.depth);
+  batch_fill_jumps(p, (int)b->tune.step, (int)b->tune.conv, dd);
   p.nstreams = b->nstreams;
-  p.depth = b->tune.depth;
   p.unit_tiles = b->tune.unit;
   p.skip = b->tune.skip;
   p.nbuf = b->tune.buffers;
   cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), cs);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(batch counter)");
-  const size_t smem = batch_smem_bytes(b->tune.block, b->tune.depth, b->tune.buffers);
+  const size_t smem = batch_smem_bytes(b->tune.block, dd, b->tune.buffers);
   void* args[] = {&p};
   e = cudaLaunchKernel(fn, dim3(b->tune.grid), dim3(b->tune.block), args, smem, cs);
   if (e != cudaSuccess) return cuda_error(e, "batch kernel launch");
@@ -99,21 +102,22 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   if (!t.conv) t.conv = d.conv ? d.conv : (uint32_t)CV_INT;
   if (!t.skip) t.skip = SK_TABLE;
   // zero fields: the plan shape the autotuner picks on GB300 for the batched
-  // workload (4096 streams of 10^3..10^7 variates)
-  if (!t.depth) t.depth = 31;
+  // workload (4096 streams of 10^3..10^7 variates); depth 0 stays for the
+  // built-in per-type depths where the kernel has them
   if (!t.block) t.block = 896;
   if (!t.unit) t.unit = 64;  // tiles per work unit
   if (!t.buffers) t.buffers = 1;
   t.buffers = batch_buffers(t);
   t.layout = RNG_LAYOUT_TILED;
   t.chains = batch_chains(t);
+  if (!t.depth && !batch_builtin_depths_ok(t)) t.depth = 31;
   if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
     return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
   if (t.conv != CV_INT && t.conv != CV_FP64)
     return set_error(RNG_EINVAL, "tune.conv %u is not a conversion", t.conv);
   if (t.skip != SK_TABLE && t.skip != SK_SQMUL)
     return set_error(RNG_EINVAL, "tune.skip %u is not a skip-ahead method", t.skip);
-  if (t.depth % 2 == 0 || t.depth > kMaxDepth)
+  if ((t.depth && t.depth % 2 == 0) || t.depth > kMaxDepth)
     return set_error(RNG_EINVAL, "tune.depth %u must be odd and at most %u", t.depth, kMaxDepth);
   if (t.block % 32 != 0 || t.block == 0 || t.block > 1024)
     return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024", t.block);
@@ -122,12 +126,13 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   DeviceInfo di;
   rng_status st = device_info(&di);
   if (st != RNG_OK) return st;
-  const size_t smem = batch_smem_bytes(t.block, t.depth, t.buffers);
+  uint32_t dd[3];
+  batch_depths(t, dd);
+  const size_t smem = batch_smem_bytes(t.block, dd, t.buffers);
   if (smem > di.smem_optin)
     return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
                      smem, di.smem_optin);
-  const uint64_t unit_elems = 32ull * t.depth * t.unit;
-  const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, t.depth);
+  const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, dd);
   if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
   cudaError_t e =
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin);
@@ -167,6 +172,7 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
     D.unit0 = units;
     prefix[k] = units;
     uint64_t nu = 0;
+    const uint64_t unit_elems = batch_unit_elems(dd, t.unit, (int)D.dt);
     if (n > 0) nu = n > D.head ? (n - D.head + unit_elems - 1) / unit_elems : 1;
     units += nu;
     elems += n;
@@ -180,7 +186,6 @@ rng_status rng_batch_create(uint32_t nstreams, const uint64_t* starts, const uin
   b->total_units = units;
   b->total_elems = elems;
   b->total_bytes = bytes;
-  b->unit_elems = (uint32_t)unit_elems;
   b->graph = nullptr;
   b->exec = nullptr;
   b->device = di.device;
@@ -331,19 +336,19 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   if (!t.conv) t.conv = d.conv ? d.conv : (uint32_t)CV_INT;
   if (!t.skip) t.skip = SK_TABLE;
   // zero fields: the same shape as a batch plan's
-  if (!t.depth) t.depth = 31;
   if (!t.block) t.block = 896;
   if (!t.unit) t.unit = 64;
   if (!t.buffers) t.buffers = 1;
   t.buffers = batch_buffers(t);
   t.chains = batch_chains(t);
+  if (!t.depth && !batch_builtin_depths_ok(t)) t.depth = 31;
   if (t.step != ST_SHARED && t.step != ST_BARRETT && t.step != ST_MONT)
     return set_error(RNG_EINVAL, "tune.step %u is not a step variant", t.step);
   if (t.conv != CV_INT && t.conv != CV_FP64)
     return set_error(RNG_EINVAL, "tune.conv %u is not a conversion", t.conv);
   if (t.skip != SK_TABLE && t.skip != SK_SQMUL)
     return set_error(RNG_EINVAL, "tune.skip %u is not a skip-ahead method", t.skip);
-  if (t.depth % 2 == 0 || t.depth > kMaxDepth)
+  if ((t.depth && t.depth % 2 == 0) || t.depth > kMaxDepth)
     return set_error(RNG_EINVAL, "tune.depth %u must be odd and at most %u", t.depth, kMaxDepth);
   if (t.block % 32 != 0 || t.block == 0 || t.block > 1024)
     return set_error(RNG_EINVAL, "tune.block %u must be a multiple of 32, <= 1024", t.block);
@@ -354,12 +359,13 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   if (st != RNG_OK) return st;
   if (di.device < 0 || di.device >= kNoallocMaxDevices)
     return set_error(RNG_EINVAL, "device %d beyond the no-allocation device table", di.device);
-  const size_t smem = batch_smem_bytes(t.block, t.depth, t.buffers);
+  uint32_t dd[3];
+  batch_depths(t, dd);
+  const size_t smem = batch_smem_bytes(t.block, dd, t.buffers);
   if (smem > di.smem_optin)
     return set_error(RNG_EINVAL, "tile buffers need %zu bytes of shared memory, %zu available",
                      smem, di.smem_optin);
-  const uint64_t unit_elems = 32ull * t.depth * t.unit;
-  const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, t.depth);
+  const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, dd);
   if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
   cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
 
@@ -416,6 +422,7 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
     D.head = n ? (uint32_t)head_elems(outs[s], esz, n) : 0;
     D.unit0 = units;
     g_noalloc_prefix[k] = units;
+    const uint64_t unit_elems = batch_unit_elems(dd, t.unit, (int)D.dt);
     if (n > 0) units += n > D.head ? (n - D.head + unit_elems - 1) / unit_elems : 1;
   }
   g_noalloc_prefix[nstreams] = units;
@@ -443,9 +450,8 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   p.prefix = reinterpret_cast<const uint64_t*>(base + kNoallocDescBytes);
   p.counter = counter;
   p.total_units = units;
-  batch_fill_jumps(p, (int)t.step, t.depth);
+  batch_fill_jumps(p, (int)t.step, (int)t.conv, dd);
   p.nstreams = nstreams;
-  p.depth = t.depth;
   p.unit_tiles = t.unit;
   p.skip = t.skip;
   p.nbuf = t.buffers;

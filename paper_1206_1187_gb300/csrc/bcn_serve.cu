@@ -324,7 +324,8 @@ static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out, uint32_t* sha
     if (total >= s->heavy_elems) shape = 1;
   }
   const rng_tune& tn = s->shape[shape].tune;
-  const uint64_t unit_elems = 32ull * tn.depth * tn.unit;
+  uint32_t dd[3];
+  batch_depths(tn, dd);
   uint32_t items = 0;
   uint64_t units = 0;
   std::vector<uint64_t> still;
@@ -347,6 +348,7 @@ static uint32_t pack(bcn_server* s, Slot& sl, uint64_t* units_out, uint32_t* sha
     D.head = (uint32_t)head_elems(D.out, esz, chunk);
     D.unit0 = units;
     sl.h_prefix[items] = units;
+    const uint64_t unit_elems = batch_unit_elems(dd, tn.unit, (int)D.dt);
     units += chunk > D.head ? (chunk - D.head + unit_elems - 1) / unit_elems : 1;
     r.scheduled += chunk;
     ++items;
@@ -402,9 +404,10 @@ static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units,
   p.prefix = reinterpret_cast<const uint64_t*>(sl.d_table + desc_bytes);
   p.counter = counter;
   p.total_units = units;
-  batch_fill_jumps(p, (int)sh.tune.step, sh.tune.depth);
+  uint32_t sd[3];
+  batch_depths(sh.tune, sd);
+  batch_fill_jumps(p, (int)sh.tune.step, (int)sh.tune.conv, sd);
   p.nstreams = items;
-  p.depth = sh.tune.depth;
   p.unit_tiles = sh.tune.unit;
   p.skip = sh.tune.skip;
   p.nbuf = sh.tune.buffers;
@@ -537,9 +540,11 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
     if (t.depth % 2 == 0 || t.depth > kMaxDepth || t.block % 32 || !t.block || t.block > 1024 ||
         t.buffers > 2)
       return set_error(RNG_EINVAL, "bad server tuning");
-    const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, t.depth);
+    uint32_t td[3];
+    batch_depths(t, td);
+    const void* fn = batch_kernel_fn((int)t.step, (int)t.conv, (int)t.chains, td);
     if (!fn) return set_error(RNG_EINVAL, "no batch kernel for this step/conversion");
-    const size_t smem = batch_smem_bytes(t.block, t.depth, t.buffers);
+    const size_t smem = batch_smem_bytes(t.block, td, t.buffers);
     if (smem > di.smem_optin) return set_error(RNG_EINVAL, "tile buffers exceed shared memory");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)di.smem_optin);
@@ -614,8 +619,9 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
     p.total_units = 0;
     for (uint32_t k = 0; k < nshapes && e == cudaSuccess; ++k) {
       const ServeShape& sh = s->shape[k];
-      batch_fill_jumps(p, (int)sh.tune.step, sh.tune.depth);
-      p.depth = sh.tune.depth;
+      uint32_t sd[3];
+      batch_depths(sh.tune, sd);
+      batch_fill_jumps(p, (int)sh.tune.step, (int)sh.tune.conv, sd);
       p.unit_tiles = sh.tune.unit;
       p.skip = sh.tune.skip;
       p.nbuf = sh.tune.buffers;
