@@ -222,6 +222,24 @@ __device__ __forceinline__ void acc_wide(uint64_t& q, uint32_t s) {
   asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(q) : "r"(s));
 }
 
+// Lane jumps of the warp's shared redo: lane l starts 2 l pairs (4 l steps)
+// after the first state of the run being redone, at z 2^(53 * 4 l) mod m (Eq. 3
+// applied 4 l times), with the precomputed quotient of each multiplier.
+struct RedoJump {
+  uint64_t j[32], q[32];
+};
+constexpr RedoJump make_redo_jump() {
+  RedoJump t{};
+  for (uint64_t l = 0; l < 32; ++l) {
+    t.j[l] = host_pow2((53ull * 4ull * l) % kP);
+    t.q[l] = host_mulmod_quotient(t.j[l]);
+  }
+  return t;
+}
+static __device__ const RedoJump kRedoJump = make_redo_jump();
+static_assert(make_redo_jump().j[0] == 1 && make_redo_jump().j[1] == host_pow2(212),
+              "redo jumps");
+
 // Round (w2:w1:w0) * 2^-scale to the nearest double, ties to even.
 __device__ double round_words(uint64_t w0, uint64_t w1, uint64_t w2, int scale) {
   int top;
@@ -272,7 +290,8 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
   // exact path: hit iff RN(x^2) + RN(y^2) <= 1 + 2^-53, i.e. on the 2^-93
   // grid (exact high parts, ceilings of the rare small squares) <= 2^93 + 2^40
   const uint64_t lim0 = 1ull << 40, lim1 = 1ull << 29;
-  if (j0 < j1) {
+  {  // every lane of the warp runs this block (the chunk loop votes), also one
+     // with no pairs (j0 = j1, a block shorter than 64 variates)
     // the kept chunks step a chain scaled by 2^10 (see shared_step_f64_ptx),
     // the exact pairs the plain state
     uint64_t z = seed_state(exponent_add(p.ebase, first + 1), p.skip);
@@ -298,15 +317,21 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
       }
     };
     // Chunks of kChunk pairs with the branch-free conversion and per-chunk
-    // partial sums.  A chunk that met a variate below 2^-16 (a quotient
-    // window below 2^37, qmin < 32: about one chunk in 2^9) drops its
-    // partials and misses, restores its starting state and is redone
-    // exactly; a kept chunk folds its partials into the block's sums:
+    // partial sums.  A kept chunk folds its partials into the block's sums:
     // v-sum += P1 2^32 + P2 2^64, and on the 2^-93 grid the squares'
-    // h += (Q0 + Q1 2^32 + Q2 2^64) 2^9.
+    // h += (Q0 + Q1 2^32 + Q2 2^64) 2^9.  A chunk that met a variate below
+    // 2^-16 (a quotient window below 2^37, qmin < 32: about one chunk in 2^9)
+    // drops its partials and misses (its state advance is exact either way),
+    // and the whole warp redoes it exactly: lane l takes pairs 2l and 2l + 1
+    // of the chunk from one jump of the chunk's first state, adding them to
+    // its own sums (the warp's totals are the same whoever adds them).  One
+    // lane alone redoing 64 pairs left the other 31 idle: 473 against 523 G
+    // variates/s.  The chunk loop runs the chunks every lane has, so that the
+    // vote sees the whole warp; the lanes' pair counts differ by at most one.
     constexpr uint32_t kChunk = 64;
-    uint64_t j = j0;
-    for (; j + kChunk <= j1; j += kChunk) {
+    static_assert(kChunk == 2 * 32, "the redo gives each lane two pairs");
+    const uint32_t nch = __reduce_min_sync(0xffffffffu, (uint32_t)((j1 - j0) / kChunk));
+    for (uint32_t ch = 0; ch < nch; ++ch) {
       const uint64_t zs = Z;
       const uint32_t smiss = miss;
       uint64_t P1 = 0, P2 = 0, Q0 = 0, Q1 = 0;
@@ -332,11 +357,9 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
         acc_wide(Q1, s1);
         Q2 += s2;
       }
-      if (__builtin_expect(qmin < 32, 0)) {
-        z = zs >> kZShift;
+      const bool redo_mine = qmin < 32;
+      if (__builtin_expect(redo_mine, 0)) {
         miss = smiss;
-        for (uint32_t k = 0; k < kChunk; ++k) exact_pair();
-        Z = z << kZShift;
       } else {
         kept += kChunk;
         add192(a0, a1, a2, P1 << 32, P1 >> 32);
@@ -345,9 +368,18 @@ __global__ void __launch_bounds__(256, 4) mc_kernel(const McParams p) {
         add128(h0, h1, Q1 << 41, Q1 >> 23);
         h1 += (uint64_t)Q2 << 9;
       }
+      uint32_t redo = __ballot_sync(0xffffffffu, redo_mine);
+      while (__builtin_expect(redo != 0, 0)) {
+        const int L = __ffs(redo) - 1;
+        redo &= redo - 1;
+        const uint64_t zr = __shfl_sync(0xffffffffu, zs, L) >> kZShift;
+        z = mulmod_pre(zr, kRedoJump.j[lane], kRedoJump.q[lane]);
+        exact_pair();
+        exact_pair();
+      }
     }
     z = Z >> kZShift;
-    for (; j < j1; ++j) exact_pair();
+    for (uint64_t j = j0 + (uint64_t)kChunk * nch; j < j1; ++j) exact_pair();
     hits += kept - miss;  // the kept chunks counted their misses
   }
   // exact warp reduction (integer addition is order-free)

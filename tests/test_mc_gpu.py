@@ -29,7 +29,7 @@ def _run(R, a, nblocks, length, block0=0, tune=None):
 
 
 @pytest.mark.parametrize("conv", ["int", "fp64"])
-@pytest.mark.parametrize("length", [2, 4, 62, 64, 66, 1000, 4096])
+@pytest.mark.parametrize("length", [2, 4, 62, 64, 66, 1000, 4076, 4096, 4176, 8194])
 def test_small_blocks_match_the_oracle(R, oracle_mod, length, conv):
     a = M + 100
     nblocks = 37
@@ -57,14 +57,20 @@ def test_block_offset_and_launch_shape(R, oracle_mod):
 
 
 def test_blocks_holding_tiny_variates(R, oracle_mod):
-    """Blocks that contain variates below 2^-21 (which leave the branch-free
-    conversion and force the exact redo of their chunk) still match."""
+    """Blocks that contain variates below 2^-16 (which leave the branch-free
+    conversion and make the warp redo their chunk exactly) still match; among
+    them blocks where two lanes redo the same chunk.  Blocks of 4096 variates
+    give each lane one chunk of 64 pairs (128 variates)."""
     a, length = M + 100, 4096
     states = oracle_mod.generate(a, 0, 1 << 24, "u64")
-    tiny = np.nonzero(states < np.uint64(M >> 21))[0]
-    blocks = sorted({int(i) // length for i in tiny})
-    assert len(blocks) >= 3
-    for b in blocks[:5]:
+    tiny = np.nonzero(states < np.uint64(M >> 16))[0]
+    lanes = {}
+    for i in tiny:
+        lanes.setdefault(int(i) // length, set()).add(int(i) % length // 128)
+    blocks = sorted(lanes)
+    multi = [b for b in blocks if len(lanes[b]) >= 2]
+    assert len(blocks) >= 100 and len(multi) >= 2
+    for b in blocks[:4] + multi[:3]:
         oh, o1, o2 = oracle_mod.mc(a, length, np.arange(b - 1, b + 2))
         for conv in ("int", "fp64"):
             total, hits, s1, s2 = _run(R, a, 3, length, block0=b - 1, tune=R.make_tune(conv=conv))
