@@ -333,6 +333,25 @@ __device__ __forceinline__ void shared_run_fast2(uint64_t* mine, uint32_t c, uin
 // whole groups of four (for c = 44: 24 and 20 elements).  A lane whose run
 // needs the exact path (see back_step_f32_ptx) redoes it forward from
 // element 0.
+// Element jumps of the warp's shared FP32 redo: element i of a run is
+// z_0 2^(53 i) mod m (Eq. 3 applied i times), with each multiplier's
+// precomputed quotient, for i up to the largest tile depth.
+struct ElemJump {
+  uint64_t j[kMaxDepth + 1], q[kMaxDepth + 1];
+};
+constexpr ElemJump make_elem_jump() {
+  ElemJump t{};
+  for (uint64_t i = 0; i <= kMaxDepth; ++i) {
+    t.j[i] = host_pow2((53ull * i) % kP);
+    t.q[i] = host_mulmod_quotient(t.j[i]);
+  }
+  return t;
+}
+static __device__ const ElemJump kElemJump = make_elem_jump();
+static_assert(make_elem_jump().j[0] == 1 && make_elem_jump().j[1] == host_pow2(53) &&
+                  make_elem_jump().j[kMaxDepth] == host_pow2(53ull * kMaxDepth),
+              "element jumps");
+
 template <int CDEPTH>
 __device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_t& ya,
                                              uint64_t& yb) {
@@ -364,11 +383,26 @@ __device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_
     }
     for (uint32_t i = nb; i < s; ++i) mine[s - 1 - i] = back_step_f32_ptx(ya, qmin);
   }
-  if (__any_sync(0xffffffffu, qmin == 0)) {
-    if (qmin == 0) {
-      const uint32_t cc = CDEPTH > 0 ? (uint32_t)CDEPTH : c;
-      uint64_t z = ya + 1;  // element 0, forward
-      for (uint32_t i = 0; i < cc; ++i) mine[i] = f32_bits_from_f64_bits(shared_step_f64(z));
+  // A flagged run is redone exactly by the whole warp: for each flagged lane,
+  // lane l makes elements l, l + 32, ... of that lane's run, each from one
+  // jump of the run's element 0 (the backward chain a ends there), with the
+  // forward step and the exact conversion.  Made by its own lane alone, the
+  // redo held the other 31 lanes for a whole run.
+  uint32_t redo = __ballot_sync(0xffffffffu, qmin == 0);
+  if (__builtin_expect(redo != 0, 0)) {
+    const uint32_t cc = CDEPTH > 0 ? (uint32_t)CDEPTH : c;
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t* const wbuf = mine - lane * cc;  // the warp's tile
+    const uint64_t z0 = ya + 1;               // element 0 of this lane's run
+    __syncwarp();  // every lane's run is in shared memory before others overwrite it
+    while (redo != 0) {
+      const int L = __ffs(redo) - 1;
+      redo &= redo - 1;
+      const uint64_t zl = __shfl_sync(0xffffffffu, z0, L);
+      for (uint32_t i = lane; i < cc; i += 32) {
+        uint64_t z = mulmod_pre(zl, __ldg(&kElemJump.j[i]), __ldg(&kElemJump.q[i]));
+        wbuf[L * cc + i] = f32_bits_from_f64_bits(shared_step_f64(z));
+      }
     }
     __syncwarp();
   }
