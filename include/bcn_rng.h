@@ -262,7 +262,8 @@ rng_status rng_batch_destroy(bcn_batch *b);
  *   - The first call on a device, with that device current, looks up the
  *     array's device address, and the first call with each kernel shape
  *     (step, conversion, chains, depth) sets that kernel's shared-memory
- *     limit.
+ *     limit.  Make that first call on each device before any stream capture
+ *     begins.
  *   - Every call rewrites the one shared table and clears its work counter:
  *     calls whose work overlaps on the GPU (on different streams, or from
  *     different host threads' streams) race and must be serialised by the
