@@ -51,6 +51,10 @@ def bulk_candidates(dtype: str) -> list[dict]:
             for block in blocks:
                 cands.append(dict(step="shared", conv="int", layout="tiled", depth=depth,
                                   block=block, chains=2, buffers=1))
+        if dtype == "f32":  # one chain: each 44-deep run from one product
+            for block in (768, 896, 1024):
+                cands.append(dict(step="shared", conv="int", layout="tiled", depth=44,
+                                  block=block, chains=1, buffers=1))
     return cands
 
 

@@ -17,6 +17,7 @@
 // This follows the paper's parallel split (Sec. 1): every unit is a block of
 // a stream reached by skip-ahead, so no result depends on which warp runs it.
 #include "bcn_batch.cuh"
+#include "bcn_digits.cuh"
 #include "bcn_gen.cuh"
 
 namespace bcn {
@@ -41,7 +42,12 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& d, uint64_t k, const
   const uint64_t ntiles = (s1 - s0) / tile_elems;
   if (ntiles > 0) {
     const uint64_t first = s0 + (uint64_t)lane * c;
-    if constexpr (ILP == 2) {
+    if constexpr (ILP == 2 && kDigitsF32<DT, STEP, CONV, CDEPTH>) {
+      // each FP32 run from one product, from the state one past it
+      warp_tiles_digits<CDEPTH>(out, s0, ntiles, p.ja[DT], p.jaq[DT],
+                                state_of(d.ebase, first + c, p.skip),
+                                reinterpret_cast<W*>(buf0_bytes), issued, lane, p.nbuf);
+    } else if constexpr (ILP == 2) {
       Gen<DT, STEP, CONV> a{0}, b{0};
       lane_chains2<DT, STEP, CONV>(d.ebase, first, c, p.skip, a, b);
       warp_tiles2<DT, STEP, CONV, CDEPTH>(out, s0, ntiles, c, p.ja[DT], p.jaq[DT], p.jb[DT],
@@ -95,7 +101,7 @@ static const void* pick_batch(int st, int cv, int ilp, const uint32_t d[3]) {
   const bool same = d[DT_F64] == d[DT_F32] && d[DT_F64] == d[DT_U64];
   if (st == ST_SHARED && cv == CV_INT) {  // the production path: fixed depths
     if (ilp == 2) {
-      if (d[DT_F64] == kBatchDepthF64 && d[DT_F32] == kBatchDepthF32)
+      if (batch_f32_digits(st, cv, ilp, d))
         return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, kBatchDepthF64, kBatchDepthF32>;
       if (same && d[0] == 15) return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 15, 15>;
       if (same && d[0] == 31) return (const void*)batch_kernel<ST_SHARED, CV_INT, 2, 31, 31>;

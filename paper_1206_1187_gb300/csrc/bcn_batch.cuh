@@ -22,7 +22,8 @@ struct BatchParams {
   uint64_t jump;
   uint64_t jump_q;       // floor(jump * 2^64 / m); one chain per lane
   // two chains per lane, by element type (DT_F64, DT_F32, DT_U64): the FP32
-  // entries are the backward chains' jumps when FP32 runs the backward step
+  // entries are the backward chains' jumps when FP32 runs the backward step,
+  // and ja alone the 32c-element jump when its runs come from one product
   uint64_t ja[3], jaq[3], jb[3], jbq[3];
   uint32_t depth[3];     // tile depth by element type
   uint32_t warp_bytes;   // one tile buffer of a warp, the largest type's tile
@@ -35,8 +36,8 @@ struct BatchParams {
 // The tile depths of a batch by element type.  A resolved tuning's depth of 0
 // (the default with the shared step on two chains) means the built-in depths
 // of each type's fastest runs: FP64 30 (two variates per shared-memory
-// store), FP32 44 (four, backward step), raw states 31; any other depth is the
-// same for every type.
+// store), FP32 44 (four, each run from one product), raw states 31; any other
+// depth is the same for every type.
 constexpr uint32_t kBatchDepthF64 = 30, kBatchDepthF32 = 44, kBatchDepthU64 = 31;
 inline void batch_depths(const rng_tune& t, uint32_t d[3]) {
   d[DT_F64] = t.depth ? t.depth : kBatchDepthF64;
@@ -71,8 +72,16 @@ inline bool batch_builtin_depths_ok(const rng_tune& t) {
   return t.step == ST_SHARED && t.conv == CV_INT && t.chains == 2;
 }
 
+// Whether the batched kernel for this tuning makes its FP32 runs from one
+// product each (bcn_digits.cuh): the shared step with the integer conversion
+// on two chains at the built-in depths.  Its other types keep two chains.
+inline bool batch_f32_digits(int step, int conv, int chains, const uint32_t d[3]) {
+  return step == ST_SHARED && conv == CV_INT && chains == 2 && d[DT_F64] == kBatchDepthF64 &&
+         d[DT_F32] == kBatchDepthF32;
+}
+
 // Fill the tile-jump multipliers (and their precomputed quotients) of p.
-void batch_fill_jumps(BatchParams& p, int step, int conv, const uint32_t d[3]);
+void batch_fill_jumps(BatchParams& p, int step, int conv, int chains, const uint32_t d[3]);
 // Tile buffers per warp for this tuning: tune.buffers, 0 meaning 2.
 inline uint32_t batch_buffers(const rng_tune& t) { return t.buffers ? t.buffers : 2u; }
 inline size_t batch_smem_bytes(uint32_t block, const uint32_t d[3], uint32_t nbuf) {

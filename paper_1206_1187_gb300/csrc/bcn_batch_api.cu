@@ -38,14 +38,18 @@ static void longest_first(uint32_t* order, uint32_t nstreams, const uint64_t* co
 
 // The tile-jump multipliers of every element type; with two chains, FP32
 // runs the backward step when the step is the shared one with the integer
-// conversion.  One chain per lane only occurs with one depth for every type.
-void batch_fill_jumps(BatchParams& p, int step, int conv, const uint32_t d[3]) {
+// conversion, or makes each run from one product (batch_f32_digits), whose
+// state, one past the run, moves 32c elements to the lane's next run.  One
+// chain per lane only occurs with one depth for every type.
+void batch_fill_jumps(BatchParams& p, int step, int conv, int chains, const uint32_t d[3]) {
   const uint64_t stride = (step == ST_MONT) ? 33ull : 31ull;
   p.jump = host_pow2((53ull * stride * d[DT_F64]) % kP);
   p.jump_q = host_mulmod_quotient(p.jump);
+  const bool digits = batch_f32_digits(step, conv, chains, d);
   for (int dt = 0; dt < 3; ++dt) {
     const bool back = dt == DT_F32 && step == ST_SHARED && conv == CV_INT;
-    p.ja[dt] = host_pow2((53ull * chain_jump_a(back, d[dt])) % kP);
+    p.ja[dt] = host_pow2((53ull * (dt == DT_F32 && digits ? 32ull * d[dt]
+                                                         : chain_jump_a(back, d[dt]))) % kP);
     p.jaq[dt] = host_mulmod_quotient(p.ja[dt]);
     p.jb[dt] = host_pow2((53ull * chain_jump_b(back, d[dt])) % kP);
     p.jbq[dt] = host_mulmod_quotient(p.jb[dt]);
@@ -66,7 +70,7 @@ static rng_status batch_launch_raw(bcn_batch* b, cudaStream_t cs) {
   p.counter = reinterpret_cast<unsigned long long*>(base + sizeof(BatchDesc) * b->nstreams +
                                                     sizeof(uint64_t) * (b->nstreams + 1));
   p.total_units = b->total_units;
-  batch_fill_jumps(p, (int)b->tune.step, (int)b->tune.conv, dd);
+  batch_fill_jumps(p, (int)b->tune.step, (int)b->tune.conv, (int)b->tune.chains, dd);
   p.nstreams = b->nstreams;
   p.unit_tiles = b->tune.unit;
   p.skip = b->tune.skip;
@@ -450,7 +454,7 @@ extern "C" rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64
   p.prefix = reinterpret_cast<const uint64_t*>(base + kNoallocDescBytes);
   p.counter = counter;
   p.total_units = units;
-  batch_fill_jumps(p, (int)t.step, (int)t.conv, dd);
+  batch_fill_jumps(p, (int)t.step, (int)t.conv, (int)t.chains, dd);
   p.nstreams = nstreams;
   p.unit_tiles = t.unit;
   p.skip = t.skip;

@@ -27,6 +27,7 @@
 // Every element's value depends only on its index, so the result is
 // identical for every layout, depth, block and grid.
 #include "bcn_bulk.cuh"
+#include "bcn_digits.cuh"
 #include "bcn_gen.cuh"
 
 namespace bcn {
@@ -57,6 +58,11 @@ __global__ void __launch_bounds__(1024) tiled_kernel(const TiledParams p) {
       warp_tiles2<DT, STEP, CONV, CDEPTH>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump_a,
                                           p.jump_aq, p.jump_b, p.jump_bq, a, b, buf0, issued,
                                           lane, p.nbuf);
+    } else if constexpr (kDigitsF32<DT, STEP, CONV, CDEPTH>) {
+      // each FP32 run from one product, starting from the state one past it
+      warp_tiles_digits<CDEPTH>(out, p.head + t0 * tile_elems, t1 - t0, p.jump, p.jump_q,
+                                state_of(p.ebase, first + c, p.skip), buf0, issued, lane,
+                                p.nbuf);
     } else {
       Gen<DT, STEP, CONV> g = lane_chain<DT, STEP, CONV>(p.ebase, first, c, p.skip);
       warp_tiles<DT, STEP, CONV, CDEPTH>(out, p.head + t0 * tile_elems, t1 - t0, c, p.jump,
@@ -117,6 +123,9 @@ static const void* pick_ilp(int layout, int ilp, uint32_t depth) {
   if constexpr (ST == ST_BARRETT || ST == ST_SHARED)
     if (ilp == 2) return (const void*)tiled_kernel<DT, ST, CV, 2>;
   if constexpr (ST == ST_SHARED && CV == CV_INT && DT != DT_U64) {
+    if constexpr (DT == DT_F32) {  // each run from one product (digit_run_f32)
+      if (depth == 44) return (const void*)tiled_kernel<DT, ST, CV, 1, 44>;
+    }
     if (depth == 9) return (const void*)tiled_kernel<DT, ST, CV, 1, 9>;
     if (depth == 15) return (const void*)tiled_kernel<DT, ST, CV, 1, 15>;
     if (depth == 31) return (const void*)tiled_kernel<DT, ST, CV, 1, 31>;

@@ -32,6 +32,10 @@ struct DirectParams {
   uint32_t skip;
 };
 
+// Whether one-chain FP32 runs of this depth are made from one product each
+// (bcn_digits.cuh; the depths with a compiled kernel).
+constexpr bool digit_run_depth(uint64_t c) { return c == 44; }
+
 // The kernel for a layout, output type, step variant, conversion, chains per
 // lane and tile depth (nullptr if there is none).
 const void* pick_kernel(int layout, int dt, int st, int cv, int ilp, uint32_t depth);

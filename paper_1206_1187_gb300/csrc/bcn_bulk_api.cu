@@ -139,7 +139,13 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
     return RNG_OK;
   }
   L.chains = 1;
-  const uint32_t want_chains = t.chains ? t.chains : kDefChains;
+  // FP32 with the shared step and the integer conversion in the tiled layout
+  // takes one chain by default, whose runs come from one product each, unless
+  // the call names a depth those runs do not take
+  const bool f32_one_product = dt == DT_F32 && L.step == ST_SHARED && L.conv == CV_INT &&
+                               L.layout == RNG_LAYOUT_TILED &&
+                               (!t.depth || digit_run_depth(t.depth));
+  const uint32_t want_chains = t.chains ? t.chains : f32_one_product ? 1u : kDefChains;
   if (L.layout == RNG_LAYOUT_TILED && (L.step == ST_SHARED || L.step == ST_BARRETT) &&
       want_chains == 2 && (t.depth ? t.depth : def_depth(dt, false)) >= 3)
     L.chains = 2;
@@ -147,18 +153,23 @@ rng_status resolve_bulk(uint64_t n, int dt, const rng_tune* tune, BulkLaunch* ou
   // odd or 4 mod 8), FP64 the forward step on scaled chains (odd or 2 mod 4)
   const bool two_shared = L.step == ST_SHARED && L.conv == CV_INT && L.chains == 2;
   const bool back32 = dt == DT_F32 && two_shared, scaled64 = dt == DT_F64 && two_shared;
+  // FP32 with the shared step on one chain makes each run from one product
+  // in runs of the depths digit_run_depth names
+  const bool digits32 = dt == DT_F32 && L.step == ST_SHARED && L.conv == CV_INT &&
+                        L.chains == 1 && L.layout == RNG_LAYOUT_TILED;
   const uint32_t depth0 = L.layout == RNG_LAYOUT_TILED
-                              ? (t.depth ? t.depth : def_depth(dt, back32 || scaled64))
+                              ? (t.depth ? t.depth : def_depth(dt, back32 || scaled64 || digits32))
                               : 0;
   const void* fn = pick_kernel(L.layout, dt, L.step, L.conv, (int)L.chains, depth0);
   if (!fn) return set_error(RNG_EINVAL, "no kernel for this combination");
   if (L.layout == RNG_LAYOUT_TILED) {
-    L.depth = t.depth ? t.depth : def_depth(dt, back32 || scaled64);
-    L.block = t.block ? t.block : (back32 ? kDefBlockF32 : kDefBlock);
+    L.depth = t.depth ? t.depth : def_depth(dt, back32 || scaled64 || digits32);
+    L.block = t.block ? t.block : (back32 || digits32 ? kDefBlockF32 : kDefBlock);
     // odd depths keep the one-variate shared-memory stores bank-conflict free;
     // the backward FP32 runs also take depths of 4 mod 8 (four-variate
     // stores), the forward FP64 runs on two chains 2 mod 4 (two-variate)
-    const bool even_ok = (back32 && vec4_depth(L.depth)) || (scaled64 && vec2_depth(L.depth));
+    const bool even_ok = (back32 && vec4_depth(L.depth)) || (scaled64 && vec2_depth(L.depth)) ||
+                         (digits32 && digit_run_depth(L.depth));
     if ((L.depth % 2 == 0 && !even_ok) || L.depth > kMaxDepth)
       return set_error(RNG_EINVAL,
                        "tune.depth %u must be odd (on two chains with the shared step also "
@@ -266,7 +277,11 @@ rng_status launch_bulk(const BulkLaunch& L, uint64_t seed, uint64_t i0, uint64_t
     p.head = head_elems(out, dtype_size(L.dt), n);
     p.ntiles = tile_count(n, p.head, L.depth);
     p.ebase = ebase;
-    const uint64_t stride = (L.step == ST_MONT) ? 33ull : 31ull;
+    // a forward chain moves c steps through its run, the backward Montgomery
+    // chain c steps back, the one-product FP32 run's state not at all
+    const bool digits = L.dt == DT_F32 && L.step == ST_SHARED && L.conv == CV_INT &&
+                        L.chains == 1 && digit_run_depth(L.depth);
+    const uint64_t stride = (L.step == ST_MONT) ? 33ull : digits ? 32ull : 31ull;
     p.jump = host_pow2((53ull * stride * L.depth) % kP);
     p.jump_q = host_mulmod_quotient(p.jump);
     // FP32 with the shared step on two chains runs the backward step

@@ -406,7 +406,7 @@ static void launch_slot(bcn_server* s, Slot& sl, uint32_t items, uint64_t units,
   p.total_units = units;
   uint32_t sd[3];
   batch_depths(sh.tune, sd);
-  batch_fill_jumps(p, (int)sh.tune.step, (int)sh.tune.conv, sd);
+  batch_fill_jumps(p, (int)sh.tune.step, (int)sh.tune.conv, (int)sh.tune.chains, sd);
   p.nstreams = items;
   p.unit_tiles = sh.tune.unit;
   p.skip = sh.tune.skip;
@@ -621,7 +621,7 @@ rng_status rng_server_create(const rng_server_config* cfg_in, bcn_server** out) 
       const ServeShape& sh = s->shape[k];
       uint32_t sd[3];
       batch_depths(sh.tune, sd);
-      batch_fill_jumps(p, (int)sh.tune.step, (int)sh.tune.conv, sd);
+      batch_fill_jumps(p, (int)sh.tune.step, (int)sh.tune.conv, (int)sh.tune.chains, sd);
       p.unit_tiles = sh.tune.unit;
       p.skip = sh.tune.skip;
       p.nbuf = sh.tune.buffers;

@@ -124,6 +124,12 @@ def test_two_chains_per_lane(R, oracle_mod, step):
                             chains=2)
             assert_same(R.generate_at(a, off, n, "f32", tune=t), want,
                         f"{step}/f32/{depth}/{block}/{grid}")
+        # one chain, each 44-deep run from one product
+        for block, grid in [(1024, 0), (32, 1), (96, 7), (896, 152), (64, 1000)]:
+            t = R.make_tune(step=step, layout="tiled", depth=44, block=block, grid=grid,
+                            chains=1)
+            assert_same(R.generate_at(a, off, n, "f32", tune=t), want,
+                        f"{step}/f32/44/{block}/{grid}/one chain")
 
 
 def test_windows_around_tiny_variates(R, oracle_mod):
@@ -145,6 +151,8 @@ def test_windows_around_tiny_variates(R, oracle_mod):
         for depth in (12, 44):
             t = R.make_tune(step="shared", layout="tiled", depth=depth)
             assert_same(R.generate_at(a, off, 6001, "f32", tune=t), want32, f"f32 {i} {depth}")
+        t = R.make_tune(step="shared", layout="tiled", depth=44, chains=1)
+        assert_same(R.generate_at(a, off, 6001, "f32", tune=t), want32, f"f32 {i} one product")
         for depth in (6, 30):
             t = R.make_tune(step="shared", layout="tiled", depth=depth)
             assert_same(R.generate_at(a, off, 6001, "f64", tune=t), want64, f"f64 {i} {depth}")
@@ -252,7 +260,8 @@ def test_bad_tuning_is_rejected(R):
     # even depths: on two chains with the shared step FP32 takes 4 mod 8 only,
     # FP64 2 mod 4 only, raw states none
     for dtype, kw in (("f32", {"depth": 16}), ("f32", {"depth": 6}), ("f32", {"depth": 30}),
-                      ("f32", {"depth": 12, "chains": 1}), ("f32", {"depth": 12, "step": "barrett"}),
+                      ("f32", {"depth": 12, "chains": 1}), ("f32", {"depth": 36, "chains": 1}),
+                      ("f32", {"depth": 44, "chains": 1, "conv": "fp64"}), ("f32", {"depth": 12, "step": "barrett"}),
                       ("f64", {"depth": 44}), ("f64", {"depth": 30, "chains": 1}),
                       ("f64", {"depth": 30, "step": "barrett"}), ("f64", {"depth": 30, "conv": "fp64"}),
                       ("u64", {"depth": 30}), ("u64", {"depth": 44})):
@@ -358,14 +367,15 @@ def test_full_size_fp32_and_states_sampled(R, oracle_mod):
     rnd = np.random.default_rng(28)
     idx = np.unique(np.concatenate([np.arange(4096), np.arange(n - 4096, n),
                                     rnd.integers(0, n, size=8192)])).astype(np.int64)
-    for dtype in ("f32", "u64"):
-        out = R.generate_at(a, 0, n, dtype)
+    one_product = R.make_tune(step="shared", layout="tiled", depth=44, chains=1)
+    for dtype, tune in (("f32", None), ("u64", None), ("f32", one_product)):
+        out = R.generate_at(a, 0, n, dtype, tune=tune)
         torch.cuda.synchronize()
         iv = torch.int32 if dtype == "f32" else torch.int64
         got = out.view(iv)[torch.from_numpy(idx).cuda()]  # index the integer view
         want = oracle_mod.at(a, idx.astype(np.uint64), dtype)
         assert np.array_equal(got.cpu().numpy(),
-                              want.view(np.int32 if dtype == "f32" else np.int64)), dtype
+                              want.view(np.int32 if dtype == "f32" else np.int64)), (dtype, tune)
         del out, got
 
 
@@ -472,7 +482,7 @@ def test_fp32_near_float_boundaries(R, oracle_mod):
     assert len(targets) >= 12
     shapes = [dict(), dict(depth=31), dict(depth=47, block=768), dict(depth=45, chains=2),
               dict(depth=63, chains=1), dict(depth=5, block=128), dict(depth=44, block=1024),
-              dict(depth=12, block=96)]
+              dict(depth=12, block=96), dict(depth=44, chains=1), dict(depth=44, chains=1, block=64)]
     for z in targets:
         e = dlog2(z * h_inv % M, 33)
         i = ((e - (a - M)) * pow(53, -1, P) - 1) % P

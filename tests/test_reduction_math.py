@@ -543,3 +543,126 @@ def test_backward_f32_from_the_quotient_is_the_truncated_double():
         zp = -(-(qv * M) // 2 ** 53)
         if 0 < zp < M and (zp << 53) // M == qv:
             assert back_step_f32_model(((zp << 53) % M) - 1)[3] == 0
+
+
+# ---------------------------------------------- FP32 runs from one product
+def neg_minv_words_model(W):
+    """-m^-1 mod 2^(32 W) word by word, as the device header builds it."""
+    inv = pow(M, -1, 2 ** 32)
+    A, words = 1, []
+    for _ in range(W):
+        n = (-A * inv) % 2 ** 32
+        A += M * n
+        assert A % 2 ** 32 == 0 and A < 2 ** 86
+        words.append(n)
+        A >>= 32
+    return words
+
+
+def f32_from_words_model(u1, u0):
+    """The conversion of X = (u1:u0) = Q 2^11 to FP32 bits and the flag (0:
+    the exact path is needed), as back_step_f32_model forms them."""
+    c = clz32(u1) if u1 else MASK32
+    mant = (((((u1 << 32) | u0) << c) >> 32) & MASK32) >> 8 if c < 32 else u0 >> 8
+    e = (c * 0xFF800000 + 0x3E800000) & MASK32
+    v = ((~(u0 | 0xFFF) & MASK32) << c) & MASK32 if c < 32 else 0
+    return (mant + e) & MASK32, v
+
+
+def digit_run_model(z, C):
+    """One lane's run of C FP32 variates from the state one past it, on 32-bit
+    words as the device code forms it: the words of z N mod 2^(32 W), each from
+    four 32-bit products and the running carry V, then digit i (element
+    C - 1 - i) read as X = (u1:u0) from bits [53i - 11, 53i + 53).  Returns
+    the words, the FP32 bits of elements 0 .. C-1 and their flags."""
+    W = (53 * C + 31) // 32
+    N = neg_minv_words_model(W)
+    z0, z1 = z & MASK32, z >> 32
+    assert z1 < 2 ** 21
+    r, V = [], 0
+    for i in range(W):
+        x = V + (z1 * N[i - 1] if i > 0 else 0)
+        assert x < 2 ** 54
+        s = x + z0 * N[i]
+        assert s < 2 ** 65
+        r.append(s & MASK32)
+        V = s >> 32
+        assert V < 2 ** 33
+
+    def bits32(pos):
+        if pos < 0:
+            return (r[0] << -pos) & MASK32
+        k, o = pos // 32, pos % 32
+        return r[k] if o == 0 else funnel_r(r[k], r[k + 1], o)
+
+    bits, flags = [0] * C, [0] * C
+    for i in range(C):
+        bits[C - 1 - i], flags[C - 1 - i] = f32_from_words_model(bits32(53 * i + 21),
+                                                                 bits32(53 * i - 11))
+    return r, bits, flags
+
+
+def test_run_constant_is_minus_the_inverse_of_m():
+    for W in (2, 9, 73, 90):
+        N = sum(w << (32 * i) for i, w in enumerate(neg_minv_words_model(W)))
+        assert (N * M + 1) % 2 ** (32 * W) == 0
+        assert N == (-pow(M, -1, 2 ** (32 * W))) % 2 ** (32 * W)
+    assert sum(w << (32 * i) for i, w in enumerate(neg_minv_words_model(2))) % 2 ** 53 == MP
+
+
+@pytest.mark.parametrize("C", [44, 4, 12, 252])
+def test_run_product_fields_are_the_runs_quotients(C):
+    """Field i of z N mod 2^(53 C) is floor(2^53 s / m) of the state s that
+    lies i + 1 steps before z (the 2-adic digits of -z/m); the word-level
+    product equals the big-integer one; every digit's top word is distinct."""
+    W = (53 * C + 31) // 32
+    N = (-pow(M, -1, 2 ** (53 * C))) % 2 ** (53 * C)
+    inv53 = pow(2, -53, M)
+    tops = [(53 * i + 52) // 32 for i in range(C)]
+    assert len(set(tops)) == C and max(tops) == W - 1
+    for z in states(300 if C < 100 else 40, seed=51 + C):
+        r, _, _ = digit_run_model(z, C)
+        P = sum(w << (32 * i) for i, w in enumerate(r))
+        assert P == z * (-pow(M, -1, 2 ** (32 * W))) % 2 ** (32 * W)
+        assert P % 2 ** (53 * C) == (z * N) % 2 ** (53 * C)
+        s = z
+        for i in range(C):
+            s = s * inv53 % M                  # one step back
+            assert (P >> (53 * i)) % 2 ** 53 == (s << 53) // M, (z, i)
+        # the run's element 0 (the redo's start) is z 2^(-53C): C steps forward give z
+        assert s == z * pow(2, -53 * C, M) % M and s * pow(2, 53 * C, M) % M == z
+
+
+def test_run_conversion_is_the_backward_steps_conversion():
+    """Every digit of a run gets the float and the flag that the backward step
+    gives the same state (the low 11 bits of u0 hold the next digit's bits
+    instead of zeros, and neither reads them), so unflagged digits are RZ of
+    the FP64 variate.  Adversarial states with quotient tails of all ones are
+    placed inside runs."""
+    C = 44
+    rnd = random.Random(57)
+    inv53 = pow(2, -53, M)
+    zs = states(2000, seed=58)
+    for tail in (9, 12, 20, 28, 29):
+        for k in (1, 2, 3):
+            for _ in range(30):
+                head = rnd.randrange(1 << 23, 1 << 24)
+                qv = (head << tail) | ((1 << tail) - k)
+                zp = -(-(qv * M) // 2 ** 53)
+                if 0 < zp < M and (zp << 53) // M == qv:
+                    pos = rnd.randrange(C)       # element pos of a run holds zp
+                    zs.append(zp * pow(2, 53 * (C - pos), M) % M)
+                    break
+    flagged = 0
+    for z in zs:
+        _, bits, flags = digit_run_model(z, C)
+        s = z
+        for e in range(C - 1, -1, -1):           # element e holds state s_e
+            _, q, sbits, v = back_step_f32_model(s - 1)
+            s = s * inv53 % M
+            assert (flags[e] == 0) == (v == 0), (z, e)
+            if v:
+                assert bits[e] == sbits == rz_f32_bits(s), (z, e)
+            else:
+                flagged += 1
+    assert flagged >= 10  # the k <= 2 tails and tail 9 must flag (11 placed)
