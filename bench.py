@@ -505,21 +505,27 @@ def measure_other_outputs(rng, stream, peaks, steps: int):
 
 def measure_m40(rng, stream, peaks, steps: int):
     """The larger-modulus variant (3^40, Sec. 1): 2^28 FP64 variates (2 GiB,
-    larger than L2) from a = 3^40+12345 into device memory, default tuning."""
+    larger than L2) from a = 3^40+12345 into device memory, default tuning;
+    beside it the same stream as 2^28 FP32 variates (1 GiB)."""
     import torch
     n, a = 1 << 28, 3 ** 40 + 12345
-    out = torch.empty(n, dtype=torch.float64, device="cuda")
-    for _ in range(3):
-        rng.generate40_at(a, 0, n, "f64", out=out, stream=stream)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        rng.generate40_at(a, 0, n, "f64", out=out, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+
+    def timed(dtype, tdt):
+        out = torch.empty(n, dtype=tdt, device="cuda")
+        for _ in range(3):
+            rng.generate40_at(a, 0, n, dtype, out=out, stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            rng.generate40_at(a, 0, n, dtype, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        del out
+        return e0.elapsed_time(e1) / steps
+
+    ms = timed("f64", torch.float64)
     gbs = 8.0 * n / (ms / 1e3) / 1e9
     out_d = {"workload": "modulus 3^40, 2^28 FP64 variates (2 GiB) from a = 3^40+12345, "
                          "truncated variates, into device memory",
@@ -531,7 +537,17 @@ def measure_m40(rng, stream, peaks, steps: int):
     out_d["roofline"] = hbm_roofline(8.0 * n, ms, out_d["traffic"], peaks)
     out_d["roofline_alu"] = issue_roofline(profiled_value("inst_per_variate", "m40_2e25", "m40"),
                                            n / (ms / 1e3), "inst_per_variate[m40_2e25]")
-    del out
+    ms32 = timed("f32", torch.float32)
+    gbs32 = 4.0 * n / (ms32 / 1e3) / 1e9
+    out_d["f32"] = {"variates_per_s": n / (ms32 / 1e3), "GBps": gbs32,
+                    "frac_of_hbm": gbs32 / peaks["hbm_gbs"], "ms_per_launch": ms32,
+                    "launches": steps, "tune": rng.resolve_tune40(n, "f32"),
+                    "roofline": hbm_roofline(
+                        4.0 * n, ms32,
+                        profiled_value("traffic_bytes_per_launch", "m40_f32_2e28", "m40"), peaks),
+                    "roofline_alu": issue_roofline(
+                        profiled_value("inst_per_variate", "m40_f32_2e25", "m40"),
+                        n / (ms32 / 1e3), "inst_per_variate[m40_f32_2e25]")}
     return out_d
 
 

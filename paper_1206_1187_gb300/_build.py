@@ -65,8 +65,8 @@ KERNEL_SOURCES = {
     "batch": ["bcn_batch.cu", "bcn_batch.cuh", "bcn_digits.cuh", "bcn_gen.cuh", "bcn_math.cuh",
               "bcn_internal.h"],
     "mc": ["bcn_mc.cu", "bcn_mc.cuh", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
-    "m40": ["bcn_m40.cu", "bcn_m40.cuh", "bcn_gen.cuh", "bcn_math.cuh", "bcn_math40.cuh",
-            "bcn_internal.h"],
+    "m40": ["bcn_m40.cu", "bcn_m40.cuh", "bcn_digits.cuh", "bcn_gen.cuh", "bcn_math.cuh",
+            "bcn_math40.cuh", "bcn_internal.h"],
 }
 
 

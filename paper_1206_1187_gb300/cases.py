@@ -5,13 +5,14 @@
     python -m paper_1206_1187_gb300.cases batch 512 [reps]   # first 512 streams of the batched workload
     python -m paper_1206_1187_gb300.cases batch 4096 [reps]  # the whole batched workload
     python -m paper_1206_1187_gb300.cases mc 16384 [reps]
-    python -m paper_1206_1187_gb300.cases m40 33554432 [reps]
+    python -m paper_1206_1187_gb300.cases m40 33554432 [reps]      # 3^40, FP64
+    python -m paper_1206_1187_gb300.cases m40f32 33554432 [reps]   # 3^40, FP32
 
 Each case runs `reps` launches (default 3) of one of the library's kernels on
 synthetic inputs and exits 0; nothing is checked here (the test suite does
 that).  Each uses the launch shape the benchmark uses for that form: the
 autotuned one for FP64 (cached per GPU model), the built-in default for FP32,
-batch plans, 3^40 and the fused consumer.
+batch plans, 3^40 (both output types) and the fused consumer.
 """
 from __future__ import annotations
 
@@ -43,10 +44,11 @@ def main(argv):
         b = rng.Batch(starts, counts, dtypes, outs=outs)
         for _ in range(reps):
             b.launch()
-    elif case == "m40":
-        out = torch.empty(size, dtype=torch.float64, device="cuda")
+    elif case in ("m40", "m40f32"):
+        f64 = case == "m40"
+        out = torch.empty(size, dtype=torch.float64 if f64 else torch.float32, device="cuda")
         for _ in range(reps):
-            rng.generate40_at(3 ** 40 + 12345, 0, size, "f64", out=out)
+            rng.generate40_at(3 ** 40 + 12345, 0, size, "f64" if f64 else "f32", out=out)
     elif case == "mc":
         for _ in range(reps):
             rng.consume_mc(3 ** 33 + 100, size, 1 << 16)

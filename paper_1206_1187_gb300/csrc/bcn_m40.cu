@@ -15,6 +15,7 @@
 // besides its state, the digit of the state above the variate it emits next.
 // The head and tail, and runs holding a variate below 2^-21, are made forward
 // with the exact quotient.
+#include "bcn_digits.cuh"
 #include "bcn_gen.cuh"
 #include "bcn_m40.cuh"
 #include "bcn_math40.cuh"
@@ -86,6 +87,155 @@ __device__ __forceinline__ uint64_t state_of40(uint64_t ebase, uint64_t idx) {
   return seed_state40(exponent_add40(ebase, idx + 1));
 }
 
+// ------------------------------------------- FP32 runs from one product
+// The identity behind the 3^33 kernel's one-product runs holds for 3^40 as
+// well (back40's step is the same reduction): the digits q of the C states
+// before z are the 53-bit fields of z N mod 2^(53C), N = -3^-40 mod 2^(53C),
+// field i being the digit of element C - 1 - i, and the bits below a field
+// are the next element's digit, i.e. the continuation of the expansion.
+// The FP32 variate truncates z/3^40 to 24 significant bits, so it is read
+// from a field with no rounding question at all: Q's leading 24 bits, which
+// lie inside the field whenever Q >= 2^23 (a run with a smaller digit,
+// probability about 2^-30 per variate, is redone by its lane with the exact
+// forward chain).
+template <int W>
+constexpr NegMinvWords<W> make_neg_minv_words40() {  // -3^-40 mod 2^(32 W)
+  NegMinvWords<W> t{};
+  const uint32_t inv = (uint32_t)inv_mod_2_64(k40M);  // 3^-40 mod 2^32
+  u128 A = 1;
+  for (int i = 0; i < W; ++i) {
+    const uint32_t n = 0u - (uint32_t)A * inv;
+    A += (u128)k40M * n;  // low word now zero; A < 2^97
+    t.w[i] = n;
+    A >>= 32;
+  }
+  return t;
+}
+static_assert((make_neg_minv_words40<2>().w[0] |
+               ((uint64_t)make_neg_minv_words40<2>().w[1] << 32)) == k40NegMinv,
+              "-3^-40 mod 2^64");
+template <int W>
+struct RunMinv40 {
+  static constexpr NegMinvWords<W> t = make_neg_minv_words40<W>();
+};
+
+// Word I of z N for a full 64-bit state z = (z1:z0).  V = (v1:v0), the part
+// of the lower words' sum above word I - 1, stays below 2^34 (v1 <= 3);
+// x = V + z1 N_(I-1) can pass 2^64, so it takes a third word (x2 <= 1), and
+// x + z0 N_I gives word I and the next V.  Four 32-bit multiply-adds and two
+// adds per word.
+template <int W, int I>
+__device__ __forceinline__ void run40_product_word(uint32_t z0, uint32_t z1, uint32_t& r,
+                                                   uint32_t& v0, uint32_t& v1) {
+  constexpr uint32_t nI = RunMinv40<W>::t.w[I];
+  if constexpr (I == 0) {
+    r = z0 * nI;
+    v0 = __umulhi(z0, nI);
+    v1 = 0;
+  } else if constexpr (I == W - 1) {  // the top word: no carry out
+    constexpr uint32_t nP = RunMinv40<W>::t.w[I - 1];
+    asm("{\n\t"
+        ".reg .u32 x0;\n\t"
+        "mad.lo.u32 x0, %3, %5, %1;\n\t"
+        "mad.lo.u32 %0, %2, %4, x0;\n\t"
+        "}"
+        : "=r"(r)
+        : "r"(v0), "r"(z0), "r"(z1), "n"(nI), "n"(nP));
+  } else {
+    constexpr uint32_t nP = RunMinv40<W>::t.w[I - 1];
+    // r is early-clobber: it must not share a register with z0
+    asm("{\n\t"
+        ".reg .u32 x0, x1, x2;\n\t"
+        "mad.lo.cc.u32 x0, %4, %6, %1;\n\t"   // x = V + z1 N_(I-1), three words
+        "madc.hi.cc.u32 x1, %4, %6, %2;\n\t"
+        "addc.u32 x2, 0, 0;\n\t"
+        "mad.lo.cc.u32 %0, %3, %5, x0;\n\t"   // x + z0 N_I: word I ...
+        "madc.hi.cc.u32 %1, %3, %5, x1;\n\t"  // ... and the next V
+        "addc.u32 %2, x2, 0;\n\t"
+        "}"
+        : "=&r"(r), "+r"(v0), "+r"(v1)
+        : "r"(z0), "r"(z1), "n"(nI), "n"(nP));
+  }
+}
+
+// FP32 bits of the truncated variate from X = (u1:u0), the field's digit Q
+// times 2^11 followed by the next digit's top 11 bits: with c the leading
+// zeros of u1 (Q >= 2^23: c <= 29), Q's leading 24 bits W = (X << c) >> 40
+// and the exponent 126 - c, i.e. W + (125 - c) 2^23.
+__device__ __forceinline__ uint32_t f32_from_digit_words40(uint32_t u1, uint32_t u0) {
+  uint32_t b;
+  asm("{\n\t"
+      ".reg .u32 c, mant, e;\n\t"
+      "bfind.shiftamt.u32 c, %1;\n\t"
+      "shf.l.clamp.b32 mant, %2, %1, c;\n\t"
+      "shr.b32 mant, mant, 8;\n\t"
+      "mad.lo.u32 e, c, 0xFF800000, 0x3E800000;\n\t"
+      "add.u32 %0, mant, e;\n\t"
+      "}"
+      : "=r"(b)
+      : "r"(u1), "r"(u0));
+  return b;
+}
+
+template <int C>
+struct DigitRun40 {
+  static constexpr int W = (53 * C + 31) / 32;  // words of the product
+  // the digit whose top bit lies in word I, or -1 (at most one: 53 > 32)
+  __host__ __device__ static constexpr int digit_of_word(int I) {
+    const int num = 32 * I + 31 - 52;
+    const int i = num < 0 ? 0 : num / 53;
+    return i < C && (53 * i + 52) / 32 == I ? i : -1;
+  }
+  // 2^(-53C) mod 3^40 in Montgomery form: one past the run -> element 0
+  static constexpr uint64_t back =
+      host40_mont_form(host40_pow2((k40P - (53ull * C) % k40P) % k40P));
+};
+
+template <int C, int I>
+__device__ __forceinline__ void digit_run40_word(uint32_t z0, uint32_t z1,
+                                                 uint32_t (&r)[DigitRun40<C>::W], uint32_t& v0,
+                                                 uint32_t& v1, uint32_t* mine, uint32_t& qmin) {
+  run40_product_word<DigitRun40<C>::W, I>(z0, z1, r[I], v0, v1);
+  constexpr int i = DigitRun40<C>::digit_of_word(I);
+  if constexpr (i >= 0) {
+    const uint32_t u1 = run_bits32<53 * i + 21>(r);
+    const uint32_t u0 = run_bits32<53 * i - 11>(r);  // field 0: zeros below, unread
+    qmin = min(qmin, u1);
+    mine[C - 1 - i] = f32_from_digit_words40(u1, u0);
+  }
+}
+
+template <int C, int... I>
+__device__ __forceinline__ void digit_run40_words(std::integer_sequence<int, I...>, uint64_t z,
+                                                  uint32_t* mine, uint32_t& qmin) {
+  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
+  uint32_t r[DigitRun40<C>::W];
+  uint32_t v0 = 0, v1 = 0;
+  (digit_run40_word<C, I>(z0, z1, r, v0, v1, mine, qmin), ...);
+}
+
+// One lane's FP32 run of C elements from z, the state one past it.  A run
+// with a digit below 2^23 (its u1 below 4) is redone by its lane, forward
+// from element 0's state.
+template <int C>
+__device__ __forceinline__ void digit_run40_f32(uint32_t* mine, uint64_t z) {
+  uint32_t qmin = 0xffffffffu;
+  digit_run40_words<C>(std::make_integer_sequence<int, DigitRun40<C>::W>{}, z, mine, qmin);
+  const bool rare = qmin < 4u;
+  if (__any_sync(0xffffffffu, rare)) {
+    if (rare) {
+      Chain40<DT_F32> f;
+      f.start(mont40(z, DigitRun40<C>::back));
+      for (uint32_t i = 0; i < (uint32_t)C; ++i) mine[i] = f.next();
+    }
+    __syncwarp();
+  }
+}
+
+// Whether a tile loop of this kind makes its runs that way.
+template <int DT, int ILP, int CDEPTH>
+constexpr bool kDigits40 = DT == DT_F32 && ILP == 1 && CDEPTH > 0 && digit_run40_depth(CDEPTH);
+
 template <int DT>
 __device__ void run_direct40(typename Word<DT>::type* __restrict__ out, uint64_t ebase,
                              uint64_t a, uint64_t b) {
@@ -112,7 +262,29 @@ __global__ void __launch_bounds__(1024) tiled40_kernel(const M40Params p) {
 
   const uint64_t t0 = gw * p.ntiles / nw;
   const uint64_t t1 = (gw + 1) * p.ntiles / nw;
-  if (t0 < t1) {
+  if constexpr (kDigits40<DT, ILP, CDEPTH>) {
+    if (t0 < t1) {
+      // each run from one product; z is the state one past this lane's run,
+      // and p.jump = 2^(53*32c) moves it to the lane's run in the next tile
+      uint64_t z = state_of40(p.ebase, p.head + t0 * tile_elems + (uint64_t)lane * c + c);
+      uint32_t issued = 0;
+      for (uint64_t t = t0; t < t1; ++t) {
+        W* const buf = buf0 + tile_buffer(issued, p.nbuf) * tile_elems;
+        wait_buffer_free(issued, p.nbuf, lane);
+        digit_run40_f32<CDEPTH>(buf + lane * c, z);
+        fence_proxy_async_shared();
+        __syncwarp();
+        if (lane == 0) {
+          bulk_store(out + p.head + t * tile_elems, buf, tile_bytes);
+          bulk_commit();
+        }
+        ++issued;
+        if (t + 1 < t1) z = mont40(z, p.jump);
+      }
+      if (lane == 0) bulk_wait_all();
+      __syncwarp();
+    }
+  } else if (t0 < t1) {
     // Backward chains: a single chain emits c-1 .. 0 of the lane's run; two
     // chains split it, b emitting c-1 .. h+1 and a h .. 0.  Afterwards chain
     // a holds element 0 (its state), chain b element h+1.

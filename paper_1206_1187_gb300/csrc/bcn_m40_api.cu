@@ -116,7 +116,10 @@ static rng_status launch40(const Launch40& L, uint64_t seed, uint64_t i0, uint64
     p.head = head_elems(out, dtype_size(L.dt), n);
     p.ntiles = n > p.head ? (n - p.head) / (32ull * c) : 0;
     p.ebase = ebase;
-    p.jump = jump40(33 * c + lead);          // element 0 -> element c of the next run
+    // element 0 -> element c of the next run; a one-product FP32 run's state
+    // (one past the run) moves 32c elements instead
+    const bool digits = L.dt == DT_F32 && L.chains == 1 && digit_run40_depth(c);
+    p.jump = digits ? jump40(32 * c) : jump40(33 * c + lead);
     p.jump_a = jump40(32 * c + h + 1 + lead); // element 0 -> element h+1 of the next run
     p.jump_b = jump40(33 * c - h - 1 + lead); // element h+1 -> element c of the next run
     p.depth = L.depth;

@@ -169,3 +169,29 @@ def test_undecided_quotients(R, oracle_mod):
             off = (i - lead) % P40
             for dtype in ("f64", "f32"):
                 _check(R, oracle_mod, a, off, n, dtype, tune)
+
+
+def test_fp32_runs_from_one_product_at_the_redo_threshold(R, oracle_mod):
+    """One-chain FP32 runs are read from one product; a digit below 2^23 sends
+    its run to the exact forward path.  States whose first 53-bit digit is
+    just below, at and above 2^23 and 2^24 are placed at the first, a middle
+    and the last element of a lane's run (the last element's field has zeros,
+    not the next digit, below it), with the default and every compiled depth."""
+    a = M40 + 4242
+    zs = []
+    for q in (2 ** 23 - 2, 2 ** 23 - 1, 2 ** 23, 2 ** 23 + 1, 2 ** 24 - 1, 2 ** 24, 2 ** 24 + 1):
+        z = -(-(q * M40) // 2 ** 53)        # the smallest state with this digit, if any
+        while z % 3 == 0 or (z << 53) // M40 != q:
+            z += 1
+        assert (z << 53) // M40 == q
+        zs.append(z)
+    for z in zs:
+        i = index_of_state(a, z)
+        for k, n, tune in [(30, 992 * 2, dict(depth=31, block=32, chains=1)),
+                           (0, 992 * 2, dict(depth=31, block=32, chains=1)),
+                           (31 * 5 + 17, 992 * 2, dict(depth=31, block=32, chains=1)),
+                           (14, 480 * 2, dict(depth=15, block=32, chains=1)),
+                           (31 * 40 + 30, 5000, None),
+                           (31 * 3 + 30, 992 * 2, dict(depth=31, block=32, chains=2))]:
+            off = (i - k) % P40
+            _check(R, oracle_mod, a, off, n, "f32", tune)

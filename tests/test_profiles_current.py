@@ -17,6 +17,8 @@ READ_BY_BENCH = {
     ("inst_per_variate", "f32_2e26"): "tiled",
     ("traffic_bytes_per_launch", "m40_f64_2e28"): "m40",
     ("inst_per_variate", "m40_2e25"): "m40",
+    ("traffic_bytes_per_launch", "m40_f32_2e28"): "m40",
+    ("inst_per_variate", "m40_f32_2e25"): "m40",
     ("inst_per_variate", "mc_2e36"): "mc",
     ("alu_pipe_busy_frac", "mc_2e36"): "mc",
     ("fp64_pipe_busy_frac", "mc_2e36"): "mc",

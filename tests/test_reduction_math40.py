@@ -14,6 +14,8 @@ import random
 import struct
 from fractions import Fraction
 
+import pytest
+
 from m40_math import H40, M40, P40, index_of_state
 
 U64 = 2 ** 64 - 1
@@ -271,3 +273,110 @@ def test_fast_conversion_funnel_form_matches():
                 q0 = ((1 << (20 - t)) << 32) | q0l
                 q1 = q1h << 32
                 assert bits_fast_funnel_model(q0, q1) == bits_fast_model(q0, q1), (t, q0l, q1h)
+
+
+# ---------------------------------------------- FP32 runs from one product
+MASK32 = 2 ** 32 - 1
+
+
+def neg_minv_words40_model(W):
+    """-3^-40 mod 2^(32 W) word by word, as the kernel builds it."""
+    inv = pow(M40, -1, 2 ** 32)
+    A, words = 1, []
+    for _ in range(W):
+        n = (-A * inv) % 2 ** 32
+        A += M40 * n
+        assert A % 2 ** 32 == 0 and A < 2 ** 97
+        words.append(n)
+        A >>= 32
+    return words
+
+
+def rz32_bits(s):
+    """Bits of s/3^40 truncated to a float (24 significant bits), exactly."""
+    k = 24 + M40.bit_length() - s.bit_length()
+    while (s << k) // M40 >= 2 ** 24:
+        k -= 1
+    while (s << k) // M40 < 2 ** 23:
+        k += 1
+    mant = (s << k) // M40
+    return struct.unpack("<I", struct.pack("<f", math.ldexp(mant, -k)))[0]
+
+
+def digit_run40_model(z, C):
+    """One lane's FP32 run of C variates from the state z one past it, on
+    32-bit words as the kernel forms it (three-word partial sums, V below
+    2^34), with the conversion of each field and the flag (digit below 2^23).
+    Returns the words, the FP32 bits of elements 0 .. C-1 and their flags."""
+    W = (53 * C + 31) // 32
+    N = neg_minv_words40_model(W)
+    z0, z1 = z & MASK32, z >> 32
+    r, V = [], 0
+    for i in range(W):
+        x = V + (z1 * N[i - 1] if i > 0 else 0)
+        assert x < 2 ** 65
+        s = x + z0 * N[i]
+        assert s < 2 ** 66
+        r.append(s & MASK32)
+        V = s >> 32
+        assert V < 2 ** 34
+
+    def bits32(pos):
+        if pos < 0:
+            return (r[0] << -pos) & MASK32
+        k, o = pos // 32, pos % 32
+        return r[k] if o == 0 else (((r[k + 1] << 32) | r[k]) >> o) & MASK32
+
+    bits, flags = [0] * C, [False] * C
+    for i in range(C):
+        u1, u0 = bits32(53 * i + 21), bits32(53 * i - 11)
+        c = 32 - u1.bit_length() if u1 else MASK32
+        mant = (((((u1 << 32) | u0) << c) >> 32) & MASK32) >> 8 if c < 32 else u0 >> 8
+        e = (c * 0xFF800000 + 0x3E800000) & MASK32
+        bits[C - 1 - i] = (mant + e) & MASK32
+        flags[C - 1 - i] = u1 < 4
+    return r, bits, flags
+
+
+def test_run40_constant():
+    for W in (2, 25, 52, 70):
+        N = sum(w << (32 * i) for i, w in enumerate(neg_minv_words40_model(W)))
+        assert N == (-pow(M40, -1, 2 ** (32 * W))) % 2 ** (32 * W)
+    assert sum(w << (32 * i) for i, w in enumerate(neg_minv_words40_model(2))) == NEG_MINV
+
+
+@pytest.mark.parametrize("C", [31, 15, 1])
+def test_run40_fields_are_the_digits_and_the_floats_truncate(C):
+    """Field i of z N is floor(2^53 s / 3^40) of the state i + 1 steps before
+    z; the word-level product equals the big-integer one; every unflagged
+    element's float is s/3^40 truncated to 24 bits, and exactly the elements
+    whose digit is below 2^23 are flagged.  States with digits around 2^23
+    and 2^24 are placed at every position of a run."""
+    W = (53 * C + 31) // 32
+    inv53 = pow(2, -53, M40)
+    zs = states(300, seed=70 + C)
+    rnd = random.Random(71 + C)
+    for q in (2 ** 23 - 2, 2 ** 23 - 1, 2 ** 23, 2 ** 23 + 1, 2 ** 24 - 1, 2 ** 24, 3, 1):
+        s = -(-(q * M40) // 2 ** 53)
+        while s % 3 == 0 or (s << 53) // M40 != q:
+            s += 1
+        for pos in {0, C - 1, rnd.randrange(C)}:
+            zs.append(s * pow(2, 53 * (C - pos), M40) % M40)   # element pos holds s
+    flagged = 0
+    for z in zs:
+        r, bits, flags = digit_run40_model(z, C)
+        P = sum(w << (32 * i) for i, w in enumerate(r))
+        assert P == z * (-pow(M40, -1, 2 ** (32 * W))) % 2 ** (32 * W)
+        s = z
+        for e in range(C - 1, -1, -1):
+            s = s * inv53 % M40                               # element e's state
+            qd = (s << 53) // M40
+            i = C - 1 - e
+            assert (P >> (53 * i)) % 2 ** 53 == qd, (z, e)
+            assert flags[e] == (qd < 2 ** 23), (z, e)
+            if flags[e]:
+                flagged += 1
+            else:
+                assert bits[e] == rz32_bits(s), (z, e)
+        assert s * pow(2, 53 * C, M40) % M40 == z             # the redo's start, C steps back
+    assert flagged >= 4
