@@ -296,7 +296,9 @@ rng_status rng_batch_generate_noalloc(uint32_t nstreams, const uint64_t *starts,
  *     RNG_ERANGE.
  *   - tune: NULL or zero fields choose; layout, depth, block, grid, chains
  *     and buffers mean what they mean for rng_generate_at; step, conv, skip
- *     and unit must be 0 (the variant has one of each), else RNG_EINVAL. */
+ *     and unit must be 0 (the variant has one of each), else RNG_EINVAL.
+ *     Tile depths are odd, except that FP32 on one chain (the default) also
+ *     takes 44, its default; any other even depth is RNG_EINVAL. */
 rng_status rng40_generate_at(uint64_t start_index, uint64_t offset, uint64_t n, rng_dtype dt,
                              void *out, void *cuda_stream, const rng_tune *tune);
 

@@ -2,7 +2,8 @@
 // Sec. 1; arithmetic in bcn_math40.cuh) on sm_103a.
 //
 // Layout and data movement are those of the 3^33 tiled kernel: the output
-// is cut into tiles of 32*c elements (c odd), each warp owns a contiguous
+// is cut into tiles of 32*c elements (c odd, or 44 for FP32 runs made from
+// one product), each warp owns a contiguous
 // range of tiles, lane l of a tile produces its elements [l*c, (l+1)*c) into
 // the warp's shared-memory tile buffer, and one lane hands the tile to the
 // bulk async-copy engine.  Head (before the first 16-byte boundary) and tail
@@ -97,7 +98,8 @@ __device__ __forceinline__ uint64_t state_of40(uint64_t ebase, uint64_t idx) {
 // from a field with no rounding question at all: Q's leading 24 bits, which
 // lie inside the field whenever Q >= 2^23 (a run with a smaller digit,
 // probability about 2^-30 per variate, is redone by its lane with the exact
-// forward chain).
+// forward chain).  Runs of 44 (4 mod 8, the FP32 default) store four
+// variates per 16-byte shared-memory store, odd runs one at a time.
 template <int W>
 constexpr NegMinvWords<W> make_neg_minv_words40() {  // -3^-40 mod 2^(32 W)
   NegMinvWords<W> t{};
@@ -194,14 +196,21 @@ struct DigitRun40 {
 template <int C, int I>
 __device__ __forceinline__ void digit_run40_word(uint32_t z0, uint32_t z1,
                                                  uint32_t (&r)[DigitRun40<C>::W], uint32_t& v0,
-                                                 uint32_t& v1, uint32_t* mine, uint32_t& qmin) {
+                                                 uint32_t& v1, uint32_t (&d)[4], uint32_t* mine,
+                                                 uint32_t& qmin) {
   run40_product_word<DigitRun40<C>::W, I>(z0, z1, r[I], v0, v1);
   constexpr int i = DigitRun40<C>::digit_of_word(I);
   if constexpr (i >= 0) {
     const uint32_t u1 = run_bits32<53 * i + 21>(r);
     const uint32_t u0 = run_bits32<53 * i - 11>(r);  // field 0: zeros below, unread
     qmin = min(qmin, u1);
-    mine[C - 1 - i] = f32_from_digit_words40(u1, u0);
+    if constexpr (vec4_depth(C)) {  // four variates per 16-byte store
+      d[i % 4] = f32_from_digit_words40(u1, u0);
+      if constexpr (i % 4 == 3)
+        *reinterpret_cast<uint4*>(mine + C - 4 * (i / 4 + 1)) = make_uint4(d[3], d[2], d[1], d[0]);
+    } else {
+      mine[C - 1 - i] = f32_from_digit_words40(u1, u0);
+    }
   }
 }
 
@@ -210,8 +219,8 @@ __device__ __forceinline__ void digit_run40_words(std::integer_sequence<int, I..
                                                   uint32_t* mine, uint32_t& qmin) {
   const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
   uint32_t r[DigitRun40<C>::W];
-  uint32_t v0 = 0, v1 = 0;
-  (digit_run40_word<C, I>(z0, z1, r, v0, v1, mine, qmin), ...);
+  uint32_t v0 = 0, v1 = 0, d[4];
+  (digit_run40_word<C, I>(z0, z1, r, v0, v1, d, mine, qmin), ...);
 }
 
 // One lane's FP32 run of C elements from z, the state one past it.  A run
@@ -377,6 +386,9 @@ static const void* pick40_dt(int layout, uint32_t chains, uint32_t depth) {
   }
   if (depth == 15) return (const void*)tiled40_kernel<DT, 1, 15>;
   if (depth == 31) return (const void*)tiled40_kernel<DT, 1, 31>;
+  if constexpr (DT == DT_F32) {  // four-variate stores
+    if (depth == 44) return (const void*)tiled40_kernel<DT, 1, 44>;
+  }
   return (const void*)tiled40_kernel<DT, 1, 0>;
 }
 

@@ -19,7 +19,7 @@ struct M40Params {
 
 // Whether one-chain FP32 runs of this depth are made from one product each
 // (the compiled depths; bcn_m40.cu).
-__host__ __device__ constexpr bool digit_run40_depth(uint64_t c) { return c == 15 || c == 31; }
+__host__ __device__ constexpr bool digit_run40_depth(uint64_t c) { return c == 15 || c == 31 || c == 44; }
 
 // The 3^40 kernel for an output type, layout, chains per lane and tile depth
 // (nullptr if there is none).

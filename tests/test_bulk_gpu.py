@@ -519,3 +519,20 @@ def test_small_calls_spread_their_tiles_over_every_sm(R, oracle_mod):
         assert_same(R.generate_at(a, 99, n, dtype), oracle_mod.generate(a, 99, n, dtype), dtype)
     assert R.resolve_tune(1 << 28, "f64")["block"] == 896
     assert R.resolve_tune(1 << 28, "f32")["block"] == 1024
+
+
+def test_fp32_one_product_runs_equal_the_backward_step_at_full_size(R, oracle_mod):
+    """The bench's 2^28 FP32 stream made by the default one-product runs and by
+    the backward step on two chains: every element identical (two different
+    computations of the same digits), and a sample equal to the oracle."""
+    import torch
+    a, n = M + 12345, 1 << 28
+    one = R.generate_at(a, 0, n, "f32", tune=R.make_tune(step="shared", layout="tiled",
+                                                        depth=44, chains=1))
+    back = R.generate_at(a, 0, n, "f32", tune=R.make_tune(step="shared", layout="tiled",
+                                                         depth=44, chains=2))
+    torch.cuda.synchronize()
+    assert torch.equal(one.view(torch.int32), back.view(torch.int32))
+    idx = np.random.default_rng(44).integers(0, n, size=4096).astype(np.int64)
+    got = one.view(torch.int32)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.array_equal(got, oracle_mod.at(a, idx.astype(np.uint64), "f32").view(np.int32))

@@ -51,6 +51,7 @@ def _check(R, oracle_mod, a, off, n, dtype, tune=None, shift=0):
 
 TUNES = [None,
          dict(depth=15, block=64, chains=1),
+         dict(depth=31, block=96, chains=1),
          dict(depth=31, block=128, chains=2),
          dict(depth=7, block=32),
          dict(depth=63, block=128, chains=2, buffers=2),
@@ -61,7 +62,8 @@ TUNES = [None,
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "u64"])
 def test_matches_the_oracle_for_every_tuning(R, oracle_mod, dtype):
-    for k, tune in enumerate(TUNES):
+    extra = [dict(depth=44, block=64, grid=5), dict(depth=44, block=1024)] if dtype == "f32" else []
+    for k, tune in enumerate(TUNES + extra):  # 44-deep runs: FP32 on one chain only
         for a, off, n in [(M40 + 100, 0, 1), (2 ** 64 - 1, 12345, 31 * 32 * 5 + 17),
                           (M40 + 987654321, 2 ** 40 + 7, 100003)]:
             _check(R, oracle_mod, a, off, n, dtype, tune, shift=k % 3)
@@ -69,10 +71,11 @@ def test_matches_the_oracle_for_every_tuning(R, oracle_mod, dtype):
 
 def test_heads_tails_and_small_sizes(R, oracle_mod):
     a = M40 + 4242
-    for n in (2, 3, 31, 32, 33, 992, 993, 31 * 32 * 3 - 1):
+    for n in (2, 3, 31, 32, 33, 992, 993, 31 * 32 * 3 - 1, 44 * 32 * 2 + 5):
         for shift in (0, 1, 2, 3):
             _check(R, oracle_mod, a, 77, n, "f64", dict(depth=31, block=64), shift)
             _check(R, oracle_mod, a, 77, n, "f32", dict(depth=15, block=64, chains=2), shift)
+            _check(R, oracle_mod, a, 77, n, "f32", None, shift)  # 44-deep one-product runs
 
 
 def test_offsets_across_the_period(R, oracle_mod):
@@ -124,6 +127,12 @@ def test_bad_arguments(R):
         with pytest.raises(R.RNGError) as e:
             R.generate40_at(M40 + 100, 0, 10, tune=tune)
         assert e.value.status == 1
+    # depth 44 is FP32 on one chain only
+    for dtype, tune in (("f64", dict(depth=44)), ("u64", dict(depth=44)),
+                        ("f32", dict(depth=44, chains=2)), ("f32", dict(depth=36))):
+        with pytest.raises(R.RNGError) as e:
+            R.generate40_at(M40 + 100, 0, 10, dtype, tune=tune)
+        assert e.value.status == 1, (dtype, tune)
 
 
 def test_full_size_sampled(R, oracle_mod):
@@ -187,7 +196,9 @@ def test_fp32_runs_from_one_product_at_the_redo_threshold(R, oracle_mod):
         zs.append(z)
     for z in zs:
         i = index_of_state(a, z)
-        for k, n, tune in [(30, 992 * 2, dict(depth=31, block=32, chains=1)),
+        for k, n, tune in [(43, 1408 * 2, dict(depth=44, block=32, chains=1)),
+                           (44 * 7 + 3, 1408 * 2, dict(depth=44, block=32, chains=1)),
+                           (30, 992 * 2, dict(depth=31, block=32, chains=1)),
                            (0, 992 * 2, dict(depth=31, block=32, chains=1)),
                            (31 * 5 + 17, 992 * 2, dict(depth=31, block=32, chains=1)),
                            (14, 480 * 2, dict(depth=15, block=32, chains=1)),
@@ -195,3 +206,18 @@ def test_fp32_runs_from_one_product_at_the_redo_threshold(R, oracle_mod):
                            (31 * 3 + 30, 992 * 2, dict(depth=31, block=32, chains=2))]:
             off = (i - k) % P40
             _check(R, oracle_mod, a, off, n, "f32", tune)
+
+
+def test_fp32_one_product_runs_equal_the_backward_step_at_full_size(R, oracle_mod):
+    """2^28 FP32 variates of the 3^40 stream from the default one-product runs
+    and from the backward step on two chains: every element identical, and a
+    sample equal to the oracle."""
+    import torch
+    a, n = M40 + 12345, 1 << 28
+    one = R.generate40_at(a, 0, n, "f32")
+    back = R.generate40_at(a, 0, n, "f32", tune=dict(depth=31, chains=2))
+    torch.cuda.synchronize()
+    assert torch.equal(one.view(torch.int32), back.view(torch.int32))
+    idx = np.random.default_rng(4040).integers(0, n, size=4096).astype(np.int64)
+    got = one.view(torch.int32)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.array_equal(got, _bits(oracle_mod.at40(a, idx.astype(np.uint64), "f32")))
