@@ -67,6 +67,8 @@ def parse_args():
     p.add_argument("--no-fused", action="store_true", help="skip the fused measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-m40", action="store_true", help="skip the 3^40-modulus measurement")
+    p.add_argument("--no-device-api", action="store_true",
+                   help="skip the device-side API measurement")
     p.add_argument("--paper-table", action="store_true",
                    help="print the paper's Table 1/2 protocol redone on this GPU and exit")
     p.add_argument("--no-autotune", action="store_true",
@@ -551,6 +553,31 @@ def measure_m40(rng, stream, peaks, steps: int):
     return out_d
 
 
+def measure_device_api(rng, stream, steps: int):
+    """The device-side generator (include/bcn_device.cuh) as a simulation uses
+    it: 2^30 FP64 variates of a = 3^33+12345 consumed in registers by 2^18
+    threads (4096 each, the paper's per-thread count), each writing only the
+    sum mod 2^64 of its variates' bit patterns (one integer add a variate)."""
+    import torch
+    n, threads = 1 << 30, 1 << 18
+    for _ in range(3):
+        rng.device_api_checksum(SEED, 0, n, threads=threads, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rng.device_api_checksum(SEED, 0, n, threads=threads, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "2^30 FP64 variates from a = 3^33+12345 consumed in registers by a "
+                        "kernel written against include/bcn_device.cuh: 2^18 threads x 4096 "
+                        "variates, each thread's sum of the variates' bit patterns stored, "
+                        "nothing else",
+            "launches": steps, "ms_per_launch": ms, "variates_per_s": n / (ms / 1e3)}
+
+
 def measure_serving(rng, n_requests: int = 20000):
     """The served form: Poisson arrivals at 20k req/s, sizes log-uniform 1 KiB..256
     MiB, random start indices and offsets, FP32/FP64 1:1, 40 GB device output pool
@@ -835,6 +862,9 @@ def run_ours(args):
     m40 = None
     if not args.no_m40 and rank == 0:
         m40 = measure_m40(rng, stream, load_peaks(), steps=max(min(args.steps // 20, 50), 5))
+    device_api = None
+    if not args.no_device_api and rank == 0:
+        device_api = measure_device_api(rng, stream, steps=10)
     serving = None
     if not args.no_serve and rank == 0:
         serving = measure_serving(rng)
@@ -900,6 +930,8 @@ def run_ours(args):
         }
         if config1 is not None:
             line["config_1e6"] = config1
+        if device_api is not None:
+            line["device_api"] = device_api
         if batched is not None:
             line["batched"] = batched
         if fused is not None:

@@ -504,6 +504,19 @@ rng_status rng_device_api_check(uint64_t start_index, uint64_t offset, uint64_t 
                                 double *out_f64, float *out_f32, uint32_t threads,
                                 void *cuda_stream);
 
+/* The device-side API used as the paper intends it for simulations on the GPU
+ * (Sec. 2: each thread an independent subsequence with a 64-bit state, no
+ * shared memory): `threads` threads (a positive multiple of 128, else
+ * RNG_EINVAL) each take variates [t*n/T, (t+1)*n/T) of offset .. offset+n-1
+ * of the sequence seeded with start_index (else RNG_ERANGE) and consume them
+ * in registers; thread t writes only the sum modulo 2^64 of their FP64 bit
+ * patterns to sums[t] (a caller-owned device array of `threads` words,
+ * 8-byte aligned, else RNG_EINVAL).  n = 0 writes zeros.  Nothing else is
+ * stored and the consumer is one integer add per variate, so the call times
+ * the generator itself.  Asynchronous on `cuda_stream`. */
+rng_status rng_device_api_checksum(uint64_t start_index, uint64_t offset, uint64_t n,
+                                   uint64_t *sums, uint32_t threads, void *cuda_stream);
+
 /* -------------------------------------------------------------- autotune */
 
 /* Time each of the `ncand` candidate tunings of a bulk call (n elements of

@@ -24,9 +24,41 @@ __global__ void device_api_kernel(uint64_t start, uint64_t offset, uint64_t n, d
   }
 }
 
+// Thread t of T consumes variates [t*n/T, (t+1)*n/T) in registers: the
+// wrap-around sum of their FP64 bit patterns (one 64-bit integer add each,
+// so the FP64 pipe stays free) is its only output (sums[t]).
+__global__ void device_api_checksum_kernel(uint64_t start, uint64_t offset, uint64_t n,
+                                           uint64_t* sums) {
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t a = (uint64_t)((unsigned __int128)n * t / T);
+  const uint64_t b = (uint64_t)((unsigned __int128)n * (t + 1) / T);
+  bcn_device::Stream g = bcn_device::make_stream(start, offset, a);
+  uint64_t s = 0;
+  for (uint64_t i = a; i < b; ++i)
+    s += (uint64_t)__double_as_longlong(bcn_device::next_f64(g));
+  sums[t] = s;
+}
+
 }  // namespace
 
 using namespace bcn;
+
+extern "C" rng_status rng_device_api_checksum(uint64_t start_index, uint64_t offset,
+                                              uint64_t n, uint64_t* sums, uint32_t threads,
+                                              void* cuda_stream) {
+  if (start_index < kSeedMin || start_index > kSeedMax)
+    return set_error(RNG_ERANGE, "start index outside [3^33+100, 2^53]");
+  if (threads == 0 || threads % 128 != 0)
+    return set_error(RNG_EINVAL, "threads %u must be a positive multiple of 128", threads);
+  if (!sums || (uintptr_t)sums % 8) return set_error(RNG_EINVAL, "sums NULL or misaligned");
+  device_api_checksum_kernel<<<threads / 128, 128, 0,
+                               static_cast<cudaStream_t>(cuda_stream)>>>(start_index, offset, n,
+                                                                        sums);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "device API checksum launch");
+  return RNG_OK;
+}
 
 extern "C" rng_status rng_device_api_check(uint64_t start_index, uint64_t offset, uint64_t n,
                                            double* out_f64, float* out_f32, uint32_t threads,

@@ -120,6 +120,7 @@ def _load() -> ctypes.CDLL:
         "rng_mc_round_totals": ([vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)], i32),
         "rng_batch_generate_noalloc": ([u32, vp, vp, vp, vp, vp, tp, vp], i32),
         "rng_device_api_check": ([u64, u64, u64, vp, vp, u32, vp], i32),
+        "rng_device_api_checksum": ([u64, u64, u64, vp, u32, vp], i32),
         "rng_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], i32),
         "rng_server_submit": ([vp, u64, u64, u64, i32, ctypes.POINTER(u64)], i32),
         "rng_server_cancel": ([vp, u64], i32),
@@ -405,6 +406,18 @@ def device_api_check(start_index: int, offset: int, n: int, threads: int = 4096,
                                     ctypes.c_void_p(f32.data_ptr()), threads,
                                     ctypes.c_void_p(_stream_handle(stream))))
     return f64, f32
+
+
+def device_api_checksum(start_index: int, offset: int, n: int, threads: int = 1 << 18,
+                        stream=None):
+    """Per-thread sums mod 2^64 of the FP64 bit patterns of variates consumed
+    in registers by a kernel written against bcn_device.cuh (thread t takes
+    [t*n/T, (t+1)*n/T)); an int64 tensor holding the 64-bit words."""
+    sums = torch.empty(threads, dtype=torch.int64, device="cuda")
+    _check(lib.rng_device_api_checksum(start_index, offset, n,
+                                       ctypes.c_void_p(sums.data_ptr()), threads,
+                                       ctypes.c_void_p(_stream_handle(stream))))
+    return sums
 
 
 class Batch:

@@ -159,6 +159,19 @@ int main(void) {
 """
 
 
+def test_device_api_checksum_checks_arguments_first(lib):
+    """Seed range, thread count and output pointer are checked on the host,
+    before any launch (these calls need no GPU)."""
+    import ctypes
+    fn = lib.lib.rng_device_api_checksum
+    buf = (ctypes.c_uint64 * 128)()
+    assert fn(3 ** 33 + 99, 0, 10, ctypes.cast(buf, ctypes.c_void_p), 128, None) == 2
+    assert fn(2 ** 53 + 1, 0, 10, ctypes.cast(buf, ctypes.c_void_p), 128, None) == 2
+    for threads in (0, 100, 129):
+        assert fn(3 ** 33 + 100, 0, 10, ctypes.cast(buf, ctypes.c_void_p), threads, None) == 1
+    assert fn(3 ** 33 + 100, 0, 10, None, 128, None) == 1
+
+
 def test_the_boundary_is_usable_from_plain_c(lib, tmp_path):
     """The header compiles as C99 with warnings as errors, and a C program
     linked against the library drives its host-side entry points."""

@@ -30,7 +30,7 @@ def test_two_ranks_print_one_weak_scaling_line():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
            os.path.join(ROOT, "bench.py"), "--gpus", "2", "--steps", "5", "--warmup", "3",
-           f"--variates={n}", "--no-batch", "--no-fused", "--no-serve", "--no-m40",
+           f"--variates={n}", "--no-batch", "--no-fused", "--no-serve", "--no-m40", "--no-device-api",
            "--no-cpu-baseline", "--no-autotune", "--e2e-steps", "1"]
     env = dict(os.environ, BCN_BENCH_BACKEND="gloo")
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)

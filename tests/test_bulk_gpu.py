@@ -170,6 +170,23 @@ def test_device_side_api_matches_the_oracle(R, oracle_mod):
         assert_same(f32, oracle_mod.generate(a, off, n, "f32"), f"f32 {a} {threads}")
 
 
+def test_device_side_api_consumed_in_registers(R, oracle_mod):
+    """The device-side API as a simulation uses it: each thread consumes its
+    own variates in registers and writes only the sum mod 2^64 of their FP64
+    bit patterns; every thread's word equals that sum over the oracle's
+    variates of the same range (uneven ranges, a range across offset 2^64,
+    and an empty call)."""
+    for a, off, n, threads in [(M + 100, 0, 100003, 128), (M + 777, 12345, (1 << 20) + 5, 1024),
+                               (2 ** 53, 2 ** 64 - 3000, 6000, 256), (M + 105, 7, 0, 128)]:
+        sums = R.device_api_checksum(a, off, n, threads=threads).cpu().numpy().view(np.uint64)
+        want = (oracle_mod.generate(a, off, n, "f64").view(np.uint64) if n
+                else np.zeros(0, dtype=np.uint64))
+        for t in range(threads):
+            lo, hi = n * t // threads, n * (t + 1) // threads
+            w = int(want[lo:hi].astype(object).sum()) % 2 ** 64 if hi > lo else 0
+            assert int(sums[t]) == w, (a, off, n, t)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_small_misaligned_outputs_and_canaries(R, oracle_mod, dtype):
     """n = 1..97 at every element offset inside a 16-byte line; the bytes
