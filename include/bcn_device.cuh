@@ -26,7 +26,7 @@
 namespace bcn_device {
 
 struct Stream {
-  uint64_t z;  // state of the next variate
+  uint64_t Z;  // state of the next variate times 2^10 (the bulk kernels' scaled chain)
 };
 
 // A generator positioned at variate `offset` (0-based) of the sequence seeded
@@ -35,7 +35,8 @@ struct Stream {
 __device__ inline Stream make_stream(uint64_t start_index, uint64_t offset) {
   const uint64_t e0 = (start_index - bcn::kM) % bcn::kP;
   Stream s;
-  s.z = bcn::seed_state_table(bcn::exponent_add(bcn::exponent_add(e0, offset), 1));
+  s.Z = bcn::seed_state_table(bcn::exponent_add(bcn::exponent_add(e0, offset), 1))
+        << bcn::kZShift;
   return s;
 }
 
@@ -44,25 +45,41 @@ __device__ inline Stream make_stream(uint64_t start_index, uint64_t offset) {
 __device__ inline Stream make_stream(uint64_t start_index, uint64_t offset, uint64_t extra) {
   const uint64_t e0 = (start_index - bcn::kM) % bcn::kP;
   Stream s;
-  s.z = bcn::seed_state_table(
-      bcn::exponent_add(bcn::exponent_add(bcn::exponent_add(e0, offset), extra), 1));
+  s.Z = bcn::seed_state_table(
+            bcn::exponent_add(bcn::exponent_add(bcn::exponent_add(e0, offset), extra), 1))
+        << bcn::kZShift;
   return s;
+}
+
+// The FP64 bits of the next variate, RN(z * r3i), and the step to the one
+// after: the bulk kernels' shared-quotient step on the scaled state, with the
+// exact conversion for the rare variate below 2^-21 that its fast rounding
+// does not cover (the state advance is exact either way).
+__device__ inline uint64_t next_bits(Stream& s) {
+  const uint64_t Z0 = s.Z;
+  uint32_t qmin = 0xffffffffu;
+  uint64_t bits = bcn::shared_step_f64_ptx(s.Z, qmin);
+  if (__builtin_expect(qmin == 0, 0)) {
+    uint64_t z = Z0 >> bcn::kZShift;
+    bits = bcn::shared_step_f64(z);
+  }
+  return bits;
 }
 
 // The next variate as a double in (0,1): RN(z * r3i), exactly.
 __device__ inline double next_f64(Stream& s) {
-  return __longlong_as_double((long long)bcn::shared_step_f64(s.z));
+  return __longlong_as_double((long long)next_bits(s));
 }
 
 // The next variate as a float in (0,1): the double variate rounded toward zero.
 __device__ inline float next_f32(Stream& s) {
-  return __uint_as_float(bcn::f32_bits_from_f64_bits(bcn::shared_step_f64(s.z)));
+  return __uint_as_float(bcn::f32_bits_from_f64_bits(next_bits(s)));
 }
 
 // The next raw state z in [1, 3^33).
 __device__ inline uint64_t next_state(Stream& s) {
-  const uint64_t z = s.z;
-  s.z = bcn::shared_advance(z);
+  const uint64_t z = s.Z >> bcn::kZShift;
+  s.Z = bcn::shared_advance_scaled(s.Z);
   return z;
 }
 

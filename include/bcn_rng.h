@@ -497,12 +497,13 @@ rng_status rng_mc_round_totals(const uint64_t *totals, double *sum, double *sums
 /* Run a kernel written only against the device-side API (bcn_device.cuh):
  * `threads` threads each create their own generator at their first variate
  * and write variates offset .. offset+n-1 of the sequence seeded with
- * start_index, as FP64 to out_f64 and FP32 to out_f32 (caller-owned device
- * arrays of n elements).  Exposes the device API to the same checks as every
- * other path.  Asynchronous on `cuda_stream`. */
+ * start_index, as FP64 to out_f64, FP32 to out_f32 and, when out_state is not
+ * NULL, their raw states to out_state (caller-owned device arrays of n
+ * elements, aligned to their element size).  Exposes the device API to the
+ * same checks as every other path.  Asynchronous on `cuda_stream`. */
 rng_status rng_device_api_check(uint64_t start_index, uint64_t offset, uint64_t n,
-                                double *out_f64, float *out_f32, uint32_t threads,
-                                void *cuda_stream);
+                                double *out_f64, float *out_f32, uint64_t *out_state,
+                                uint32_t threads, void *cuda_stream);
 
 /* The device-side API used as the paper intends it for simulations on the GPU
  * (Sec. 2: each thread an independent subsequence with a 64-bit state, no

@@ -8,19 +8,22 @@
 namespace {
 
 // Thread t of T takes variates [t*n/T, (t+1)*n/T) of the call, with its own
-// generator positioned there; FP64 and FP32 of each variate go to two arrays.
+// generator positioned there; FP64, FP32 and (when `st` is not null) the raw
+// state of each variate go to their arrays, each from its own copy of the
+// generator.
 __global__ void device_api_kernel(uint64_t start, uint64_t offset, uint64_t n, double* f64,
-                                  float* f32) {
+                                  float* f32, uint64_t* st) {
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t a = (uint64_t)((unsigned __int128)n * t / T);
   const uint64_t b = (uint64_t)((unsigned __int128)n * (t + 1) / T);
   if (a >= b) return;
   bcn_device::Stream g = bcn_device::make_stream(start, offset, a);
-  bcn_device::Stream h = g;
+  bcn_device::Stream h = g, k = g;
   for (uint64_t i = a; i < b; ++i) {
     f64[i] = bcn_device::next_f64(g);
     f32[i] = bcn_device::next_f32(h);
+    if (st) st[i] = bcn_device::next_state(k);
   }
 }
 
@@ -61,18 +64,20 @@ extern "C" rng_status rng_device_api_checksum(uint64_t start_index, uint64_t off
 }
 
 extern "C" rng_status rng_device_api_check(uint64_t start_index, uint64_t offset, uint64_t n,
-                                           double* out_f64, float* out_f32, uint32_t threads,
+                                           double* out_f64, float* out_f32,
+                                           uint64_t* out_state, uint32_t threads,
                                            void* cuda_stream) {
   if (start_index < kSeedMin || start_index > kSeedMax)
     return set_error(RNG_ERANGE, "start index outside [3^33+100, 2^53]");
   if (n == 0) return RNG_OK;
-  if (!out_f64 || !out_f32 || (uintptr_t)out_f64 % 8 || (uintptr_t)out_f32 % 4)
+  if (!out_f64 || !out_f32 || (uintptr_t)out_f64 % 8 || (uintptr_t)out_f32 % 4 ||
+      (uintptr_t)out_state % 8)
     return set_error(RNG_EINVAL, "outputs NULL or misaligned");
   if (threads == 0) threads = 1;
   const uint32_t block = threads < 128 ? threads : 128;
   const uint32_t grid = (threads + block - 1) / block;
   device_api_kernel<<<grid, block, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
-      start_index, offset, n, out_f64, out_f32);
+      start_index, offset, n, out_f64, out_f32, out_state);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "device API check launch");
   return RNG_OK;

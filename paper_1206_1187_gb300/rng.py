@@ -119,7 +119,7 @@ def _load() -> ctypes.CDLL:
         "rng_consume_mc_totals": ([u64, u64, u64, u64, vp, vp, vp, vp, vp, vp, tp], i32),
         "rng_mc_round_totals": ([vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)], i32),
         "rng_batch_generate_noalloc": ([u32, vp, vp, vp, vp, vp, tp, vp], i32),
-        "rng_device_api_check": ([u64, u64, u64, vp, vp, u32, vp], i32),
+        "rng_device_api_check": ([u64, u64, u64, vp, vp, vp, u32, vp], i32),
         "rng_device_api_checksum": ([u64, u64, u64, vp, u32, vp], i32),
         "rng_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], i32),
         "rng_server_submit": ([vp, u64, u64, u64, i32, ctypes.POINTER(u64)], i32),
@@ -398,14 +398,18 @@ def mc_round_totals(words) -> tuple[float, float]:
     return s1.value, s2.value
 
 
-def device_api_check(start_index: int, offset: int, n: int, threads: int = 4096, stream=None):
-    """Variates from a kernel written against bcn_device.cuh: (f64, f32) tensors."""
+def device_api_check(start_index: int, offset: int, n: int, threads: int = 4096, stream=None,
+                     states: bool = False):
+    """Variates from a kernel written against bcn_device.cuh: (f64, f32)
+    tensors, and the raw states as a third (uint64) when `states` is set."""
     f64 = torch.empty(n, dtype=torch.float64, device="cuda")
     f32 = torch.empty(n, dtype=torch.float32, device="cuda")
+    st = torch.empty(n, dtype=torch.uint64, device="cuda") if states else None
     _check(lib.rng_device_api_check(start_index, offset, n, ctypes.c_void_p(f64.data_ptr()),
-                                    ctypes.c_void_p(f32.data_ptr()), threads,
+                                    ctypes.c_void_p(f32.data_ptr()),
+                                    ctypes.c_void_p(st.data_ptr() if states else 0), threads,
                                     ctypes.c_void_p(_stream_handle(stream))))
-    return f64, f32
+    return (f64, f32, st) if states else (f64, f32)
 
 
 def device_api_checksum(start_index: int, offset: int, n: int, threads: int = 1 << 18,

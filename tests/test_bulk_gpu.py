@@ -165,9 +165,10 @@ def test_device_side_api_matches_the_oracle(R, oracle_mod):
     for a, off, n, threads in [(M + 100, 0, 100003, 1000), (2 ** 53, 2 ** 50 + 7, 4097, 1),
                                (M + 12345, 123, 250000, 65536), (M + 100, 2 ** 64 - 3000, 6000, 64),
                                (2 ** 53, 2 ** 64 - 1, 10, 3)]:
-        f64, f32 = R.device_api_check(a, off, n, threads=threads)
+        f64, f32, st = R.device_api_check(a, off, n, threads=threads, states=True)
         assert_same(f64, oracle_mod.generate(a, off, n, "f64"), f"f64 {a} {threads}")
         assert_same(f32, oracle_mod.generate(a, off, n, "f32"), f"f32 {a} {threads}")
+        assert_same(st, oracle_mod.generate(a, off, n, "u64"), f"u64 {a} {threads}")
 
 
 def test_device_side_api_consumed_in_registers(R, oracle_mod):
