@@ -22,33 +22,45 @@
 
 namespace bcn {
 
-// -m^-1 mod 2^(32 W) as W 32-bit words, lowest first, solved word by word:
-// A = (m * (words so far) + 1) / 2^(32 w), and the next word n makes
-// A + m n divisible by 2^32 (n = -A m^-1 mod 2^32).
+// -M^-1 mod 2^(32 W) for an odd modulus M < 2^64 as W 32-bit words, lowest
+// first, solved word by word: A = (M * (words so far) + 1) / 2^(32 w), and
+// the next word n makes A + M n divisible by 2^32 (n = -A M^-1 mod 2^32).
 template <int W>
 struct NegMinvWords {
   uint32_t w[W];
 };
-template <int W>
+template <int W, uint64_t M>
 constexpr NegMinvWords<W> make_neg_minv_words() {
   NegMinvWords<W> t{};
-  const uint32_t inv = (uint32_t)inv_mod_2_64(kM);  // m^-1 mod 2^32
+  const uint32_t inv = (uint32_t)inv_mod_2_64(M);  // M^-1 mod 2^32
   u128 A = 1;
   for (int i = 0; i < W; ++i) {
     const uint32_t n = 0u - (uint32_t)A * inv;
-    A += (u128)kM * n;  // low word now zero; A < 2^86
+    A += (u128)M * n;  // low word now zero; A < 2^97
     t.w[i] = n;
     A >>= 32;
   }
   return t;
 }
-static_assert((make_neg_minv_words<2>().w[0] |
-               ((uint64_t)(make_neg_minv_words<2>().w[1] & 0x1FFFFFu) << 32)) == kNegMinv53,
+static_assert((make_neg_minv_words<2, kM>().w[0] |
+               ((uint64_t)(make_neg_minv_words<2, kM>().w[1] & 0x1FFFFFu) << 32)) == kNegMinv53,
               "the low 53 bits of -m^-1 mod 2^64");
 
-template <int W>
+template <int W, uint64_t M = kM>
 struct RunMinv {
-  static constexpr NegMinvWords<W> t = make_neg_minv_words<W>();
+  static constexpr NegMinvWords<W> t = make_neg_minv_words<W, M>();
+};
+
+// Where a run's C digits sit in its product: W words, and the digit whose
+// top bit lies in word I (-1 if none; at most one, as 53 > 32).
+template <int C>
+struct DigitGeometry {
+  static constexpr int W = (53 * C + 31) / 32;
+  __host__ __device__ static constexpr int digit_of_word(int I) {
+    const int num = 32 * I + 31 - 52;
+    const int i = num < 0 ? 0 : num / 53;
+    return i < C && (53 * i + 52) / 32 == I ? i : -1;
+  }
 };
 
 // Word I of z N (z = (z1:z0) on 32-bit words, z1 < 2^21), built from the
@@ -132,29 +144,6 @@ __device__ __forceinline__ uint32_t f32_from_digit_words(uint32_t u1, uint32_t u
   return b;
 }
 
-// The warp's exact redo of flagged runs of C elements: for each lane whose
-// bit is set in `redo`, lane l makes elements l, l + 32, ... of that lane's
-// run, each from one jump of the run's element 0 (`z0`, that element's
-// state, taken from its lane), with the forward step and the exact
-// conversion.
-template <int C>
-__device__ __forceinline__ void warp_redo_digit_runs(uint32_t* mine, uint64_t z0,
-                                                     uint32_t redo) {
-  const uint32_t lane = threadIdx.x & 31u;
-  uint32_t* const wbuf = mine - lane * C;  // the warp's tile
-  __syncwarp();  // every lane's run is in shared memory before others overwrite it
-  while (redo != 0) {
-    const int L = __ffs(redo) - 1;
-    redo &= redo - 1;
-    const uint64_t zl = __shfl_sync(0xffffffffu, z0, L);
-    for (uint32_t i = lane; i < (uint32_t)C; i += 32) {
-      uint64_t z = mulmod_pre(zl, __ldg(&kElemJump.j[i]), __ldg(&kElemJump.q[i]));
-      wbuf[L * C + i] = f32_bits_from_f64_bits(shared_step_f64(z));
-    }
-  }
-  __syncwarp();
-}
-
 // An FP32 run of C elements (C of 4 mod 8, four-variate shared-memory stores
 // as in back_run_f32) from the state one past the run, z = s_(f+C): field i
 // of z N mod 2^(53C) is the digit of element C - 1 - i.  Words are formed
@@ -162,14 +151,7 @@ __device__ __forceinline__ void warp_redo_digit_runs(uint32_t* mine, uint64_t z0
 // only a few words are live at a time.  A run that needs the exact path is
 // redone by the warp from the state of its element 0, z 2^(-53C) mod m.
 template <int C>
-struct DigitRunF32 {
-  static constexpr int W = (53 * C + 31) / 32;  // words of the product
-  // the digit whose top bit lies in word I, or -1 (at most one: 53 > 32)
-  __host__ __device__ static constexpr int digit_of_word(int I) {
-    const int num = 32 * I + 31 - 52;
-    const int i = num < 0 ? 0 : num / 53;
-    return i < C && (53 * i + 52) / 32 == I ? i : -1;
-  }
+struct DigitRunF32 : DigitGeometry<C> {
   static constexpr uint64_t back = host_pow2((kP - (53ull * C) % kP) % kP);  // 2^(-53C)
   static constexpr uint64_t back_q = host_mulmod_quotient(back);
 };
@@ -207,8 +189,8 @@ __device__ __forceinline__ void digit_run_f32(uint32_t* mine, uint64_t z) {
   digit_run_words<C>(std::make_integer_sequence<int, DigitRunF32<C>::W>{}, z, mine, qmin);
   const uint32_t redo = __ballot_sync(0xffffffffu, qmin == 0);
   if (__builtin_expect(redo != 0, 0))
-    warp_redo_digit_runs<C>(mine, mulmod_pre(z, DigitRunF32<C>::back, DigitRunF32<C>::back_q),
-                            redo);
+    warp_redo_runs_f32(mine, C, mulmod_pre(z, DigitRunF32<C>::back, DigitRunF32<C>::back_q),
+                       redo);
 }
 
 // Whether a one-chain tile loop of this kind makes its FP32 runs this way

@@ -352,6 +352,29 @@ static_assert(make_elem_jump().j[0] == 1 && make_elem_jump().j[1] == host_pow2(5
                   make_elem_jump().j[kMaxDepth] == host_pow2(53ull * kMaxDepth),
               "element jumps");
 
+// The warp's exact redo of flagged FP32 runs of c elements: for each lane
+// whose bit is set in `redo`, lane l makes elements l, l + 32, ... of that
+// lane's run, each from one jump of the run's element 0 (`z0`, the state of
+// that element, taken from its lane), with the forward step and the exact
+// conversion.  Made by its own lane alone, a redo held the other 31 lanes
+// for a whole run.
+__device__ __forceinline__ void warp_redo_runs_f32(uint32_t* mine, uint32_t c, uint64_t z0,
+                                                   uint32_t redo) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t* const wbuf = mine - lane * c;  // the warp's tile
+  __syncwarp();  // every lane's run is in shared memory before others overwrite it
+  while (redo != 0) {
+    const int L = __ffs(redo) - 1;
+    redo &= redo - 1;
+    const uint64_t zl = __shfl_sync(0xffffffffu, z0, L);
+    for (uint32_t i = lane; i < c; i += 32) {
+      uint64_t z = mulmod_pre(zl, __ldg(&kElemJump.j[i]), __ldg(&kElemJump.q[i]));
+      wbuf[L * c + i] = f32_bits_from_f64_bits(shared_step_f64(z));
+    }
+  }
+  __syncwarp();
+}
+
 template <int CDEPTH>
 __device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_t& ya,
                                              uint64_t& yb) {
@@ -383,29 +406,11 @@ __device__ __forceinline__ void back_run_f32(uint32_t* mine, uint32_t c, uint64_
     }
     for (uint32_t i = nb; i < s; ++i) mine[s - 1 - i] = back_step_f32_ptx(ya, qmin);
   }
-  // A flagged run is redone exactly by the whole warp: for each flagged lane,
-  // lane l makes elements l, l + 32, ... of that lane's run, each from one
-  // jump of the run's element 0 (the backward chain a ends there), with the
-  // forward step and the exact conversion.  Made by its own lane alone, the
-  // redo held the other 31 lanes for a whole run.
-  uint32_t redo = __ballot_sync(0xffffffffu, qmin == 0);
-  if (__builtin_expect(redo != 0, 0)) {
-    const uint32_t cc = CDEPTH > 0 ? (uint32_t)CDEPTH : c;
-    const uint32_t lane = threadIdx.x & 31u;
-    uint32_t* const wbuf = mine - lane * cc;  // the warp's tile
-    const uint64_t z0 = ya + 1;               // element 0 of this lane's run
-    __syncwarp();  // every lane's run is in shared memory before others overwrite it
-    while (redo != 0) {
-      const int L = __ffs(redo) - 1;
-      redo &= redo - 1;
-      const uint64_t zl = __shfl_sync(0xffffffffu, z0, L);
-      for (uint32_t i = lane; i < cc; i += 32) {
-        uint64_t z = mulmod_pre(zl, __ldg(&kElemJump.j[i]), __ldg(&kElemJump.q[i]));
-        wbuf[L * cc + i] = f32_bits_from_f64_bits(shared_step_f64(z));
-      }
-    }
-    __syncwarp();
-  }
+  // A flagged run is redone exactly by the whole warp (the backward chain a
+  // ends at the state of the run's element 0).
+  const uint32_t redo = __ballot_sync(0xffffffffu, qmin == 0);
+  if (__builtin_expect(redo != 0, 0))
+    warp_redo_runs_f32(mine, CDEPTH > 0 ? (uint32_t)CDEPTH : c, ya + 1, redo);
 }
 
 // Whether a two-chain tile loop of this kind runs the backward FP32 step.

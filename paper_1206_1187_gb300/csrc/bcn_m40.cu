@@ -100,26 +100,9 @@ __device__ __forceinline__ uint64_t state_of40(uint64_t ebase, uint64_t idx) {
 // probability about 2^-30 per variate, is redone by its lane with the exact
 // forward chain).  Runs of 44 (4 mod 8, the FP32 default) store four
 // variates per 16-byte shared-memory store, odd runs one at a time.
-template <int W>
-constexpr NegMinvWords<W> make_neg_minv_words40() {  // -3^-40 mod 2^(32 W)
-  NegMinvWords<W> t{};
-  const uint32_t inv = (uint32_t)inv_mod_2_64(k40M);  // 3^-40 mod 2^32
-  u128 A = 1;
-  for (int i = 0; i < W; ++i) {
-    const uint32_t n = 0u - (uint32_t)A * inv;
-    A += (u128)k40M * n;  // low word now zero; A < 2^97
-    t.w[i] = n;
-    A >>= 32;
-  }
-  return t;
-}
-static_assert((make_neg_minv_words40<2>().w[0] |
-               ((uint64_t)make_neg_minv_words40<2>().w[1] << 32)) == k40NegMinv,
+static_assert((make_neg_minv_words<2, k40M>().w[0] |
+               ((uint64_t)make_neg_minv_words<2, k40M>().w[1] << 32)) == k40NegMinv,
               "-3^-40 mod 2^64");
-template <int W>
-struct RunMinv40 {
-  static constexpr NegMinvWords<W> t = make_neg_minv_words40<W>();
-};
 
 // Word I of z N for a full 64-bit state z = (z1:z0).  V = (v1:v0), the part
 // of the lower words' sum above word I - 1, stays below 2^34 (v1 <= 3);
@@ -129,13 +112,13 @@ struct RunMinv40 {
 template <int W, int I>
 __device__ __forceinline__ void run40_product_word(uint32_t z0, uint32_t z1, uint32_t& r,
                                                    uint32_t& v0, uint32_t& v1) {
-  constexpr uint32_t nI = RunMinv40<W>::t.w[I];
+  constexpr uint32_t nI = RunMinv<W, k40M>::t.w[I];
   if constexpr (I == 0) {
     r = z0 * nI;
     v0 = __umulhi(z0, nI);
     v1 = 0;
   } else if constexpr (I == W - 1) {  // the top word: no carry out
-    constexpr uint32_t nP = RunMinv40<W>::t.w[I - 1];
+    constexpr uint32_t nP = RunMinv<W, k40M>::t.w[I - 1];
     asm("{\n\t"
         ".reg .u32 x0;\n\t"
         "mad.lo.u32 x0, %3, %5, %1;\n\t"
@@ -144,7 +127,7 @@ __device__ __forceinline__ void run40_product_word(uint32_t z0, uint32_t z1, uin
         : "=r"(r)
         : "r"(v0), "r"(z0), "r"(z1), "n"(nI), "n"(nP));
   } else {
-    constexpr uint32_t nP = RunMinv40<W>::t.w[I - 1];
+    constexpr uint32_t nP = RunMinv<W, k40M>::t.w[I - 1];
     // r is early-clobber: it must not share a register with z0
     asm("{\n\t"
         ".reg .u32 x0, x1, x2;\n\t"
@@ -180,14 +163,7 @@ __device__ __forceinline__ uint32_t f32_from_digit_words40(uint32_t u1, uint32_t
 }
 
 template <int C>
-struct DigitRun40 {
-  static constexpr int W = (53 * C + 31) / 32;  // words of the product
-  // the digit whose top bit lies in word I, or -1 (at most one: 53 > 32)
-  __host__ __device__ static constexpr int digit_of_word(int I) {
-    const int num = 32 * I + 31 - 52;
-    const int i = num < 0 ? 0 : num / 53;
-    return i < C && (53 * i + 52) / 32 == I ? i : -1;
-  }
+struct DigitRun40 : DigitGeometry<C> {
   // 2^(-53C) mod 3^40 in Montgomery form: one past the run -> element 0
   static constexpr uint64_t back =
       host40_mont_form(host40_pow2((k40P - (53ull * C) % k40P) % k40P));
