@@ -575,7 +575,9 @@ def measure_device_api(rng, stream, steps: int):
                         "kernel written against include/bcn_device.cuh: 2^18 threads x 4096 "
                         "variates, each thread's sum of the variates' bit patterns stored, "
                         "nothing else",
-            "launches": steps, "ms_per_launch": ms, "variates_per_s": n / (ms / 1e3)}
+            "launches": steps, "ms_per_launch": ms, "variates_per_s": n / (ms / 1e3),
+            "roofline": issue_roofline(profiled_value("inst_per_variate", "devapi_2e30", "device"),
+                                       n / (ms / 1e3), "inst_per_variate[devapi_2e30]")}
 
 
 def measure_serving(rng, n_requests: int = 20000):

@@ -67,6 +67,7 @@ KERNEL_SOURCES = {
     "mc": ["bcn_mc.cu", "bcn_mc.cuh", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
     "m40": ["bcn_m40.cu", "bcn_m40.cuh", "bcn_digits.cuh", "bcn_gen.cuh", "bcn_math.cuh",
             "bcn_math40.cuh", "bcn_internal.h"],
+    "device": ["bcn_device_check.cu", "bcn_device.cuh", "bcn_math.cuh", "bcn_internal.h"],
 }
 
 

@@ -5,6 +5,7 @@
     python -m paper_1206_1187_gb300.cases batch 512 [reps]   # first 512 streams of the batched workload
     python -m paper_1206_1187_gb300.cases batch 4096 [reps]  # the whole batched workload
     python -m paper_1206_1187_gb300.cases mc 16384 [reps]
+    python -m paper_1206_1187_gb300.cases devapi 1073741824 [reps]  # device-side header
     python -m paper_1206_1187_gb300.cases m40 33554432 [reps]      # 3^40, FP64
     python -m paper_1206_1187_gb300.cases m40f32 33554432 [reps]   # 3^40, FP32
 
@@ -52,6 +53,9 @@ def main(argv):
     elif case == "mc":
         for _ in range(reps):
             rng.consume_mc(3 ** 33 + 100, size, 1 << 16)
+    elif case == "devapi":  # size variates consumed in registers by 2^18 threads
+        for _ in range(reps):
+            rng.device_api_checksum(seed, 0, size, threads=1 << 18)
     else:
         raise SystemExit(f"unknown case {case!r}")
     torch.cuda.synchronize()

@@ -24,6 +24,7 @@ READ_BY_BENCH = {
     ("fp64_pipe_busy_frac", "mc_2e36"): "mc",
     ("traffic_per_algorithmic_byte", "batch_512"): "batch",
     ("inst_per_variate", "batch_512"): "batch",
+    ("inst_per_variate", "devapi_2e30"): "device",
 }
 
 
