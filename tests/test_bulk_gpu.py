@@ -124,12 +124,13 @@ def test_two_chains_per_lane(R, oracle_mod, step):
                             chains=2)
             assert_same(R.generate_at(a, off, n, "f32", tune=t), want,
                         f"{step}/f32/{depth}/{block}/{grid}")
-        # one chain, each 44-deep run from one product
-        for block, grid in [(1024, 0), (32, 1), (96, 7), (896, 152), (64, 1000)]:
+        # one chain, each 44-deep run from one product, one or two tile buffers
+        for block, grid, buffers in [(1024, 0, 1), (32, 1, 1), (96, 7, 1), (896, 152, 1),
+                                     (64, 1000, 1), (512, 0, 2), (128, 3, 2)]:
             t = R.make_tune(step=step, layout="tiled", depth=44, block=block, grid=grid,
-                            chains=1)
+                            chains=1, buffers=buffers)
             assert_same(R.generate_at(a, off, n, "f32", tune=t), want,
-                        f"{step}/f32/44/{block}/{grid}/one chain")
+                        f"{step}/f32/44/{block}/{grid}/{buffers}/one chain")
 
 
 def test_windows_around_tiny_variates(R, oracle_mod):

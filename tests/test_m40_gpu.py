@@ -62,7 +62,8 @@ TUNES = [None,
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "u64"])
 def test_matches_the_oracle_for_every_tuning(R, oracle_mod, dtype):
-    extra = [dict(depth=44, block=64, grid=5), dict(depth=44, block=1024)] if dtype == "f32" else []
+    extra = ([dict(depth=44, block=64, grid=5), dict(depth=44, block=1024),
+              dict(depth=44, block=512, buffers=2)] if dtype == "f32" else [])
     for k, tune in enumerate(TUNES + extra):  # 44-deep runs: FP32 on one chain only
         for a, off, n in [(M40 + 100, 0, 1), (2 ** 64 - 1, 12345, 31 * 32 * 5 + 17),
                           (M40 + 987654321, 2 ** 40 + 7, 100003)]:
