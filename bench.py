@@ -571,13 +571,28 @@ def measure_device_api(rng, stream, steps: int):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    for _ in range(3):
+        rng.device_api_checksum(SEED, 0, n, threads=threads, stream=stream, dtype="f32")
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        rng.device_api_checksum(SEED, 0, n, threads=threads, stream=stream, dtype="f32")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1) / steps
     return {"workload": "2^30 FP64 variates from a = 3^33+12345 consumed in registers by a "
                         "kernel written against include/bcn_device.cuh: 2^18 threads x 4096 "
                         "variates, each thread's sum of the variates' bit patterns stored, "
                         "nothing else",
             "launches": steps, "ms_per_launch": ms, "variates_per_s": n / (ms / 1e3),
             "roofline": issue_roofline(profiled_value("inst_per_variate", "devapi_2e30", "device"),
-                                       n / (ms / 1e3), "inst_per_variate[devapi_2e30]")}
+                                       n / (ms / 1e3), "inst_per_variate[devapi_2e30]"),
+            "f32_runs": {"workload": "the same 2^30 variates as FP32, 32 at a time from "
+                                     "bcn_device::f32_run (one product per run)",
+                         "ms_per_launch": ms32, "variates_per_s": n / (ms32 / 1e3),
+                         "roofline": issue_roofline(
+                             profiled_value("inst_per_variate", "devapi32_2e30", "device"),
+                             n / (ms32 / 1e3), "inst_per_variate[devapi32_2e30]")}}
 
 
 def measure_serving(rng, n_requests: int = 20000):

@@ -10,6 +10,8 @@
 //   __global__ void sim(uint64_t seed, ...) {
 //     bcn_device::Stream g = bcn_device::make_stream(seed, my_first_variate);
 //     for (...) { double u = bcn_device::next_f64(g); ... }
+//     float w[32];                      // or 32 floats at a time, from one product:
+//     bcn_device::f32_run<32>(seed, my_first_float, w);
 //   }
 //
 // Variate i of the sequence seeded with start index a (Algorithm BB) is
@@ -20,7 +22,9 @@
 // step 1 (3^33+100 <= a <= 2^53); nothing is checked on the device.
 #pragma once
 #include <cstdint>
+#include <utility>
 
+#include "bcn_digits_math.cuh"
 #include "bcn_math.cuh"
 
 namespace bcn_device {
@@ -81,6 +85,57 @@ __device__ inline uint64_t next_state(Stream& s) {
   const uint64_t z = s.Z >> bcn::kZShift;
   s.Z = bcn::shared_advance_scaled(s.Z);
   return z;
+}
+
+namespace detail {
+template <int C, int I>
+__device__ __forceinline__ void f32_run_word(uint32_t z0, uint32_t z1,
+                                             uint32_t (&r)[bcn::DigitGeometry<C>::W],
+                                             uint32_t& v0, uint32_t& v1, float (&v)[C],
+                                             uint32_t& qmin) {
+  bcn::run_product_word<bcn::DigitGeometry<C>::W, I>(z0, z1, r[I], v0, v1);
+  constexpr int i = bcn::DigitGeometry<C>::digit_of_word(I);
+  if constexpr (i >= 0)
+    v[C - 1 - i] = __uint_as_float(bcn::f32_from_digit_words(
+        bcn::run_bits32<53 * i + 21>(r), bcn::run_bits32<53 * i - 11>(r), qmin));
+}
+template <int C, int... I>
+__device__ __forceinline__ void f32_run_words(std::integer_sequence<int, I...>, uint64_t z,
+                                              float (&v)[C], uint32_t& qmin) {
+  const uint32_t z0 = (uint32_t)z, z1 = (uint32_t)(z >> 32);
+  uint32_t r[bcn::DigitGeometry<C>::W];
+  uint32_t v0 = 0, v1 = 0;
+  (f32_run_word<C, I>(z0, z1, r, v0, v1, v, qmin), ...);
+}
+}  // namespace detail
+
+// C consecutive FP32 variates, elements offset + extra .. offset + extra +
+// C - 1 of the sequence seeded with start_index (the sum taken without
+// 64-bit wrap-around), into v[0..C): the same values as C calls of next_f32,
+// made together from one product of the state one past them
+// (bcn_digits_math.cuh) -- about 19 instructions a variate against about 42
+// for next_f32.  C is a compile-time constant; v is meant to stay in
+// registers.  One skip-ahead per call; a run holding a digit that may round
+// up or a variate below 2^-20 (about C in 2^16 runs) is made again exactly.
+template <int C>
+__device__ inline void f32_run(uint64_t start_index, uint64_t offset, uint64_t extra,
+                               float (&v)[C]) {
+  const uint64_t e0 = (start_index - bcn::kM) % bcn::kP;
+  const uint64_t e = bcn::exponent_add(bcn::exponent_add(e0, offset), extra);
+  const uint64_t z = bcn::seed_state_table(bcn::exponent_add(e, C + 1));  // one past the run
+  uint32_t qmin = 0xffffffffu;
+  detail::f32_run_words<C>(std::make_integer_sequence<int, bcn::DigitGeometry<C>::W>{}, z, v,
+                           qmin);
+  if (__builtin_expect(qmin == 0, 0)) {
+    Stream s;
+    s.Z = bcn::seed_state_table(bcn::exponent_add(e, 1)) << bcn::kZShift;  // the run's first
+    for (int i = 0; i < C; ++i) v[i] = next_f32(s);
+  }
+}
+
+template <int C>
+__device__ inline void f32_run(uint64_t start_index, uint64_t offset, float (&v)[C]) {
+  f32_run<C>(start_index, offset, 0, v);
 }
 
 }  // namespace bcn_device

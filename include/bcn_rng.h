@@ -510,13 +510,26 @@ rng_status rng_device_api_check(uint64_t start_index, uint64_t offset, uint64_t 
  * shared memory): `threads` threads (a positive multiple of 128, else
  * RNG_EINVAL) each take variates [t*n/T, (t+1)*n/T) of offset .. offset+n-1
  * of the sequence seeded with start_index (else RNG_ERANGE) and consume them
- * in registers; thread t writes only the sum modulo 2^64 of their FP64 bit
+ * in registers; thread t writes only the sum modulo 2^64 of their bit
  * patterns to sums[t] (a caller-owned device array of `threads` words,
- * 8-byte aligned, else RNG_EINVAL).  n = 0 writes zeros.  Nothing else is
- * stored and the consumer is one integer add per variate, so the call times
- * the generator itself.  Asynchronous on `cuda_stream`. */
+ * 8-byte aligned, else RNG_EINVAL).  dt = RNG_F64: one next_f64 call per
+ * variate; RNG_F32: runs of 32 from f32_run, the rest from next_f32 (32-bit
+ * patterns); any other dt is RNG_EINVAL.  n = 0 writes zeros.  Nothing else
+ * is stored and the consumer is one integer add per variate, so the call
+ * times the generator itself.  Asynchronous on `cuda_stream`. */
 rng_status rng_device_api_checksum(uint64_t start_index, uint64_t offset, uint64_t n,
-                                   uint64_t *sums, uint32_t threads, void *cuda_stream);
+                                   rng_dtype dt, uint64_t *sums, uint32_t threads,
+                                   void *cuda_stream);
+
+/* The device-side FP32 runs (bcn_device::f32_run): `threads` threads (a
+ * positive multiple of 128, else RNG_EINVAL) each write FP32 variates
+ * [t*n/T, (t+1)*n/T) of offset .. offset+n-1 of the sequence seeded with
+ * start_index (else RNG_ERANGE) to `out` (a caller-owned device array of n
+ * floats, 4-byte aligned, else RNG_EINVAL), in runs of 32 made by f32_run and
+ * the remainder by next_f32, so that the runs meet the same checks as every
+ * other path.  n = 0 is a no-op.  Asynchronous on `cuda_stream`. */
+rng_status rng_device_api_f32_runs(uint64_t start_index, uint64_t offset, uint64_t n,
+                                   float *out, uint32_t threads, void *cuda_stream);
 
 /* -------------------------------------------------------------- autotune */
 

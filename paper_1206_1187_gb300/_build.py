@@ -60,14 +60,15 @@ def _inputs_digest(extra_flags: list[str]) -> str:
 # host-side launchers (the *_api.cu files: argument checks, launch shapes) are
 # kept out of these files so that changing them does not void the counters.
 KERNEL_SOURCES = {
-    "tiled": ["bcn_bulk.cu", "bcn_bulk.cuh", "bcn_digits.cuh", "bcn_gen.cuh", "bcn_math.cuh",
-              "bcn_internal.h"],
-    "batch": ["bcn_batch.cu", "bcn_batch.cuh", "bcn_digits.cuh", "bcn_gen.cuh", "bcn_math.cuh",
-              "bcn_internal.h"],
+    "tiled": ["bcn_bulk.cu", "bcn_bulk.cuh", "bcn_digits.cuh", "bcn_digits_math.cuh",
+              "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
+    "batch": ["bcn_batch.cu", "bcn_batch.cuh", "bcn_digits.cuh", "bcn_digits_math.cuh",
+              "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
     "mc": ["bcn_mc.cu", "bcn_mc.cuh", "bcn_gen.cuh", "bcn_math.cuh", "bcn_internal.h"],
-    "m40": ["bcn_m40.cu", "bcn_m40.cuh", "bcn_digits.cuh", "bcn_gen.cuh", "bcn_math.cuh",
-            "bcn_math40.cuh", "bcn_internal.h"],
-    "device": ["bcn_device_check.cu", "bcn_device.cuh", "bcn_math.cuh", "bcn_internal.h"],
+    "m40": ["bcn_m40.cu", "bcn_m40.cuh", "bcn_digits.cuh", "bcn_digits_math.cuh", "bcn_gen.cuh",
+            "bcn_math.cuh", "bcn_math40.cuh", "bcn_internal.h"],
+    "device": ["bcn_device_check.cu", "bcn_device.cuh", "bcn_digits_math.cuh", "bcn_math.cuh",
+               "bcn_internal.h"],
 }
 
 

@@ -5,7 +5,8 @@
     python -m paper_1206_1187_gb300.cases batch 512 [reps]   # first 512 streams of the batched workload
     python -m paper_1206_1187_gb300.cases batch 4096 [reps]  # the whole batched workload
     python -m paper_1206_1187_gb300.cases mc 16384 [reps]
-    python -m paper_1206_1187_gb300.cases devapi 1073741824 [reps]  # device-side header
+    python -m paper_1206_1187_gb300.cases devapi 1073741824 [reps]    # device-side header
+    python -m paper_1206_1187_gb300.cases devapi32 1073741824 [reps]  # its FP32 runs
     python -m paper_1206_1187_gb300.cases m40 33554432 [reps]      # 3^40, FP64
     python -m paper_1206_1187_gb300.cases m40f32 33554432 [reps]   # 3^40, FP32
 
@@ -53,9 +54,10 @@ def main(argv):
     elif case == "mc":
         for _ in range(reps):
             rng.consume_mc(3 ** 33 + 100, size, 1 << 16)
-    elif case == "devapi":  # size variates consumed in registers by 2^18 threads
+    elif case in ("devapi", "devapi32"):  # size variates consumed by 2^18 threads
         for _ in range(reps):
-            rng.device_api_checksum(seed, 0, size, threads=1 << 18)
+            rng.device_api_checksum(seed, 0, size, threads=1 << 18,
+                                    dtype="f64" if case == "devapi" else "f32")
     else:
         raise SystemExit(f"unknown case {case!r}")
     torch.cuda.synchronize()

@@ -120,7 +120,8 @@ def _load() -> ctypes.CDLL:
         "rng_mc_round_totals": ([vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)], i32),
         "rng_batch_generate_noalloc": ([u32, vp, vp, vp, vp, vp, tp, vp], i32),
         "rng_device_api_check": ([u64, u64, u64, vp, vp, vp, u32, vp], i32),
-        "rng_device_api_checksum": ([u64, u64, u64, vp, u32, vp], i32),
+        "rng_device_api_checksum": ([u64, u64, u64, i32, vp, u32, vp], i32),
+        "rng_device_api_f32_runs": ([u64, u64, u64, vp, u32, vp], i32),
         "rng_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], i32),
         "rng_server_submit": ([vp, u64, u64, u64, i32, ctypes.POINTER(u64)], i32),
         "rng_server_cancel": ([vp, u64], i32),
@@ -413,15 +414,27 @@ def device_api_check(start_index: int, offset: int, n: int, threads: int = 4096,
 
 
 def device_api_checksum(start_index: int, offset: int, n: int, threads: int = 1 << 18,
-                        stream=None):
-    """Per-thread sums mod 2^64 of the FP64 bit patterns of variates consumed
-    in registers by a kernel written against bcn_device.cuh (thread t takes
-    [t*n/T, (t+1)*n/T)); an int64 tensor holding the 64-bit words."""
+                        stream=None, dtype: str = "f64"):
+    """Per-thread sums mod 2^64 of the bit patterns of variates consumed in
+    registers by a kernel written against bcn_device.cuh (thread t takes
+    [t*n/T, (t+1)*n/T); FP64 by next_f64, FP32 by f32_run in runs of 32); an
+    int64 tensor holding the 64-bit words."""
+    code, _ = _dtype(dtype)
     sums = torch.empty(threads, dtype=torch.int64, device="cuda")
-    _check(lib.rng_device_api_checksum(start_index, offset, n,
+    _check(lib.rng_device_api_checksum(start_index, offset, n, code,
                                        ctypes.c_void_p(sums.data_ptr()), threads,
                                        ctypes.c_void_p(_stream_handle(stream))))
     return sums
+
+
+def device_api_f32_runs(start_index: int, offset: int, n: int, threads: int = 4096,
+                        stream=None):
+    """FP32 variates written by a kernel using bcn_device::f32_run (runs of 32,
+    the remainder by next_f32)."""
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib.rng_device_api_f32_runs(start_index, offset, n, ctypes.c_void_p(out.data_ptr()),
+                                       threads, ctypes.c_void_p(_stream_handle(stream))))
+    return out
 
 
 class Batch:

@@ -160,16 +160,24 @@ int main(void) {
 
 
 def test_device_api_checksum_checks_arguments_first(lib):
-    """Seed range, thread count and output pointer are checked on the host,
-    before any launch (these calls need no GPU)."""
+    """Seed range, output type, thread count and output pointer are checked on
+    the host, before any launch (these calls need no GPU)."""
     import ctypes
     fn = lib.lib.rng_device_api_checksum
-    buf = (ctypes.c_uint64 * 128)()
-    assert fn(3 ** 33 + 99, 0, 10, ctypes.cast(buf, ctypes.c_void_p), 128, None) == 2
-    assert fn(2 ** 53 + 1, 0, 10, ctypes.cast(buf, ctypes.c_void_p), 128, None) == 2
+    buf = ctypes.cast((ctypes.c_uint64 * 128)(), ctypes.c_void_p)
+    assert fn(3 ** 33 + 99, 0, 10, 0, buf, 128, None) == 2
+    assert fn(2 ** 53 + 1, 0, 10, 0, buf, 128, None) == 2
     for threads in (0, 100, 129):
-        assert fn(3 ** 33 + 100, 0, 10, ctypes.cast(buf, ctypes.c_void_p), threads, None) == 1
-    assert fn(3 ** 33 + 100, 0, 10, None, 128, None) == 1
+        assert fn(3 ** 33 + 100, 0, 10, 0, buf, threads, None) == 1
+    for dt in (2, 3, -1):
+        assert fn(3 ** 33 + 100, 0, 10, dt, buf, 128, None) == 1
+    assert fn(3 ** 33 + 100, 0, 10, 0, None, 128, None) == 1
+    runs = lib.lib.rng_device_api_f32_runs
+    out = ctypes.cast((ctypes.c_float * 64)(), ctypes.c_void_p)
+    assert runs(3 ** 33 + 99, 0, 10, out, 128, None) == 2
+    assert runs(3 ** 33 + 100, 0, 10, out, 96, None) == 1
+    assert runs(3 ** 33 + 100, 0, 10, None, 128, None) == 1
+    assert runs(3 ** 33 + 100, 0, 0, None, 128, None) == 0  # n = 0: nothing to write
 
 
 def test_the_boundary_is_usable_from_plain_c(lib, tmp_path):

@@ -187,6 +187,26 @@ def test_device_side_api_consumed_in_registers(R, oracle_mod):
             lo, hi = n * t // threads, n * (t + 1) // threads
             w = int(want[lo:hi].astype(object).sum()) % 2 ** 64 if hi > lo else 0
             assert int(sums[t]) == w, (a, off, n, t)
+        # FP32: runs of 32 from f32_run, the rest from next_f32
+        sums = R.device_api_checksum(a, off, n, threads=threads,
+                                     dtype="f32").cpu().numpy().view(np.uint64)
+        want = (oracle_mod.generate(a, off, n, "f32").view(np.uint32) if n
+                else np.zeros(0, dtype=np.uint32))
+        for t in range(threads):
+            lo, hi = n * t // threads, n * (t + 1) // threads
+            w = int(want[lo:hi].astype(object).sum()) % 2 ** 64 if hi > lo else 0
+            assert int(sums[t]) == w, ("f32", a, off, n, t)
+
+
+def test_device_side_f32_runs_match_the_oracle(R, oracle_mod):
+    """bcn_device::f32_run (32 FP32 variates from one product) and next_f32 for
+    the remainder write the oracle's FP32 variates: uneven thread ranges, a
+    range across offset 2^64, ranges shorter than one run."""
+    for a, off, n, threads in [(M + 100, 0, 100003, 128), (M + 777, 12345, (1 << 20) + 5, 1024),
+                               (2 ** 53, 2 ** 64 - 3000, 6000, 128), (M + 5555, 3, 31, 128),
+                               (M + 999, 2 ** 40 + 1, 4096 * 33, 4096)]:
+        got = R.device_api_f32_runs(a, off, n, threads=threads)
+        assert_same(got, oracle_mod.generate(a, off, n, "f32"), f"{a} {off} {n} {threads}")
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -511,6 +531,8 @@ def test_fp32_near_float_boundaries(R, oracle_mod):
         for shape in shapes:
             t = R.make_tune(step="shared", layout="tiled", **shape)
             assert_same(R.generate_at(a, off, 4001, "f32", tune=t), want, f"{z} {shape}")
+        # the device-side runs (bcn_device::f32_run), whose flagged runs are made again
+        assert_same(R.device_api_f32_runs(a, off, 4001, threads=128), want, f"{z} device runs")
         outs = [torch.empty(4001, dtype=torch.float32, device="cuda"),
                 torch.empty(3, dtype=torch.float64, device="cuda")]
         b = R.Batch(np.array([a, a], dtype=np.uint64), np.array([4001, 3], dtype=np.uint64),

@@ -25,6 +25,7 @@ READ_BY_BENCH = {
     ("traffic_per_algorithmic_byte", "batch_512"): "batch",
     ("inst_per_variate", "batch_512"): "batch",
     ("inst_per_variate", "devapi_2e30"): "device",
+    ("inst_per_variate", "devapi32_2e30"): "device",
 }
 
 
