@@ -610,7 +610,7 @@ def test_run_constant_is_minus_the_inverse_of_m():
     assert sum(w << (32 * i) for i, w in enumerate(neg_minv_words_model(2))) % 2 ** 53 == MP
 
 
-@pytest.mark.parametrize("C", [44, 4, 12, 252])
+@pytest.mark.parametrize("C", [44, 32, 4, 12, 252])
 def test_run_product_fields_are_the_runs_quotients(C):
     """Field i of z N mod 2^(53 C) is floor(2^53 s / m) of the state s that
     lies i + 1 steps before z (the 2-adic digits of -z/m); the word-level
