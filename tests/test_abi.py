@@ -200,3 +200,41 @@ def test_the_boundary_is_usable_from_plain_c(lib, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert r.stdout.strip() == f"ok {lib.version()}"
+
+
+DEVICE_KERNEL = r"""
+#include "bcn_device.cuh"
+
+__global__ void user_sim(unsigned long long seed, unsigned long long first, double* f64,
+                         float* f32, unsigned long long* st, float* runs) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  bcn_device::Stream g = bcn_device::make_stream(seed, first, 4ull * t);
+  bcn_device::Stream h = g, k = g;
+  for (int i = 0; i < 4; ++i) {
+    f64[4 * t + i] = bcn_device::next_f64(g);
+    f32[4 * t + i] = bcn_device::next_f32(h);
+    st[4 * t + i] = bcn_device::next_state(k);
+  }
+  float w[8];
+  bcn_device::f32_run<8>(seed, first, 8ull * t, w);
+  for (int i = 0; i < 8; ++i) runs[8 * t + i] = w[i];
+}
+"""
+
+
+def test_device_header_is_usable_from_a_user_kernel(tmp_path):
+    """include/bcn_device.cuh compiles for sm_103a in a user's kernel with only
+    include/ on the include path (no GPU needed to compile)."""
+    import subprocess
+    from paper_1206_1187_gb300 import _build
+    try:
+        nvcc = _build._nvcc()
+    except RuntimeError:
+        pytest.skip("no nvcc")
+    src = tmp_path / "user.cu"
+    src.write_text(DEVICE_KERNEL)
+    r = subprocess.run([nvcc] + _build.ARCH + ["-std=c++17", "-O3", "-I",
+                                               os.path.join(ROOT, "include"), "-c", str(src),
+                                               "-o", str(tmp_path / "user.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
